@@ -1,0 +1,78 @@
+/*
+ * CPU oracle of the cell-centred ALE ADER-WENO finite volume scheme with
+ * time-accurate local time stepping (Boscheri, Dumbser, Zanotti).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This plain, serial FP64 C implementation exists
+ * to check the CUDA path; only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or helper with the CUDA library.
+ *
+ * Array layouts match the C ABI of the CUDA library (row-major, the last
+ * index fastest):
+ *   Q, QM      [n_tris][4]   conserved (rho, rho u, rho v, rho E)
+ *   HM         [n_tris][3]   geometric memory (x, y, t components)
+ *   t, dt      [n_tris]      int64 ticks, 1 tick = t_end / 2^K
+ *   X          [n_tris][6]   own vertex coordinates x0,y0,x1,y1,x2,y2
+ *   qhat       [n_tris][N_st][4], space-time node l = tau_index*Mc + s
+ *   node X     [n_nodes][2], node t [n_nodes] int64 ticks
+ */
+#ifndef AW_ORACLE_H
+#define AW_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oc_ctx oc_ctx;
+
+typedef struct {
+  int order_M;          /* polynomial degree M in {1,2,3} */
+  double gamma;         /* ratio of specific heats */
+  double cfl;           /* CFL number, eq. timestep */
+  int time_quantum_log2;/* K: t_end is 2^K ticks */
+  double t_end;
+  int gts;              /* 1: global time step (min of local steps) */
+  int predictor_iters;  /* Picard iterations of eq. CGfinal; <=0 means M+1 */
+  int mesh_velocity;    /* 0: V = v (Lagrangian-type), 1: V = 0 (Eulerian) */
+} oc_config;
+
+int oc_create(const oc_config* cfg, oc_ctx** out);
+void oc_destroy(oc_ctx* c);
+const char* oc_last_error(const oc_ctx* c);
+int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris,
+                 const int32_t* tri, const int8_t* bc, const int8_t* shift,
+                 const double* period);
+int oc_load_state(oc_ctx* c, const double* Q);
+int oc_sweep(oc_ctx* c, int64_t* n_updated);
+int oc_get_elem(const oc_ctx* c, double* Q, double* QM, double* HM, int64_t* t,
+                int64_t* dt, double* X, int64_t* count, double* qhat);
+int oc_set_elem(oc_ctx* c, const double* Q, const double* QM, const double* HM,
+                const int64_t* t, const int64_t* dt, const double* X,
+                const int64_t* count, const double* qhat);
+int oc_get_nodes(const oc_ctx* c, double* X, int64_t* t);
+int oc_set_nodes(oc_ctx* c, const double* X, const int64_t* t);
+int64_t oc_n_st(const oc_ctx* c);
+int64_t oc_n_edges(const oc_ctx* c);
+/* diagnostics: [0] max GCL residual / |T|, [1] number of updates checked */
+int oc_diag(const oc_ctx* c, double* out);
+/* stencils of element i: members[7][n_e] (-1 where a stencil was dropped),
+   total stencil S^W (returns its size; writes up to cap entries) */
+int oc_get_stencils(const oc_ctx* c, int64_t i, int32_t* members, int32_t* sw, int cap);
+/* Debug entry points used by the pin tests. */
+int oc_reconstruct_eval(oc_ctx* c, int64_t i, int64_t npts, const double* xy, double* out);
+int oc_predict_debug(oc_ctx* c, const double* X6, double dt_sec, const double* w_nodal,
+                     double* qhat_out);
+int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const double* n3,
+                  int bc, double* out);
+int oc_eval_qh(const oc_ctx* c, const double* qhat, int64_t npts, const double* pts, double* out);
+/* tables: what = 0 Dubiner at points (npts x Mc), 1 Sigma (Mc x Mc),
+   2 GLL nodes (M+1), 3 K_t ((M+1)^2), 4 M_t ((M+1)^2), 5 lattice nodes (Mc x 2),
+   6 Gauss-Legendre nodes+weights on [0,1] for n=npts (2n),
+   7 spatial Lagrange basis at points (npts x Mc) */
+int oc_table(const oc_ctx* c, int what, int64_t npts, const double* pts, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
