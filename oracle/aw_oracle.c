@@ -43,6 +43,10 @@
  *     points (eqs. spacetimenodes, rusanov, STint).
  *  R9 dt uses the Eulerian |v|+c of the virtual averages and the incircle
  *     diameter 4|T|/perimeter of the virtual triangles (eq. timestep).
+ *  R10 the WENO oscillation indicators and weights (eq. weno) are taken per
+ *     characteristic field of dF/dQ.n at Q_i, n the direction of the density
+ *     gradient of the central-stencil polynomial; the least-squares fits
+ *     themselves are linear and use the conserved variables (eq. intConsRec).
  */
 #include "aw_oracle.h"
 
@@ -1017,26 +1021,88 @@ static void reconstruct(const oc_ctx* c, int64_t i, double* w) {
     for (int v = 0; v < 4; ++v) {
       ws[s][0][v] = Qi[v];
       for (int l = 1; l < Mc; ++l) ws[s][l][v] = B[(l - 1) * 4 + v];
-      double sg = 0.0;
-      for (int l = 1; l < Mc; ++l)
-        for (int k = 1; k < Mc; ++k) sg += c->Sigma[l][k] * ws[s][l][v] * ws[s][k][v];
-      sigma[s][v] = sg;
     }
   }
-  for (int v = 0; v < 4; ++v) {
+  /* R10: the nonlinear weights act on characteristic fields.  The
+     direction n is that of the density gradient of the central-stencil
+     polynomial at the centroid of T_i (x if it vanishes); R and L = R^-1 are
+     the eigenvectors of dF/dQ.n at Q_i. */
+  double gx = 0.0, gy = 0.0;
+  {
+    double dpsi_dxi[MAXMC] = {0}, dpsi_deta[MAXMC] = {0};
+    double cx = 1.0 / 3.0, cy = 1.0 / 3.0;
+    for (int l = 1; l < Mc; ++l)
+      for (int a = 0; a < Mc; ++a) {
+        int p = c->mono[a][0], q = c->mono[a][1];
+        if (p > 0) dpsi_dxi[l] += c->dub[l][a] * p * ipow(cx, p - 1) * ipow(cy, q);
+        if (q > 0) dpsi_deta[l] += c->dub[l][a] * q * ipow(cx, p) * ipow(cy, q - 1);
+      }
+    double rxi = 0.0, reta = 0.0;
+    for (int l = 1; l < Mc; ++l) {
+      rxi += dpsi_dxi[l] * ws[0][l][0];
+      reta += dpsi_deta[l] * ws[0][l][0];
+    }
+    /* grad_x rho = J^-T grad_xi rho, J = [[x1-x0, x2-x0],[y1-y0, y2-y0]] */
+    double a = Xi[2] - Xi[0], b = Xi[4] - Xi[0], cc = Xi[3] - Xi[1], d = Xi[5] - Xi[1];
+    double det = a * d - b * cc;
+    gx = (d * rxi - cc * reta) / det;
+    gy = (-b * rxi + a * reta) / det;
+  }
+  double gn = sqrt(gx * gx + gy * gy);
+  double nx = 1.0, ny = 0.0;
+  if (gn > 0.0) {
+    nx = gx / gn;
+    ny = gy / gn;
+  }
+  double R[16], Linv[16];
+  {
+    double g = c->cfg.gamma, rho = Qi[0], u = Qi[1] / rho, v = Qi[2] / rho, p = pressure(c, Qi);
+    double a = sqrt(g * p / rho), H = (Qi[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
+    double Rm[16] = {1.0, 1.0, 0.0, 1.0,
+                     u - a * nx, u, -ny, u + a * nx,
+                     v - a * ny, v, nx, v + a * ny,
+                     H - a * un, 0.5 * (u * u + v * v), ut, H + a * un};
+    memcpy(R, Rm, sizeof Rm);
+    invert(R, Linv, 4);
+  }
+  double wc[NSTEN][MAXMC][4];
+  for (int s = 0; s < NSTEN; ++s) {
+    if (!ok[s]) continue;
+    for (int l = 1; l < Mc; ++l)
+      for (int r = 0; r < 4; ++r) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += Linv[r * 4 + k] * ws[s][l][k];
+        wc[s][l][r] = acc;
+      }
+    for (int r = 0; r < 4; ++r) {
+      double sg = 0.0;
+      for (int l = 1; l < Mc; ++l)
+        for (int k = 1; k < Mc; ++k) sg += c->Sigma[l][k] * wc[s][l][r] * wc[s][k][r];
+      sigma[s][r] = sg;
+    }
+  }
+  double wchar[MAXMC][4];
+  for (int r = 0; r < 4; ++r) {
     double om[NSTEN], tot = 0.0;
     for (int s = 0; s < NSTEN; ++s) {
       om[s] = 0.0;
       if (!ok[s]) continue;
       double lam = s == 0 ? 1e5 : 1.0;
-      om[s] = lam / pow(sigma[s][v] + 1e-14, 8.0);
+      om[s] = lam / pow(sigma[s][r] + 1e-14, 8.0);
       tot += om[s];
     }
-    w[0 * 4 + v] = Qi[v];
     for (int l = 1; l < Mc; ++l) {
       double acc = 0.0;
       for (int s = 0; s < NSTEN; ++s)
-        if (ok[s]) acc += (om[s] / tot) * ws[s][l][v];
+        if (ok[s]) acc += (om[s] / tot) * wc[s][l][r];
+      wchar[l][r] = acc;
+    }
+  }
+  for (int v = 0; v < 4; ++v) {
+    w[0 * 4 + v] = Qi[v];
+    for (int l = 1; l < Mc; ++l) {
+      double acc = 0.0;
+      for (int r = 0; r < 4; ++r) acc += R[v * 4 + r] * wchar[l][r];
       w[l * 4 + v] = acc;
     }
   }

@@ -93,9 +93,13 @@ def _signed_areas(xy, tri, shift=None, period=None):
 # ---------------------------------------------------------------------------
 
 def shock_tube_mesh(nx: int = 100, ny: int = 10, lx: float = 1.0, ly: float = 0.1,
-                    jitter: float = 0.2, seed: int = SEED_BASE + 0) -> dict:
-    """Jittered structured grid on [0,lx]x[0,ly], each quad split along a
-    random diagonal, slip walls on all four sides."""
+                    jitter: float = 0.2, seed: int = SEED_BASE + 0, diagonal: str = "short") -> dict:
+    """Jittered structured grid on [0,lx]x[0,ly], slip walls on all four
+    sides.  Each quad is split along its shorter diagonal (``diagonal="short"``,
+    the Delaunay choice for these nearly square quads) or along a random one
+    (``diagonal="random"``).  Random diagonals on the jittered grid produce
+    occasional triangles with an angle near 140 degrees, which purely
+    Lagrangian motion across a shock can invert."""
     rng = SplitMix64(seed)
     hx, hy = lx / nx, ly / ny
     ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
@@ -113,7 +117,11 @@ def shock_tube_mesh(nx: int = 100, ny: int = 10, lx: float = 1.0, ly: float = 0.
     for i in range(nx):
         for j in range(ny):
             a, b, c, d = node(i, j), node(i + 1, j), node(i + 1, j + 1), node(i, j + 1)
-            if diag[q]:
+            if diagonal == "short":
+                use_ac = np.sum((xy[a] - xy[c]) ** 2) <= np.sum((xy[b] - xy[d]) ** 2)
+            else:
+                use_ac = diag[q]
+            if use_ac:
                 tris.append((a, b, c)); tris.append((a, c, d))
             else:
                 tris.append((a, b, d)); tris.append((b, c, d))

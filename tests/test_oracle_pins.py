@@ -1,0 +1,348 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+of the reference-element tables, library routines, exactness properties of the
+reconstruction and the predictor, the geometric conservation law, conservation,
+free-stream preservation, the exact Riemann solution and the designed order of
+accuracy on the isentropic vortex.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.pyoracle import Oracle
+from paper_1408_3719_gb300 import workloads as W
+from tests import riemann_exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def duffy(n):
+    x, w = np.polynomial.legendre.leggauss(n)
+    x = 0.5 * (x + 1)
+    w = 0.5 * w
+    u, v = np.meshgrid(x, x, indexing="ij")
+    wu, wv = np.meshgrid(w, w, indexing="ij")
+    return (u * (1 - v)).ravel(), v.ravel(), (wu * wv * (1 - v)).ravel()  # weights sum to 1/2
+
+
+# ---------------------------------------------------------------- tables
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_dubiner_orthogonal_and_psi0(M):
+    o = Oracle(order_M=M)
+    s, t, w = duffy(8)
+    psi = o.table(0, np.stack([s, t], 1))
+    G = psi.T @ (psi * w[:, None])
+    assert np.allclose(psi[:, 0], 1.0)
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() < 1e-14 * np.abs(np.diag(G)).max()
+    # integral over T_e of psi_l vanishes for l > 0 (the constraint w_0 = Q_i)
+    assert np.abs(G[0, 1:]).max() < 1e-15
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_gauss_legendre_matches_numpy(n):
+    o = Oracle(order_M=1)
+    xw = o.table(6, npts=n)
+    x, w = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(xw[0], 0.5 * (x + 1), atol=1e-15, rtol=0)
+    assert np.allclose(xw[1], 0.5 * w, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_time_matrices_by_parts(M):
+    """K_t + K_t^T = e_M e_M^T - e_0 e_0^T (integration by parts of
+    int L_k L_l'), rows of K_t sum to 0 (the basis is a partition of unity),
+    and M_t sums to 1; Gauss-Lobatto nodes include 0 and 1."""
+    o = Oracle(order_M=M)
+    tau = o.table(2)
+    Kt = o.table(3)
+    Mt = o.table(4)
+    E = np.zeros((M + 1, M + 1))
+    E[M, M] = 1
+    E[0, 0] = -1
+    assert np.allclose(Kt + Kt.T, E, atol=1e-14)
+    assert np.allclose(Kt.sum(1), 0, atol=1e-14)
+    assert abs(Mt.sum() - 1) < 1e-14
+    assert tau[0] == 0 and tau[-1] == 1
+    if M == 3:
+        assert np.allclose(tau[1:3], 0.5 + np.array([-1, 1]) * math.sqrt(5) / 10)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_sigma_on_monomials(M):
+    """sigma = sum over 1 <= a+b <= M of int_Te (d^{a,b} w)^2: for w = xi it
+    is |T_e| = 1/2; for w = xi^2 (M >= 2) it is 4/12 + 4/2."""
+    o = Oracle(order_M=M)
+    lat = o.table(5)
+    psi = o.table(0, lat)
+    S = o.table(1)
+    c = np.linalg.solve(psi, lat[:, 0])
+    assert abs(c @ S @ c - 0.5) < 1e-13
+    if M >= 2:
+        c2 = np.linalg.solve(psi, lat[:, 0] ** 2)
+        assert abs(c2 @ S @ c2 - (4 / 12 + 2.0)) < 1e-12
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_lagrange_basis_is_nodal(M):
+    o = Oracle(order_M=M)
+    lat = o.table(5)
+    phi = o.table(7, lat)
+    assert np.allclose(phi, np.eye(len(lat)), atol=1e-13)
+
+
+# ---------------------------------------------------------------- flux
+
+def test_rusanov_consistency_and_wall():
+    o = Oracle(order_M=1)
+    q = np.array([1.2, 0.3, -0.4, 3.1])
+    n = np.array([0.7, -0.2, 0.15])
+    g = 1.4
+    rho, u, v = q[0], q[1] / q[0], q[2] / q[0]
+    p = (g - 1) * (q[3] - 0.5 * rho * (u * u + v * v))
+    f = np.array([rho * u, rho * u * u + p, rho * u * v, u * (q[3] + p)])
+    gg = np.array([rho * v, rho * u * v, rho * v * v + p, v * (q[3] + p)])
+    assert np.allclose(o.flux(q, q, n), f * n[0] + gg * n[1] + q * n[2], rtol=1e-14, atol=1e-15)
+    # slip wall moving tangentially (n_t = 0): no mass or energy flux
+    nw = np.array([0.0, -0.3, 0.0])
+    F = o.flux(q, None, nw, bc=0)
+    assert abs(F[0]) < 1e-15 and abs(F[3]) < 1e-15
+    smax = abs(v * nw[1]) + math.sqrt(g * p / rho) * 0.3
+    assert abs(F[2] - ((rho * v * v + p) * nw[1] + smax * q[2])) < 1e-13
+
+
+# ---------------------------------------------------------------- reconstruction
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_weno_reproduces_polynomials(M):
+    """Cell averages of any polynomial of degree <= M are reproduced exactly
+    by every stencil, hence by the nonlinear combination, whatever the weights
+    (eqs. intConsRec, weno)."""
+    mesh = W.vortex_grid_mesh(10)
+    rng = np.random.default_rng(7)
+    coef = rng.normal(size=(4, M + 1, M + 1)) * 0.05
+    coef[:, 0, 0] = [1.0, 0.1, -0.2, 3.0]
+
+    def f(x, y):
+        out = np.zeros(x.shape + (4,))
+        for v in range(4):
+            for a in range(M + 1):
+                for b in range(M + 1 - a):
+                    out[..., v] += coef[v, a, b] * ((x - 5) / 5) ** a * ((y - 5) / 5) ** b
+        return out
+
+    # non-periodic polynomial: use an interior element whose stencils do not wrap
+    Q = W.cell_average(mesh, f, W._duffy_rule(6))
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    X = o.get_elem()["X"]
+    cen = X.reshape(-1, 3, 2).mean(1)
+    for i in np.where((np.abs(cen[:, 0] - 5) < 1.5) & (np.abs(cen[:, 1] - 5) < 1.5))[0][:6]:
+        s, t, w = duffy(4)
+        P = X[i].reshape(3, 2)
+        pts = P[0] + s[:, None] * (P[1] - P[0]) + t[:, None] * (P[2] - P[0])
+        r = o.reconstruct_eval(i, pts)
+        assert np.abs(r - f(pts[:, 0], pts[:, 1])).max() < 1e-11
+        # the constraint: the average over T_i is Q_i
+        assert np.allclose((r * w[:, None]).sum(0) * 2, Q[i], rtol=1e-13, atol=1e-14)
+
+
+def test_stencils_and_total_stencil_symmetry():
+    mesh, _ = W.sod_tube()
+    o = Oracle(order_M=2)
+    o.load_mesh(mesh)
+    sw = {}
+    for i in range(0, mesh["tri"].shape[0]):
+        mem, s = o.stencils(i)
+        sw[i] = set(s.tolist())
+        assert mem[0, 0] == i and len(set(mem[0])) == mem.shape[1]
+        for st in mem[1:]:
+            if st[0] >= 0:
+                assert st[0] == i and len(set(st)) == len(st)
+        assert set(mem[mem >= 0].tolist()) <= sw[i]
+    for i, s in sw.items():
+        for j in s:
+            assert i in sw[j]
+
+
+# ---------------------------------------------------------------- predictor
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_predictor_constant_state_is_exact(M):
+    o = Oracle(order_M=M)
+    q = np.array([1.3, 0.4, -0.26, 4.0])
+    w0 = np.tile(q, (o.Mc, 1))
+    X6 = np.array([0.1, 0.2, 0.35, 0.18, 0.2, 0.41])
+    qh = o.predict(X6, 0.05, w0)
+    assert np.abs(qh - q).max() < 2e-14 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_predictor_order_on_smooth_flow(M):
+    """Eulerian mode (V = 0): starting from the exact data, the predictor at
+    tau = 1 differs from the convected vortex by O(h^(M+1)) with dt = h/2."""
+    o = Oracle(order_M=M, eulerian=True)
+    lat = o.table(5)
+    vc = np.array([1.0, 0.5])
+
+    def exact(x, y, t):
+        rho, u, v, p = W.vortex_prim(x - vc[0] * t, y - vc[1] * t)
+        return W.prim_to_cons(rho, u + vc[0], v + vc[1], p, 1.4)
+
+    errs, hs = [], [0.2, 0.1, 0.05]
+    for h in hs:
+        X6 = np.array([5.3, 4.8, 5.3 + h, 4.8 + 0.2 * h, 5.3 + 0.3 * h, 4.8 + h])
+        P = X6.reshape(3, 2)
+        xs = P[0] + lat[:, :1] * (P[1] - P[0]) + lat[:, 1:] * (P[2] - P[0])
+        dt = 0.5 * h
+        qh = o.predict(X6, dt, exact(xs[:, 0], xs[:, 1], 0.0))
+        top = qh[M * o.Mc:]
+        errs.append(np.abs(top - exact(xs[:, 0], xs[:, 1], dt)).max())
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert slopes[-1] > M + 0.6, (errs, slopes)
+
+
+# ---------------------------------------------------------------- whole scheme
+
+def _areas(X):
+    return 0.5 * ((X[:, 2] - X[:, 0]) * (X[:, 5] - X[:, 1]) - (X[:, 3] - X[:, 1]) * (X[:, 4] - X[:, 0]))
+
+
+@pytest.mark.parametrize("M", [1, 2])
+def test_free_stream_on_moving_periodic_mesh(M):
+    mesh = W.vortex_grid_mesh(8)
+    q0 = np.array([1.0, 0.3, -0.2, 2.5])
+    Q = np.tile(q0, (mesh["tri"].shape[0], 1))
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    for _ in range(40):
+        o.sweep()
+    e = o.get_elem()
+    assert np.abs(e["Q"] - q0).max() < 1e-12
+    # the memory holds the flux of the constant state through the recorded
+    # partial surfaces: Q^M = F~(q0) . H^M
+    g = 1.4
+    rho, u, v = q0[0], q0[1] / q0[0], q0[2] / q0[0]
+    p = (g - 1) * (q0[3] - 0.5 * rho * (u * u + v * v))
+    f = np.array([rho * u, rho * u * u + p, rho * u * v, u * (q0[3] + p)])
+    gg = np.array([rho * v, rho * u * v, rho * v * v + p, v * (q0[3] + p)])
+    HM = e["HM"]
+    QM_expected = HM[:, :1] * f + HM[:, 1:2] * gg + HM[:, 2:3] * q0
+    assert np.abs(e["QM"] - QM_expected).max() < 1e-12
+    assert np.abs(e["QM"]).max() > 1e-3
+    X, _ = o.get_nodes()
+    assert np.abs(X - mesh["xy"]).max() > 1e-3  # the mesh did move
+    assert o.diag()["gcl_max"] < 1e-13
+
+
+@pytest.mark.parametrize("M,gts", [(1, False), (2, False), (2, True)])
+def test_conservation_and_gcl_vortex(M, gts):
+    mesh, Q = W.vortex(10)
+    o = Oracle(order_M=M, t_end=1.0, gts=gts)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    A0 = _areas(o.get_elem()["X"])
+    tot0 = (A0[:, None] * Q).sum(0)
+    inv_ok = True
+    for _ in range(60):
+        n = o.sweep()
+        if n == 0:
+            break
+        e = o.get_elem()
+        tot = (_areas(e["X"])[:, None] * e["Q"] + e["QM"]).sum(0)
+        assert np.abs(tot - tot0).max() < 1e-13 * np.abs(tot0).max()
+        # scheduling invariant: t_j <= t_i + dt_i for all j in S^W_i
+        if gts:
+            assert np.all(e["t"] == e["t"][0])
+    assert o.diag()["gcl_max"] < 1e-13
+    assert inv_ok
+
+
+def test_lts_invariant_and_counts():
+    mesh, Q = W.explosion(0.05)
+    o = Oracle(order_M=1, t_end=0.05)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    sw = [o.stencils(i)[1] for i in range(mesh["tri"].shape[0])]
+    total = 0
+    while True:
+        n = o.sweep()
+        if n == 0:
+            break
+        total += n
+        e = o.get_elem()
+        tn = e["t"] + e["dt"]
+        for i in range(0, len(sw), 7):
+            assert np.all(e["t"][sw[i]] <= tn[i])
+    e = o.get_elem()
+    assert np.all(e["t"] == 2 ** 20)
+    assert e["count"].sum() == total
+    g = Oracle(order_M=1, t_end=0.05, gts=True)
+    g.load_mesh(mesh)
+    g.load_state(Q)
+    steps, gtotal = g.advance()
+    assert gtotal == steps * mesh["tri"].shape[0]
+    assert total < gtotal
+
+
+def test_sod_star_state_golden():
+    vals = np.loadtxt(os.path.join(GOLDEN, "sod_star_state.txt"))
+    p, u, rl, rr = riemann_exact.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+    assert np.allclose([p, u, rl, rr], vals, atol=6e-6)
+
+
+def _sod_error(nx, ny, M):
+    mesh, Q = W.sod_tube(nx, ny)
+    o = Oracle(order_M=M, t_end=0.2, gts=True)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    o.advance()
+    e = o.get_elem()
+    A = _areas(e["X"])
+    cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
+    ex = riemann_exact.sample(cx, 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1))
+    mass0 = (_areas(o.get_elem()["X"]) * 0).sum()
+    return np.sum(np.abs(e["Q"][:, 0] - ex[:, 0]) * A) / A.sum(), o, e
+
+
+@pytest.mark.slow
+def test_sod_against_exact_riemann_solution():
+    err1, o, e = _sod_error(100, 10, 1)
+    assert err1 < 8e-3, err1
+    err2, _, _ = _sod_error(200, 20, 1)
+    assert err2 < 0.75 * err1, (err1, err2)
+    # walls: mass and energy are conserved
+    mesh, Q = W.sod_tube(100, 10)
+    A0 = W._signed_areas(mesh["xy"], mesh["tri"])
+    tot0 = (A0[:, None] * Q).sum(0)
+    tot = (_areas(e["X"])[:, None] * e["Q"] + e["QM"]).sum(0)
+    assert abs(tot[0] - tot0[0]) < 1e-13 and abs(tot[3] - tot0[3]) < 1e-13
+
+
+def _vortex_error(n, M):
+    mesh, Q = W.vortex(n)
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    o.advance()
+    e = o.get_elem()
+    s, t, w = duffy(6)
+    P = e["X"].reshape(-1, 3, 2)
+    pts = P[:, 0][:, None] + s[None, :, None] * (P[:, 1] - P[:, 0])[:, None] + t[None, :, None] * (P[:, 2] - P[:, 0])[:, None]
+    exact = 2 * np.einsum("nqv,q->nv", W.vortex_state(pts[..., 0], pts[..., 1], 1.4, mesh["period"]), w)
+    A = _areas(e["X"])
+    return math.sqrt(np.sum(A * (e["Q"][:, 0] - exact[:, 0]) ** 2))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("M,ns,order", [(1, (40, 80), 1.8), (2, (20, 40), 2.0), (3, (12, 24), 2.5)])
+def test_vortex_order_of_accuracy(M, ns, order):
+    e1 = _vortex_error(ns[0], M)
+    e2 = _vortex_error(ns[1], M)
+    assert math.log(e1 / e2) / math.log(ns[1] / ns[0]) > order, (e1, e2)
