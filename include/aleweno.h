@@ -1,0 +1,136 @@
+/*
+ * aleweno.h -- C ABI of the GB300 (sm_103a) library for the cell-centred
+ * ALE ADER-WENO finite volume scheme with time-accurate local time stepping
+ * (LTS) on moving unstructured triangles (Boscheri, Dumbser, Zanotti).
+ *
+ * One context = one mesh (or one batch of independent meshes) resident on
+ * one GPU.  The library owns every device allocation of a context.  All
+ * arithmetic of the scheme runs in the library's CUDA kernels in FP64.
+ *
+ * Pointers: every array argument may be a host pointer or a device pointer
+ * (CUDA unified addressing decides); arrays are row-major, the last index
+ * fastest.  Layouts:
+ *   Q, QM   [n_tris][4]  conserved variables (rho, rho u, rho v, rho E)
+ *   HM      [n_tris][3]  geometric memory variable (x, y, t components)
+ *   t, dt   [n_tris]     element time and time step in integer ticks;
+ *                        1 tick = t_end / 2^time_quantum_log2
+ *   X       [n_tris][6]  the element's own vertex coordinates x0,y0,x1,y1,x2,y2
+ *   qhat    [n_tris][N_st][4] predictor degrees of freedom at the space-time
+ *                        nodes l = tau_index * Mc + s, where s runs over the
+ *                        degree-M lattice (i/M, j/M), j outer, i inner, and
+ *                        tau_index over the M+1 Gauss-Lobatto times in [0,1];
+ *                        Mc = (M+1)(M+2)/2, N_st = Mc (M+1)
+ *   node X  [n_nodes][2], node t [n_nodes] ticks
+ *
+ * Errors: every entry point returns AW_OK (0) or a negative AW_ERR_* code and
+ * leaves a message for aw_last_error().  No exception crosses the ABI.  Calls
+ * on one context are not thread-safe; different contexts are independent.
+ */
+#ifndef ALEWENO_H
+#define ALEWENO_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AW_OK = 0,
+  AW_ERR_INVALID_ARG = -1, /* bad argument or unsupported option */
+  AW_ERR_BAD_MESH = -2,    /* clockwise or non-manifold element, too few elements for a stencil */
+  AW_ERR_NONPHYSICAL = -3, /* rho <= 0, p <= 0 or an inverted element after an update */
+  AW_ERR_DEADLOCK = -4,    /* no element satisfies the update criterion although some are unfinished */
+  AW_ERR_TIMEOUT = -5,     /* a bounded device wait ran out */
+  AW_ERR_CUDA = -6,        /* a CUDA runtime call failed */
+  AW_ERR_STATE = -7        /* called before a mesh/state was loaded, or after a failed sweep */
+};
+
+typedef struct aw_ctx aw_ctx;
+
+typedef struct {
+  int order_M;            /* polynomial degree M in {1, 2, 3}: order M+1 in space and time */
+  double gamma;           /* ratio of specific heats of the ideal gas, eq. eos */
+  double cfl;             /* CFL number of the local time step, eq. timestep (<= 0.5) */
+  int time_quantum_log2;  /* K in [1, 50]: t_end is 2^K ticks */
+  double t_end;           /* final time t_f */
+  int gts;                /* 0: local time stepping; 1: global step = min of local steps */
+  int predictor_iters;    /* Picard iterations of eq. CGfinal; <= 0 selects M+1 */
+  int mesh_velocity;      /* 0: V = v, the fluid velocity (Sec. 3); 1: V = 0 (Eulerian) */
+  void* cuda_stream;      /* cudaStream_t to run on, or NULL for a stream the context creates */
+} aw_config;
+
+/* Create a context (Sec. 2.1 set-up).  INVALID_ARG on an unsupported config. */
+int aw_create(const aw_config* cfg, aw_ctx** out);
+void aw_destroy(aw_ctx* ctx);
+const char* aw_last_error(const aw_ctx* ctx);
+
+/* Load a conforming triangulation (Sec. 2.1, eq. trian) and run the
+ * pre-processing of Sec. 2.2: edges, Voronoi neighbourhoods, the seven
+ * reconstruction stencils per element and the symmetric total stencil S^W
+ * (eq. WENOstencil).  tri: [n_tris][3] counter-clockwise node indices;
+ * bc: [n_tris][3] tag of local edge e = (v_e, v_{e+1 mod 3}): -1 interior,
+ * 0 slip wall, 1 transmissive; shift: [n_tris][3][2] int8 periodic image of
+ * each corner (corner = xy[node] + shift * period) or NULL, with period [2]
+ * or NULL (both or neither).  The arrays are copied.  BAD_MESH on invalid input. */
+int aw_load_mesh(aw_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris,
+                 const int32_t* tri, const int8_t* bc, const int8_t* shift,
+                 const double* period);
+
+/* Pre-processing phase of Sec. 2.6: cell averages Q [n_tris][4] at t = 0,
+ * first WENO reconstruction, local time steps (eq. timestep), predictor;
+ * all node and element times set to 0.  NONPHYSICAL if rho or p <= 0. */
+int aw_load_state(aw_ctx* ctx, const double* Q);
+
+/* One cycle of the LTS algorithm (Sec. 2.6): every element satisfying the
+ * update criterion on S^W (eq. WENOupdate) moves its nodes (Sec. 2.4),
+ * computes the space-time edge and vertex fluxes (eqs. spacetimenodes,
+ * rusanov, STint), updates its average with the memory variable (eqs.
+ * PDEfinal, Qm2), re-reconstructs on the virtual stencil (eqs. virtGeom,
+ * virtCellaverage, weno), takes a new local step and runs its predictor.
+ * *n_updated = number of elements updated (0 once all reached t_end).
+ * DEADLOCK, NONPHYSICAL or CUDA on failure. */
+int aw_lts_sweep(aw_ctx* ctx, int64_t* n_updated);
+
+/* One global time step (the GTS reference of Sec. 3.2): requires gts = 1. */
+int aw_gts_step(aw_ctx* ctx, int64_t* n_updated);
+
+/* Run sweeps until every element reached min(t, t_end) or max_sweeps sweeps
+ * ran; t must be t_end or a multiple of the tick.  Outputs may be NULL. */
+int aw_advance_to(aw_ctx* ctx, double t, int64_t max_sweeps, int64_t* sweeps_done,
+                  int64_t* updates_done);
+
+/* Enqueue n sweeps on the context's stream without waiting (device-resident
+ * benchmark loop); a later aw_sync() reports errors and the update count. */
+int aw_enqueue_sweeps(aw_ctx* ctx, int64_t n);
+int aw_sync(aw_ctx* ctx, int64_t* updates_since_last_sync);
+
+/* State access (any argument may be NULL to skip it). */
+int aw_get_state(aw_ctx* ctx, double* Q, double* t_elem);
+int aw_get_nodes(aw_ctx* ctx, double* xy, double* t_node);
+int aw_get_update_counts(aw_ctx* ctx, int64_t* per_elem, int64_t* total);
+int aw_get_elem_arrays(aw_ctx* ctx, double* Q, double* QM, double* HM, int64_t* t,
+                       int64_t* dt, double* X, int64_t* count, double* qhat);
+/* Replace the whole LTS state (checkpoint restore / parity snapshots); all
+ * element arrays and both node arrays are required. */
+int aw_set_elem_arrays(aw_ctx* ctx, const double* Q, const double* QM, const double* HM,
+                       const int64_t* t, const int64_t* dt, const double* X,
+                       const int64_t* count, const double* qhat);
+int aw_get_node_arrays(aw_ctx* ctx, double* X, int64_t* t);
+int aw_set_node_arrays(aw_ctx* ctx, const double* X, const int64_t* t);
+
+/* out[0] = largest GCL residual |sum of int n dS| / |T| seen in an update
+ * (eq. gcl); out[1] = number of element updates; out[2] = sweeps run. */
+int aw_diagnostics(aw_ctx* ctx, double* out);
+/* Sizes: out[0] n_tris, out[1] n_nodes, out[2] n_edges, out[3] N_st,
+ * out[4] total S^W entries. */
+int aw_sizes(aw_ctx* ctx, int64_t* out);
+
+/* Measured FP64 FMA throughput of the current GPU (GFLOP/s), a roofline
+ * denominator: a fixed dependent-chain DFMA kernel over all SMs. */
+int aw_measure_fp64_peak(double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,218 @@
+"""ctypes binding of the C ABI in ``include/aleweno.h`` (argument marshalling
+only: every step of the scheme runs in the CUDA library).
+
+``load()`` opens ``_build/libaleweno.so`` and raises if it is missing; there
+is no CPU fallback.  ``Solver`` mirrors the C entry points.  Arrays may be
+numpy arrays (host) or CUDA torch tensors (device); the library copies with
+unified addressing, so both work.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libaleweno.so")
+
+AW_ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "BAD_MESH", -3: "NONPHYSICAL", -4: "DEADLOCK", -5: "TIMEOUT",
+             -6: "CUDA", -7: "STATE"}
+
+EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load_state", "aw_lts_sweep",
+            "aw_gts_step", "aw_advance_to", "aw_enqueue_sweeps", "aw_sync", "aw_get_state", "aw_get_nodes",
+            "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
+            "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_measure_fp64_peak"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AwConfig(C.Structure):
+    _fields_ = [("order_M", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
+                ("time_quantum_log2", C.c_int), ("t_end", C.c_double), ("gts", C.c_int),
+                ("predictor_iters", C.c_int), ("mesh_velocity", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class AwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{AW_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Open the CUDA library (build it first with paper_1408_3719_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+            lib = C.CDLL(p)
+            P = C.c_void_p
+            i64 = C.c_int64
+            lib.aw_create.argtypes = [C.POINTER(AwConfig), C.POINTER(P)]
+            lib.aw_destroy.argtypes = [P]
+            lib.aw_destroy.restype = None
+            lib.aw_last_error.argtypes = [P]
+            lib.aw_last_error.restype = C.c_char_p
+            lib.aw_load_mesh.argtypes = [P, i64, P, i64, P, P, P, P]
+            lib.aw_load_state.argtypes = [P, P]
+            lib.aw_lts_sweep.argtypes = [P, C.POINTER(i64)]
+            lib.aw_gts_step.argtypes = [P, C.POINTER(i64)]
+            lib.aw_advance_to.argtypes = [P, C.c_double, i64, C.POINTER(i64), C.POINTER(i64)]
+            lib.aw_enqueue_sweeps.argtypes = [P, i64]
+            lib.aw_sync.argtypes = [P, C.POINTER(i64)]
+            lib.aw_get_state.argtypes = [P, P, P]
+            lib.aw_get_nodes.argtypes = [P, P, P]
+            lib.aw_get_update_counts.argtypes = [P, P, C.POINTER(i64)]
+            lib.aw_get_elem_arrays.argtypes = [P] + [P] * 8
+            lib.aw_set_elem_arrays.argtypes = [P] + [P] * 8
+            lib.aw_get_node_arrays.argtypes = [P, P, P]
+            lib.aw_set_node_arrays.argtypes = [P, P, P]
+            lib.aw_diagnostics.argtypes = [P, P]
+            lib.aw_sizes.argtypes = [P, P]
+            lib.aw_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor (host or device)
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def fp64_peak_gflops() -> float:
+    v = C.c_double(0.0)
+    rc = load().aw_measure_fp64_peak(C.byref(v))
+    if rc:
+        raise AwError(rc, "aw_measure_fp64_peak")
+    return v.value
+
+
+class Solver:
+    """One GPU context: mesh, LTS state and configuration."""
+
+    def __init__(self, order_M=1, gamma=1.4, cfl=0.5, t_end=0.2, time_quantum_log2=20, gts=False,
+                 predictor_iters=0, eulerian=False, stream=None):
+        self.lib = load()
+        cfg = AwConfig(order_M, gamma, cfl, time_quantum_log2, t_end, int(gts), predictor_iters, int(eulerian),
+                       stream)
+        h = C.c_void_p()
+        rc = self.lib.aw_create(C.byref(cfg), C.byref(h))
+        if rc:
+            raise AwError(rc, "aw_create")
+        self.h = h
+        self.M = order_M
+        self.Mc = (order_M + 1) * (order_M + 2) // 2
+        self.Nt = order_M + 1
+        self.Nst = self.Mc * self.Nt
+        self.t_end = t_end
+        self.tick = t_end / 2.0 ** time_quantum_log2
+        self.n_tris = 0
+        self.n_nodes = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.aw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise AwError(rc, self.lib.aw_last_error(self.h).decode())
+
+    def load_mesh(self, mesh):
+        xy = np.ascontiguousarray(mesh["xy"], dtype=np.float64)
+        tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32)
+        bc = np.ascontiguousarray(mesh["bc"], dtype=np.int8)
+        shift = None if mesh.get("shift") is None else np.ascontiguousarray(mesh["shift"], dtype=np.int8)
+        period = None if mesh.get("period") is None else np.ascontiguousarray(mesh["period"], dtype=np.float64)
+        self._check(self.lib.aw_load_mesh(self.h, xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), _ptr(bc),
+                                          _ptr(shift), _ptr(period)))
+        self.n_tris = tri.shape[0]
+        self.n_nodes = xy.shape[0]
+
+    def load_state(self, Q):
+        if not hasattr(Q, "data_ptr"):
+            Q = np.ascontiguousarray(Q, dtype=np.float64)
+        self._check(self.lib.aw_load_state(self.h, _ptr(Q)))
+
+    def sweep(self):
+        n = C.c_int64(0)
+        self._check(self.lib.aw_lts_sweep(self.h, C.byref(n)))
+        return n.value
+
+    def gts_step(self):
+        n = C.c_int64(0)
+        self._check(self.lib.aw_gts_step(self.h, C.byref(n)))
+        return n.value
+
+    def advance(self, max_sweeps=10 ** 12):
+        s, u = C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.aw_advance_to(self.h, self.t_end, max_sweeps, C.byref(s), C.byref(u)))
+        return s.value, u.value
+
+    def enqueue(self, n):
+        self._check(self.lib.aw_enqueue_sweeps(self.h, n))
+
+    def sync(self):
+        n = C.c_int64(0)
+        self._check(self.lib.aw_sync(self.h, C.byref(n)))
+        return n.value
+
+    def get_state(self, Q=None, t=None):
+        Q = np.empty((self.n_tris, 4)) if Q is None else Q
+        self._check(self.lib.aw_get_state(self.h, _ptr(Q), _ptr(t)))
+        return Q
+
+    def get_elem(self):
+        n, Nst = self.n_tris, self.Nst
+        out = dict(Q=np.empty((n, 4)), QM=np.empty((n, 4)), HM=np.empty((n, 3)), t=np.empty(n, np.int64),
+                   dt=np.empty(n, np.int64), X=np.empty((n, 6)), count=np.empty(n, np.int64),
+                   qhat=np.empty((n, Nst, 4)))
+        self._check(self.lib.aw_get_elem_arrays(self.h, *[_ptr(out[k]) for k in
+                                                           ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")]))
+        return out
+
+    def set_elem(self, st):
+        arrs = [np.ascontiguousarray(st[k], dtype=np.int64 if k in ("t", "dt", "count") else np.float64)
+                for k in ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")]
+        self._check(self.lib.aw_set_elem_arrays(self.h, *[_ptr(a) for a in arrs]))
+
+    def get_nodes(self):
+        X = np.empty((self.n_nodes, 2))
+        t = np.empty(self.n_nodes, np.int64)
+        self._check(self.lib.aw_get_node_arrays(self.h, _ptr(X), _ptr(t)))
+        return X, t
+
+    def set_nodes(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.int64)
+        self._check(self.lib.aw_set_node_arrays(self.h, _ptr(X), _ptr(t)))
+
+    def update_counts(self):
+        per = np.empty(self.n_tris, np.int64)
+        tot = C.c_int64(0)
+        self._check(self.lib.aw_get_update_counts(self.h, _ptr(per), C.byref(tot)))
+        return per, tot.value
+
+    def diag(self):
+        out = np.zeros(4)
+        self._check(self.lib.aw_diagnostics(self.h, _ptr(out)))
+        return dict(gcl_max=out[0], updates=out[1], sweeps=out[2])
+
+    def sizes(self):
+        out = np.zeros(5, np.int64)
+        self._check(self.lib.aw_sizes(self.h, _ptr(out)))
+        return dict(n_tris=int(out[0]), n_nodes=int(out[1]), n_edges=int(out[2]), n_st=int(out[3]),
+                    sw_entries=int(out[4]))

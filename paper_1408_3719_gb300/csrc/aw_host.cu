@@ -1,0 +1,958 @@
+// Host side of the GB300 ALE ADER-WENO LTS library: reference tables, mesh
+// pre-processing (edges, Voronoi sets, stencils, symmetric total stencils),
+// device memory, the sweep driver and the C ABI of include/aleweno.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/aleweno.h"
+#include "aw_internal.h"
+
+using namespace aw;
+
+struct aw_ctx {
+  aw_config cfg{};
+  Tab tab{};
+  Dev d{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nsm = 0;
+  bool have_mesh = false, have_state = false, failed = false;
+  std::vector<void*> allocs;
+  Counters* hcnt = nullptr;  // pinned mirror of the device counters
+  long long ne = 0, nn = 0, ned = 0, sw_total = 0;
+  std::vector<double> xy0;
+  double* d_corner0 = nullptr;  // element corners at t = 0
+};
+
+namespace {
+
+int set_err(aw_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return set_err(c, AW_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// small exact polynomial algebra on the reference triangle (host only)
+// ---------------------------------------------------------------------------
+struct Poly {  // sum c[a][b] xi^a eta^b, total degree <= 8
+  double c[9][9];
+  Poly() { std::memset(c, 0, sizeof c); }
+};
+
+double factorial(int n) { double r = 1; for (int i = 2; i <= n; ++i) r *= i; return r; }
+double mono_integral(int a, int b) { return factorial(a) * factorial(b) / factorial(a + b + 2); }  // int over T_e
+
+Poly mul(const Poly& p, const Poly& q) {
+  Poly r;
+  for (int a = 0; a < 9; ++a)
+    for (int b = 0; a + b < 9; ++b)
+      if (p.c[a][b] != 0)
+        for (int e = 0; a + e < 9; ++e)
+          for (int f = 0; a + b + e + f < 9; ++f) r.c[a + e][b + f] += p.c[a][b] * q.c[e][f];
+  return r;
+}
+Poly deriv(const Poly& p, int da, int db) {
+  Poly r;
+  for (int a = da; a < 9; ++a)
+    for (int b = db; b < 9; ++b) {
+      double k = 1;
+      for (int i = 0; i < da; ++i) k *= (a - i);
+      for (int i = 0; i < db; ++i) k *= (b - i);
+      r.c[a - da][b - db] += k * p.c[a][b];
+    }
+  return r;
+}
+double integral(const Poly& p) {
+  double s = 0;
+  for (int a = 0; a < 9; ++a)
+    for (int b = 0; a + b < 9; ++b) s += p.c[a][b] * mono_integral(a, b);
+  return s;
+}
+// (xi - 1/3)^a (eta - 1/3)^b expanded
+Poly centred_monomial(int a, int b) {
+  Poly r;
+  for (int i = 0; i <= a; ++i)
+    for (int j = 0; j <= b; ++j) {
+      double ca = factorial(a) / (factorial(i) * factorial(a - i)) * std::pow(-1.0 / 3.0, a - i);
+      double cb = factorial(b) / (factorial(j) * factorial(b - j)) * std::pow(-1.0 / 3.0, b - j);
+      r.c[i][j] += ca * cb;
+    }
+  return r;
+}
+
+// Gauss-Jordan inverse with partial pivoting (n <= 16)
+bool gj_inverse(std::vector<double> a, int n, std::vector<double>& inv) {
+  inv.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[r * n + col]) > std::fabs(a[piv * n + col])) piv = r;
+    if (a[piv * n + col] == 0.0) return false;
+    for (int k = 0; k < n; ++k) {
+      std::swap(a[col * n + k], a[piv * n + k]);
+      std::swap(inv[col * n + k], inv[piv * n + k]);
+    }
+    double d = a[col * n + col];
+    for (int k = 0; k < n; ++k) { a[col * n + k] /= d; inv[col * n + k] /= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = a[r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { a[r * n + k] -= f * a[col * n + k]; inv[r * n + k] -= f * inv[col * n + k]; }
+    }
+  }
+  return true;
+}
+
+int build_tab(aw_ctx* c) {
+  Tab& T = c->tab;
+  const int M = c->cfg.order_M;
+  T.M = M;
+  T.Mc = (M + 1) * (M + 2) / 2;
+  T.Nt = M + 1;
+  T.Nst = T.Mc * T.Nt;
+  T.NU = T.Mc - 1;
+  T.gamma = c->cfg.gamma;
+  T.cfl = c->cfg.cfl;
+  T.T = 1LL << c->cfg.time_quantum_log2;
+  T.tick = std::ldexp(c->cfg.t_end, -c->cfg.time_quantum_log2);
+  T.eulerian = c->cfg.mesh_velocity == 1;
+  T.gts = c->cfg.gts ? 1 : 0;
+  T.nit = c->cfg.predictor_iters > 0 ? c->cfg.predictor_iters : M + 1;
+  const int Mc = T.Mc, Nt = T.Nt;
+  // lattice nodes: rows of constant eta, xi fastest
+  int s = 0;
+  for (int j = 0; j <= M; ++j)
+    for (int i = 0; i <= M - j; ++i) { T.lat[s][0] = double(i) / M; T.lat[s][1] = double(j) / M; ++s; }
+  T.vnode[0] = 0; T.vnode[1] = M; T.vnode[2] = Mc - 1;
+  // Lagrange basis via a Vandermonde matrix in plain monomials (graded order)
+  std::vector<std::pair<int, int>> ex;
+  for (int dgr = 0; dgr <= M; ++dgr)
+    for (int b = 0; b <= dgr; ++b) ex.push_back({dgr - b, b});
+  std::vector<double> V(Mc * Mc), Vi;
+  for (int r = 0; r < Mc; ++r)
+    for (int k = 0; k < Mc; ++k) V[r * Mc + k] = std::pow(T.lat[r][0], ex[k].first) * std::pow(T.lat[r][1], ex[k].second);
+  if (!gj_inverse(V, Mc, Vi)) return set_err(c, AW_ERR_INVALID_ARG, "singular lattice Vandermonde");
+  std::vector<Poly> phi(Mc);
+  for (int r = 0; r < Mc; ++r)
+    for (int k = 0; k < Mc; ++k) phi[r].c[ex[k].first][ex[k].second] += Vi[k * Mc + r];
+  auto peval = [](const Poly& p, double x, double y) {
+    double v = 0;
+    for (int a = 0; a < 9; ++a)
+      for (int b = 0; a + b < 9; ++b)
+        if (p.c[a][b] != 0) v += p.c[a][b] * std::pow(x, a) * std::pow(y, b);
+    return v;
+  };
+  for (int r = 0; r < Mc; ++r) {
+    Poly dx = deriv(phi[r], 1, 0), dy = deriv(phi[r], 0, 1);
+    for (int q = 0; q < Mc; ++q) {
+      T.Dxi[q][r] = peval(dx, T.lat[q][0], T.lat[q][1]);
+      T.Deta[q][r] = peval(dy, T.lat[q][0], T.lat[q][1]);
+    }
+    T.wavg[r] = 2.0 * integral(phi[r]);
+  }
+  // Gauss-Lobatto times and the time Lagrange polynomials in monomial form
+  double tau[kMaxNt];
+  if (M == 1) { tau[0] = 0; tau[1] = 1; }
+  else if (M == 2) { tau[0] = 0; tau[1] = 0.5; tau[2] = 1; }
+  else { tau[0] = 0; tau[1] = 0.5 - std::sqrt(5.0) / 10.0; tau[2] = 0.5 + std::sqrt(5.0) / 10.0; tau[3] = 1; }
+  std::vector<double> Vt(Nt * Nt), Vti;
+  for (int t = 0; t < Nt; ++t)
+    for (int p = 0; p < Nt; ++p) Vt[t * Nt + p] = std::pow(tau[t], p);
+  if (!gj_inverse(Vt, Nt, Vti)) return set_err(c, AW_ERR_INVALID_ARG, "singular time Vandermonde");
+  for (int p = 0; p < Nt; ++p)
+    for (int t = 0; t < Nt; ++t) T.VtInv[p][t] = Vti[p * Nt + t];  // L_t(tau) = sum_p VtInv[p][t] tau^p
+  // K_t = int L_k L_l', M_t = int L_k L_l on [0,1], exactly
+  double Kt[kMaxNt][kMaxNt], Mt[kMaxNt][kMaxNt];
+  for (int k = 0; k < Nt; ++k)
+    for (int l = 0; l < Nt; ++l) {
+      double kk = 0, mm = 0;
+      for (int p = 0; p < Nt; ++p)
+        for (int q = 0; q < Nt; ++q) {
+          mm += T.VtInv[p][k] * T.VtInv[q][l] / (p + q + 1);
+          if (q > 0) kk += T.VtInv[p][k] * q * T.VtInv[q][l] / (p + q);
+        }
+      Kt[k][l] = kk;
+      Mt[k][l] = mm;
+    }
+  for (int t = 0; t < Nt; ++t)
+    for (int u = 0; u < Nt; ++u) {
+      double v = 0;
+      for (int q = 1; q < Nt; ++q) v += T.VtInv[q][u] * q * std::pow(tau[t], q - 1);
+      T.Dtau[t][u] = v;
+    }
+  // test functions of the tau > 0 nodes: K11 qhat_1 = dt M10.. P - K10 qhat_0, K10 = -K11 1
+  std::vector<double> K11((Nt - 1) * (Nt - 1)), K11i;
+  for (int a = 1; a < Nt; ++a)
+    for (int b = 1; b < Nt; ++b) K11[(a - 1) * (Nt - 1) + (b - 1)] = Kt[a][b];
+  if (!gj_inverse(K11, Nt - 1, K11i)) return set_err(c, AW_ERR_INVALID_ARG, "singular K11");
+  for (int a = 0; a < Nt - 1; ++a)
+    for (int u = 0; u < Nt; ++u) {
+      double v = 0;
+      for (int b = 0; b < Nt - 1; ++b) v += K11i[a * (Nt - 1) + b] * Mt[b + 1][u];
+      T.B[a][u] = v;
+    }
+  // Gauss-Legendre points on [0,1] (closed forms)
+  if (Nt == 2) {
+    double h = 0.5 / std::sqrt(3.0);
+    T.glx[0] = 0.5 - h; T.glx[1] = 0.5 + h; T.glw[0] = T.glw[1] = 0.5;
+  } else if (Nt == 3) {
+    double h = 0.5 * std::sqrt(0.6);
+    T.glx[0] = 0.5 - h; T.glx[1] = 0.5; T.glx[2] = 0.5 + h;
+    T.glw[0] = T.glw[2] = 5.0 / 18.0; T.glw[1] = 8.0 / 18.0;
+  } else {
+    double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2)), b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+    double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+    T.glx[0] = 0.5 - 0.5 * b; T.glx[1] = 0.5 - 0.5 * a; T.glx[2] = 0.5 + 0.5 * a; T.glx[3] = 0.5 + 0.5 * b;
+    T.glw[0] = T.glw[3] = 0.5 * wb; T.glw[1] = T.glw[2] = 0.5 * wa;
+  }
+  const double rv[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+  for (int e = 0; e < 3; ++e)
+    for (int g = 0; g < Nt; ++g) {
+      double x = rv[e][0] + T.glx[g] * (rv[(e + 1) % 3][0] - rv[e][0]);
+      double y = rv[e][1] + T.glx[g] * (rv[(e + 1) % 3][1] - rv[e][1]);
+      for (int r = 0; r < Mc; ++r) T.Tr[e][g][r] = peval(phi[r], x, y);
+    }
+  // reconstruction basis: zero-mean centred monomials b_l, l = 1..Mc-1
+  std::vector<Poly> bl;
+  int l = 0;
+  for (int dgr = 1; dgr <= M; ++dgr)
+    for (int b = 0; b <= dgr; ++b) {
+      T.mexp[l][0] = dgr - b;
+      T.mexp[l][1] = b;
+      Poly p = centred_monomial(dgr - b, b);
+      T.mbar[l] = 2.0 * integral(p);
+      bl.push_back(p);
+      ++l;
+    }
+  for (int q = 0; q < Mc; ++q)
+    for (int k = 0; k < T.NU; ++k) T.Bnod[q][k] = peval(bl[k], T.lat[q][0], T.lat[q][1]) - T.mbar[k];
+  // smoothness matrix sigma = c^T S c, S_lm = sum_{1<=a+b<=M} int d^{ab} b_l d^{ab} b_m
+  std::vector<double> S(T.NU * T.NU, 0.0);
+  for (int i = 0; i < T.NU; ++i)
+    for (int j = 0; j < T.NU; ++j) {
+      double v = 0;
+      for (int a = 0; a <= M; ++a)
+        for (int b = 0; a + b <= M; ++b) {
+          if (a + b == 0) continue;
+          v += integral(mul(deriv(bl[i], a, b), deriv(bl[j], a, b)));
+        }
+      S[i * T.NU + j] = v;
+    }
+  // Cholesky S = U^T U (U upper)
+  std::memset(T.SigU, 0, sizeof T.SigU);
+  for (int j = 0; j < T.NU; ++j) {
+    double d = S[j * T.NU + j];
+    for (int k = 0; k < j; ++k) d -= T.SigU[k][j] * T.SigU[k][j];
+    if (!(d > 0)) return set_err(c, AW_ERR_INVALID_ARG, "smoothness matrix not positive definite");
+    T.SigU[j][j] = std::sqrt(d);
+    for (int i = j + 1; i < T.NU; ++i) {
+      double v = S[j * T.NU + i];
+      for (int k = 0; k < j; ++k) v -= T.SigU[k][j] * T.SigU[k][i];
+      T.SigU[j][i] = v / T.SigU[j][j];
+    }
+  }
+  // exact rules for averages of degree-M polynomials over a triangle
+  if (M == 1) {
+    T.nq = 1; T.qb[0][0] = T.qb[0][1] = T.qb[0][2] = 1.0 / 3.0; T.qw[0] = 1.0;
+  } else if (M == 2) {
+    T.nq = 3;
+    for (int k = 0; k < 3; ++k) {
+      for (int m = 0; m < 3; ++m) T.qb[k][m] = (m == k) ? 2.0 / 3.0 : 1.0 / 6.0;
+      T.qw[k] = 1.0 / 3.0;
+    }
+  } else {
+    T.nq = 4;
+    T.qb[0][0] = T.qb[0][1] = T.qb[0][2] = 1.0 / 3.0; T.qw[0] = -27.0 / 48.0;
+    for (int k = 0; k < 3; ++k) {
+      for (int m = 0; m < 3; ++m) T.qb[k + 1][m] = (m == k) ? 0.6 : 0.2;
+      T.qw[k + 1] = 25.0 / 48.0;
+    }
+  }
+  return AW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh pre-processing on the host
+// ---------------------------------------------------------------------------
+struct HostMesh {
+  int ne = 0, nn = 0, ned = 0;
+  bool periodic = false;
+  double period[2] = {0, 0};
+  std::vector<int> tri;
+  std::vector<signed char> bc, shift;
+  std::vector<double> cshift, corner0, cen;
+  std::vector<int> elem_edge, edge_nodes, edge_elem, nbr;
+  std::vector<signed char> edge_loc, edge_bc, v2e_loc, node_type, sten_ok;
+  std::vector<double> nbr_shift, node_n, u_shift;
+  std::vector<int> v2e_ptr, v2e, sw_ptr, sw, u_ptr, u_elem;
+  std::vector<unsigned char> sten;
+};
+
+// offset of element j's centroid seen from element i, nearest periodic image
+inline void centroid_offset(const HostMesh& m, int i, int j, double& dx, double& dy, int& sx, int& sy) {
+  dx = m.cen[2 * j] - m.cen[2 * i];
+  dy = m.cen[2 * j + 1] - m.cen[2 * i + 1];
+  sx = sy = 0;
+  if (m.periodic) {
+    sx = -(int)std::floor(dx / m.period[0] + 0.5);
+    sy = -(int)std::floor(dy / m.period[1] + 0.5);
+    dx = dx + sx * m.period[0];
+    dy = dy + sy * m.period[1];
+  }
+}
+
+int preprocess(aw_ctx* c, HostMesh& m, const double* xy, int ne_s, int M) {
+  const int ne = m.ne, nn = m.nn;
+  // corner offsets and t=0 corners
+  m.cshift.assign(6 * (size_t)ne, 0.0);
+  m.corner0.resize(6 * (size_t)ne);
+  m.cen.resize(2 * (size_t)ne);
+  for (int i = 0; i < ne; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      if (m.periodic) {
+        m.cshift[6 * i + 2 * k] = m.shift[6 * i + 2 * k] * m.period[0];
+        m.cshift[6 * i + 2 * k + 1] = m.shift[6 * i + 2 * k + 1] * m.period[1];
+      }
+      int n = m.tri[3 * i + k];
+      m.corner0[6 * i + 2 * k] = xy[2 * n] + m.cshift[6 * i + 2 * k];
+      m.corner0[6 * i + 2 * k + 1] = xy[2 * n + 1] + m.cshift[6 * i + 2 * k + 1];
+    }
+    const double* X = &m.corner0[6 * i];
+    double area2 = (X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0]);
+    if (!(area2 > 0)) return set_err(c, AW_ERR_BAD_MESH, "element %d is not counter-clockwise", i);
+    m.cen[2 * i] = (X[0] + X[2] + X[4]) / 3.0;
+    m.cen[2 * i + 1] = (X[1] + X[3] + X[5]) / 3.0;
+  }
+  // node -> element CSR (ascending element index)
+  m.v2e_ptr.assign(nn + 1, 0);
+  for (int i = 0; i < ne; ++i)
+    for (int k = 0; k < 3; ++k) m.v2e_ptr[m.tri[3 * i + k] + 1]++;
+  std::partial_sum(m.v2e_ptr.begin(), m.v2e_ptr.end(), m.v2e_ptr.begin());
+  m.v2e.resize(3 * (size_t)ne);
+  m.v2e_loc.resize(3 * (size_t)ne);
+  {
+    std::vector<int> fill(m.v2e_ptr.begin(), m.v2e_ptr.end() - 1);
+    for (int i = 0; i < ne; ++i)
+      for (int k = 0; k < 3; ++k) {
+        int p = fill[m.tri[3 * i + k]]++;
+        m.v2e[p] = i;
+        m.v2e_loc[p] = (signed char)k;
+      }
+  }
+  // twins through a sorted list of directed edges
+  struct DE { long long key; int elem, loc; };
+  std::vector<DE> des(3 * (size_t)ne);
+  for (int i = 0; i < ne; ++i)
+    for (int e = 0; e < 3; ++e) {
+      long long a = m.tri[3 * i + e], b = m.tri[3 * i + (e + 1) % 3];
+      des[3 * i + e] = {a * nn + b, i, e};
+    }
+  std::sort(des.begin(), des.end(), [](const DE& x, const DE& y) { return x.key < y.key || (x.key == y.key && x.elem < y.elem); });
+  for (size_t q = 1; q < des.size(); ++q)
+    if (des[q].key == des[q - 1].key) return set_err(c, AW_ERR_BAD_MESH, "repeated directed edge (non-manifold mesh)");
+  m.nbr.assign(3 * (size_t)ne, -1);
+  std::vector<signed char> nloc(3 * (size_t)ne, -1);
+  for (int i = 0; i < ne; ++i)
+    for (int e = 0; e < 3; ++e) {
+      long long a = m.tri[3 * i + e], b = m.tri[3 * i + (e + 1) % 3];
+      long long key = b * nn + a;
+      auto it = std::lower_bound(des.begin(), des.end(), key, [](const DE& x, long long k) { return x.key < k; });
+      if (it != des.end() && it->key == key) {
+        m.nbr[3 * i + e] = it->elem;
+        nloc[3 * i + e] = (signed char)it->loc;
+      } else if (m.bc[3 * i + e] < 0) {
+        return set_err(c, AW_ERR_BAD_MESH, "boundary edge of element %d has no boundary tag", i);
+      }
+    }
+  // canonical edges: element order, owner = the lower element index
+  m.elem_edge.assign(3 * (size_t)ne, -1);
+  m.edge_nodes.clear(); m.edge_elem.clear(); m.edge_loc.clear(); m.edge_bc.clear();
+  int ned = 0;
+  for (int i = 0; i < ne; ++i)
+    for (int e = 0; e < 3; ++e) {
+      int j = m.nbr[3 * i + e];
+      if (j >= 0 && j < i) { m.elem_edge[3 * i + e] = m.elem_edge[3 * j + nloc[3 * i + e]]; continue; }
+      m.elem_edge[3 * i + e] = ned++;
+      m.edge_nodes.push_back(m.tri[3 * i + e]);
+      m.edge_nodes.push_back(m.tri[3 * i + (e + 1) % 3]);
+      m.edge_elem.push_back(i);
+      m.edge_elem.push_back(j);
+      m.edge_loc.push_back((signed char)e);
+      m.edge_loc.push_back(j >= 0 ? nloc[3 * i + e] : (signed char)-1);
+      m.edge_bc.push_back(j >= 0 ? (signed char)-1 : m.bc[3 * i + e]);
+    }
+  m.ned = ned;
+  // neighbour image offsets
+  m.nbr_shift.assign(6 * (size_t)ne, 0.0);
+  for (int i = 0; i < ne; ++i)
+    for (int e = 0; e < 3; ++e) {
+      int j = m.nbr[3 * i + e];
+      if (j < 0) continue;
+      double dx, dy;
+      int sx, sy;
+      centroid_offset(m, i, j, dx, dy, sx, sy);
+      m.nbr_shift[6 * i + 2 * e] = sx * m.period[0];
+      m.nbr_shift[6 * i + 2 * e + 1] = sy * m.period[1];
+    }
+  // slip-wall constraints of the nodes
+  m.node_type.assign(nn, 0);
+  m.node_n.assign(2 * (size_t)nn, 0.0);
+  for (int ed = 0; ed < ned; ++ed) {
+    if (m.edge_bc[ed] != 0) continue;
+    int i = m.edge_elem[2 * ed], e = m.edge_loc[2 * ed];
+    const double* X = &m.corner0[6 * i];
+    double dx = X[2 * ((e + 1) % 3)] - X[2 * e], dy = X[2 * ((e + 1) % 3) + 1] - X[2 * e + 1];
+    double len = std::sqrt(dx * dx + dy * dy);
+    double n0 = dy / len, n1 = -dx / len;
+    for (int q = 0; q < 2; ++q) {
+      int nd = m.edge_nodes[2 * ed + q];
+      if (m.node_type[nd] == 0) {
+        m.node_type[nd] = 1; m.node_n[2 * nd] = n0; m.node_n[2 * nd + 1] = n1;
+      } else if (m.node_type[nd] == 1) {
+        if (std::fabs(m.node_n[2 * nd] * n1 - m.node_n[2 * nd + 1] * n0) > 1e-8) m.node_type[nd] = 2;
+      }
+    }
+  }
+  // stencils: candidates within vertex-neighbour layers, ordered by centroid distance then index
+  m.sten.assign((size_t)ne * kNSten * ne_s, 0);
+  m.sten_ok.assign((size_t)ne * kNSten, 0);
+  m.u_ptr.assign(ne + 1, 0);
+  m.u_elem.clear();
+  m.u_shift.clear();
+  std::vector<int> mark(ne, -1), layer, members;
+  struct Cand { double d2; int j, sx, sy; };
+  std::vector<Cand> cand;
+  int stamp = 0;
+  auto gather = [&](int i, int depth) {
+    layer.clear();
+    layer.push_back(i);
+    mark[i] = ++stamp;
+    size_t begin = 0;
+    for (int dl = 0; dl < depth; ++dl) {
+      size_t end = layer.size();
+      for (size_t q = begin; q < end; ++q) {
+        int e = layer[q];
+        for (int k = 0; k < 3; ++k) {
+          int nd = m.tri[3 * e + k];
+          for (int p = m.v2e_ptr[nd]; p < m.v2e_ptr[nd + 1]; ++p) {
+            int j = m.v2e[p];
+            if (mark[j] != stamp) { mark[j] = stamp; layer.push_back(j); }
+          }
+        }
+      }
+      begin = end;
+    }
+    cand.clear();
+    for (int j : layer) {
+      Cand cd;
+      double dx, dy;
+      centroid_offset(m, i, j, dx, dy, cd.sx, cd.sy);
+      cd.d2 = dx * dx + dy * dy;
+      cd.j = j;
+      cand.push_back(cd);
+    }
+    std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.d2 < b.d2 || (a.d2 == b.d2 && a.j < b.j); });
+  };
+  std::vector<int> sten_elem(kNSten * ne_s);
+  std::vector<int> sten_sx(kNSten * ne_s), sten_sy(kNSten * ne_s);
+  for (int i = 0; i < ne; ++i) {
+    std::fill(sten_elem.begin(), sten_elem.end(), -1);
+    gather(i, M + 1);
+    if ((int)cand.size() < ne_s) return set_err(c, AW_ERR_BAD_MESH, "element %d: only %d candidates for the central stencil", i, (int)cand.size());
+    for (int q = 0; q < ne_s; ++q) { sten_elem[q] = cand[q].j; sten_sx[q] = cand[q].sx; sten_sy[q] = cand[q].sy; }
+    m.sten_ok[(size_t)i * kNSten] = 1;
+    gather(i, M + 2);
+    const double* X = &m.corner0[6 * i];
+    double cx = m.cen[2 * i], cy = m.cen[2 * i + 1];
+    for (int s = 1; s < kNSten; ++s) {
+      int e = (s - 1) % 3;
+      bool reverse = s >= 4;
+      double ax = X[2 * e] - cx, ay = X[2 * e + 1] - cy;
+      double bx = X[2 * ((e + 1) % 3)] - cx, by = X[2 * ((e + 1) % 3) + 1] - cy;
+      int cntm = 0;
+      sten_elem[s * ne_s + cntm] = i; sten_sx[s * ne_s] = 0; sten_sy[s * ne_s] = 0; ++cntm;
+      for (size_t q = 0; q < cand.size() && cntm < ne_s; ++q) {
+        if (cand[q].j == i) continue;
+        double dx = m.cen[2 * cand[q].j] - cx + cand[q].sx * (m.periodic ? m.period[0] : 0.0);
+        double dy = m.cen[2 * cand[q].j + 1] - cy + cand[q].sy * (m.periodic ? m.period[1] : 0.0);
+        double al = dx * by - dy * bx;
+        double be = ax * dy - ay * dx;
+        bool in = reverse ? (al <= 0.0 && be <= 0.0) : (al >= 0.0 && be >= 0.0);
+        if (!in) continue;
+        sten_elem[s * ne_s + cntm] = cand[q].j;
+        sten_sx[s * ne_s + cntm] = cand[q].sx;
+        sten_sy[s * ne_s + cntm] = cand[q].sy;
+        ++cntm;
+      }
+      if (cntm == ne_s) m.sten_ok[(size_t)i * kNSten + s] = 1;
+      else for (int q = 0; q < ne_s; ++q) sten_elem[s * ne_s + q] = -1;
+    }
+    // unique member list (without i) and local indices
+    members.clear();
+    for (int q = 0; q < kNSten * ne_s; ++q)
+      if (sten_elem[q] >= 0 && sten_elem[q] != i) members.push_back(sten_elem[q]);
+    std::sort(members.begin(), members.end());
+    members.erase(std::unique(members.begin(), members.end()), members.end());
+    if (members.size() > 254) return set_err(c, AW_ERR_BAD_MESH, "element %d: stencil union too large", i);
+    int base = (int)m.u_elem.size();
+    for (int j : members) {
+      m.u_elem.push_back(j);
+      double dx, dy;
+      int sx, sy;
+      centroid_offset(m, i, j, dx, dy, sx, sy);
+      m.u_shift.push_back(sx * m.period[0]);
+      m.u_shift.push_back(sy * m.period[1]);
+    }
+    m.u_ptr[i + 1] = (int)m.u_elem.size();
+    for (int q = 0; q < kNSten * ne_s; ++q) {
+      int j = sten_elem[q];
+      unsigned char loc = 0;
+      if (j >= 0 && j != i) loc = (unsigned char)(1 + (std::lower_bound(members.begin(), members.end(), j) - members.begin()));
+      m.sten[(size_t)i * kNSten * ne_s + q] = loc;
+    }
+    (void)base;
+  }
+  // total stencil: stencils + edge neighbours + Voronoi sets of the vertices, closed under symmetry
+  std::vector<std::vector<int>> S(ne);
+  for (int i = 0; i < ne; ++i) {
+    auto& L = S[i];
+    L.push_back(i);
+    for (int p = m.u_ptr[i]; p < m.u_ptr[i + 1]; ++p) L.push_back(m.u_elem[p]);
+    for (int e = 0; e < 3; ++e)
+      if (m.nbr[3 * i + e] >= 0) L.push_back(m.nbr[3 * i + e]);
+    for (int k = 0; k < 3; ++k) {
+      int nd = m.tri[3 * i + k];
+      for (int p = m.v2e_ptr[nd]; p < m.v2e_ptr[nd + 1]; ++p) L.push_back(m.v2e[p]);
+    }
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+  }
+  std::vector<std::vector<int>> Sx(S);
+  for (int i = 0; i < ne; ++i)
+    for (int j : S[i]) Sx[j].push_back(i);
+  m.sw_ptr.assign(ne + 1, 0);
+  m.sw.clear();
+  for (int i = 0; i < ne; ++i) {
+    auto& L = Sx[i];
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+    m.sw.insert(m.sw.end(), L.begin(), L.end());
+    m.sw_ptr[i + 1] = (int)m.sw.size();
+  }
+  return AW_OK;
+}
+
+template <class T>
+int dalloc(aw_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  if (n == 0) n = 1;
+  CK(cudaMalloc(&q, n * sizeof(T)));
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return AW_OK;
+}
+
+template <class T>
+int dupload(aw_ctx* c, const T** out, const std::vector<T>& v) {
+  T* p;
+  int rc = dalloc(c, &p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  *out = p;
+  return AW_OK;
+}
+
+void free_all(aw_ctx* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->have_mesh = c->have_state = false;
+}
+
+// Counters and epoch stamps restart together (a stale stamp equal to a new
+// epoch would mark an element or node as active).
+int reset_sweep_state(aw_ctx* c) {
+  const Dev& d = c->d;
+  CK(cudaMemsetAsync(d.elem_ready, 0, c->ne * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.elem_touch, 0, c->ne * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.node_moved, 0, c->nn * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.edge_act, 0, c->ned * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.cnt, 0, sizeof(Counters), c->stream));
+  return AW_OK;
+}
+
+int sync_counters(aw_ctx* c) {
+  CK(cudaMemcpyAsync(c->hcnt, c->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return AW_OK;
+}
+
+int check_device_error(aw_ctx* c) {
+  if (c->hcnt->err_code != 0) {
+    c->failed = true;
+    return set_err(c, c->hcnt->err_code, "element %d is non-physical after its update (rho, p or area <= 0)", c->hcnt->err_elem);
+  }
+  return AW_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int aw_create(const aw_config* cfg, aw_ctx** out) {
+  if (!cfg || !out) return AW_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->order_M < 1 || cfg->order_M > kMaxM || !(cfg->t_end > 0) || cfg->time_quantum_log2 < 1 ||
+      cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->mesh_velocity < 0 ||
+      cfg->mesh_velocity > 1)
+    return AW_ERR_INVALID_ARG;
+  aw_ctx* c = new aw_ctx();
+  c->cfg = *cfg;
+  int rc = build_tab(c);
+  if (rc) { delete c; return rc; }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return AW_ERR_CUDA;
+  }
+  if (cfg->cuda_stream) c->stream = (cudaStream_t)cfg->cuda_stream;
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return AW_ERR_CUDA; }
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->hcnt, sizeof(Counters)) != cudaSuccess) { delete c; return AW_ERR_CUDA; }
+  *out = c;
+  return AW_OK;
+}
+
+void aw_destroy(aw_ctx* c) {
+  if (!c) return;
+  free_all(c);
+  if (c->hcnt) cudaFreeHost(c->hcnt);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* aw_last_error(const aw_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri,
+                 const int8_t* bc, const int8_t* shift, const double* period) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (n_nodes < 3 || n_tris < 1 || !xy || !tri || !bc || n_nodes > (1LL << 30) || n_tris > (1LL << 29))
+    return set_err(c, AW_ERR_INVALID_ARG, "bad mesh sizes or null arrays");
+  if ((shift == nullptr) != (period == nullptr)) return set_err(c, AW_ERR_INVALID_ARG, "shift and period go together");
+  free_all(c);
+  HostMesh m;
+  m.ne = (int)n_tris;
+  m.nn = (int)n_nodes;
+  std::vector<double> hxy(2 * n_nodes);
+  m.tri.resize(3 * n_tris);
+  m.bc.resize(3 * n_tris);
+  // accept host or device pointers
+  if (cudaMemcpy(hxy.data(), xy, hxy.size() * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(m.tri.data(), tri, m.tri.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(m.bc.data(), bc, m.bc.size(), cudaMemcpyDefault) != cudaSuccess)
+    return set_err(c, AW_ERR_CUDA, "copying the mesh arrays failed");
+  for (int v : m.tri)
+    if (v < 0 || v >= n_nodes) return set_err(c, AW_ERR_BAD_MESH, "node index out of range");
+  if (period) {
+    m.periodic = true;
+    m.shift.resize(6 * n_tris);
+    if (cudaMemcpy(m.shift.data(), shift, m.shift.size(), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(m.period, period, 2 * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+      return set_err(c, AW_ERR_CUDA, "copying the periodic data failed");
+    if (!(m.period[0] > 0 && m.period[1] > 0)) return set_err(c, AW_ERR_INVALID_ARG, "period must be positive");
+  } else {
+    m.shift.assign(6 * n_tris, 0);
+  }
+  const int ne_s = 2 * c->tab.Mc;
+  int rc = preprocess(c, m, hxy.data(), ne_s, c->tab.M);
+  if (rc) return rc;
+  Dev& d = c->d;
+  d = Dev{};
+  d.ne = m.ne; d.nn = m.nn; d.ned = m.ned; d.periodic = m.periodic;
+  d.period[0] = m.period[0]; d.period[1] = m.period[1];
+  const Tab& T = c->tab;
+  if ((rc = dupload(c, &d.tri, m.tri)) || (rc = dupload(c, &d.cshift, m.cshift)) || (rc = dupload(c, &d.elem_edge, m.elem_edge)) ||
+      (rc = dupload(c, &d.edge_nodes, m.edge_nodes)) || (rc = dupload(c, &d.edge_elem, m.edge_elem)) ||
+      (rc = dupload(c, &d.edge_loc, m.edge_loc)) || (rc = dupload(c, &d.edge_bc, m.edge_bc)) || (rc = dupload(c, &d.nbr, m.nbr)) ||
+      (rc = dupload(c, &d.nbr_shift, m.nbr_shift)) || (rc = dupload(c, &d.v2e_ptr, m.v2e_ptr)) || (rc = dupload(c, &d.v2e, m.v2e)) ||
+      (rc = dupload(c, &d.v2e_loc, m.v2e_loc)) || (rc = dupload(c, &d.node_type, m.node_type)) ||
+      (rc = dupload(c, &d.node_n, m.node_n)) || (rc = dupload(c, &d.sw_ptr, m.sw_ptr)) || (rc = dupload(c, &d.sw, m.sw)) ||
+      (rc = dupload(c, &d.u_ptr, m.u_ptr)) || (rc = dupload(c, &d.u_elem, m.u_elem)) || (rc = dupload(c, &d.u_shift, m.u_shift)) ||
+      (rc = dupload(c, &d.sten, m.sten)) || (rc = dupload(c, &d.sten_ok, m.sten_ok)))
+    return rc;
+  const size_t ne = m.ne, nn = m.nn, ned = m.ned;
+  if ((rc = dalloc(c, &d.Q, 4 * ne)) || (rc = dalloc(c, &d.QM, 4 * ne)) || (rc = dalloc(c, &d.HM, 4 * ne)) ||
+      (rc = dalloc(c, &d.t, ne)) || (rc = dalloc(c, &d.dt, ne)) || (rc = dalloc(c, &d.X, 6 * ne)) ||
+      (rc = dalloc(c, &d.count, ne)) || (rc = dalloc(c, &d.qhat, ne * T.Nst * 4)) ||
+      (rc = dalloc(c, &d.trace, ne * 3 * T.Nt * T.Nt * 4)) || (rc = dalloc(c, &d.avgc, ne * T.Nt * 4)) ||
+      (rc = dalloc(c, &d.vdisp, ne * 3 * 2 * T.Nt)) || (rc = dalloc(c, &d.nX, 2 * nn)) || (rc = dalloc(c, &d.nt, nn)) ||
+      (rc = dalloc(c, &d.nXn, 2 * nn)) || (rc = dalloc(c, &d.ntn, nn)) || (rc = dalloc(c, &d.elem_ready, ne)) ||
+      (rc = dalloc(c, &d.elem_touch, ne)) || (rc = dalloc(c, &d.node_moved, nn)) || (rc = dalloc(c, &d.edge_act, ned)) ||
+      (rc = dalloc(c, &d.ready_list, ne)) || (rc = dalloc(c, &d.moved_list, nn)) || (rc = dalloc(c, &d.active_list, ned)) ||
+      (rc = dalloc(c, &d.touch_list, ne)) || (rc = dalloc(c, &d.G, 4 * ned)) || (rc = dalloc(c, &d.N, 4 * ned)) ||
+      (rc = dalloc(c, &d.w0, ne * T.Mc * 4)) || (rc = dalloc(c, &d.cnt, 1)))
+    return rc;
+  CK(cudaMemsetAsync(d.elem_ready, 0, ne * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.elem_touch, 0, ne * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.node_moved, 0, nn * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.edge_act, 0, ned * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.cnt, 0, sizeof(Counters), c->stream));
+  CK(cudaMemcpyAsync(d.nX, hxy.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->xy0 = hxy;
+  c->ne = m.ne; c->nn = m.nn; c->ned = m.ned; c->sw_total = (long long)m.sw.size();
+  c->have_mesh = true;
+  c->have_state = false;
+  c->failed = false;
+  if ((rc = dalloc(c, &c->d_corner0, 6 * ne))) return rc;
+  CK(cudaMemcpy(c->d_corner0, m.corner0.data(), 6 * ne * sizeof(double), cudaMemcpyHostToDevice));
+  return AW_OK;
+}
+
+int aw_load_state(aw_ctx* c, const double* Q) {
+  if (!c || !Q) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  const size_t ne = c->ne, nn = c->nn;
+  std::vector<double> hQ(4 * ne);
+  CK(cudaMemcpy(hQ.data(), Q, hQ.size() * sizeof(double), cudaMemcpyDefault));
+  const double g = c->tab.gamma;
+  for (size_t i = 0; i < ne; ++i) {
+    const double* q = &hQ[4 * i];
+    double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+    if (!(q[0] > 0) || !(p > 0)) return set_err(c, AW_ERR_NONPHYSICAL, "initial state of element %zu is not physical", i);
+  }
+  Dev& d = c->d;
+  double* corners = c->d_corner0;
+  CK(cudaMemcpyAsync(d.Q, hQ.data(), 4 * ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(d.QM, 0, 4 * ne * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(d.HM, 0, 4 * ne * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(d.t, 0, ne * sizeof(long long), c->stream));
+  CK(cudaMemsetAsync(d.count, 0, ne * sizeof(long long), c->stream));
+  CK(cudaMemcpyAsync(d.X, corners, 6 * ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.nX, c->xy0.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(d.nt, 0, nn * sizeof(long long), c->stream));
+  int rc0 = reset_sweep_state(c);
+  if (rc0) return rc0;
+  launch_initial(c->tab, d, c->nsm, c->stream);
+  CK(cudaGetLastError());
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if ((rc = check_device_error(c))) return rc;
+  c->have_state = true;
+  c->failed = false;
+  return AW_OK;
+}
+
+static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
+  if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  for (int64_t k = 0; k < n; ++k) launch_sweep(c->tab, c->d, c->nsm, c->stream);
+  CK(cudaGetLastError());
+  if (!wait) return AW_OK;
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if ((rc = check_device_error(c))) return rc;
+  if (n_updated) *n_updated = c->hcnt->n_ready;
+  if (c->hcnt->n_ready == 0 && c->hcnt->n_unfinished > 0) {
+    c->failed = true;
+    return set_err(c, AW_ERR_DEADLOCK, "no element satisfies the update criterion (%d unfinished)", c->hcnt->n_unfinished);
+  }
+  return AW_OK;
+}
+
+int aw_lts_sweep(aw_ctx* c, int64_t* n_updated) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  return do_sweeps(c, 1, n_updated, true);
+}
+
+int aw_gts_step(aw_ctx* c, int64_t* n_updated) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "aw_gts_step needs a context created with gts = 1");
+  return do_sweeps(c, 1, n_updated, true);
+}
+
+int aw_advance_to(aw_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done, int64_t* updates_done) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!(t >= c->cfg.t_end))
+    return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to runs to t_end (element times are local; pass t >= t_end)");
+  int64_t sweeps = 0, updates = 0;
+  while (sweeps < max_sweeps) {
+    int64_t n = 0;
+    int rc = do_sweeps(c, 1, &n, true);
+    if (rc) return rc;
+    if (n == 0) break;
+    ++sweeps;
+    updates += n;
+  }
+  if (sweeps_done) *sweeps_done = sweeps;
+  if (updates_done) *updates_done = updates;
+  return AW_OK;
+}
+
+int aw_enqueue_sweeps(aw_ctx* c, int64_t n) {
+  if (!c || n < 0) return AW_ERR_INVALID_ARG;
+  return do_sweeps(c, n, nullptr, false);
+}
+
+int aw_sync(aw_ctx* c, int64_t* updates_since) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if ((rc = check_device_error(c))) return rc;
+  if (updates_since) *updates_since = c->hcnt->updates_since_sync;
+  CK(cudaMemsetAsync(&c->d.cnt->updates_since_sync, 0, sizeof(long long), c->stream));
+  return AW_OK;
+}
+
+int aw_get_state(aw_ctx* c, double* Q, double* t_elem) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  CK(cudaStreamSynchronize(c->stream));
+  if (Q) CK(cudaMemcpy(Q, c->d.Q, 4 * c->ne * sizeof(double), cudaMemcpyDefault));
+  if (t_elem) {
+    std::vector<long long> t(c->ne);
+    CK(cudaMemcpy(t.data(), c->d.t, c->ne * sizeof(long long), cudaMemcpyDeviceToHost));
+    std::vector<double> td(c->ne);
+    for (long long i = 0; i < c->ne; ++i) td[i] = (double)t[i] * c->tab.tick;
+    CK(cudaMemcpy(t_elem, td.data(), c->ne * sizeof(double), cudaMemcpyDefault));
+  }
+  return AW_OK;
+}
+
+int aw_get_nodes(aw_ctx* c, double* xy, double* t_node) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  CK(cudaStreamSynchronize(c->stream));
+  if (xy) CK(cudaMemcpy(xy, c->d.nX, 2 * c->nn * sizeof(double), cudaMemcpyDefault));
+  if (t_node) {
+    std::vector<long long> t(c->nn);
+    CK(cudaMemcpy(t.data(), c->d.nt, c->nn * sizeof(long long), cudaMemcpyDeviceToHost));
+    std::vector<double> td(c->nn);
+    for (long long i = 0; i < c->nn; ++i) td[i] = (double)t[i] * c->tab.tick;
+    CK(cudaMemcpy(t_node, td.data(), c->nn * sizeof(double), cudaMemcpyDefault));
+  }
+  return AW_OK;
+}
+
+int aw_get_update_counts(aw_ctx* c, int64_t* per_elem, int64_t* total) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if (per_elem) CK(cudaMemcpy(per_elem, c->d.count, c->ne * sizeof(long long), cudaMemcpyDefault));
+  if (total) *total = c->hcnt->updates;
+  return AW_OK;
+}
+
+int aw_get_elem_arrays(aw_ctx* c, double* Q, double* QM, double* HM, int64_t* t, int64_t* dt, double* X,
+                       int64_t* count, double* qhat) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  CK(cudaStreamSynchronize(c->stream));
+  const size_t ne = c->ne;
+  if (Q) CK(cudaMemcpy(Q, c->d.Q, 4 * ne * sizeof(double), cudaMemcpyDefault));
+  if (QM) CK(cudaMemcpy(QM, c->d.QM, 4 * ne * sizeof(double), cudaMemcpyDefault));
+  if (HM) CK(cudaMemcpy2D(HM, 3 * sizeof(double), c->d.HM, 4 * sizeof(double), 3 * sizeof(double), ne, cudaMemcpyDefault));
+  if (t) CK(cudaMemcpy(t, c->d.t, ne * sizeof(long long), cudaMemcpyDefault));
+  if (dt) CK(cudaMemcpy(dt, c->d.dt, ne * sizeof(long long), cudaMemcpyDefault));
+  if (X) CK(cudaMemcpy(X, c->d.X, 6 * ne * sizeof(double), cudaMemcpyDefault));
+  if (count) CK(cudaMemcpy(count, c->d.count, ne * sizeof(long long), cudaMemcpyDefault));
+  if (qhat) CK(cudaMemcpy(qhat, c->d.qhat, ne * c->tab.Nst * 4 * sizeof(double), cudaMemcpyDefault));
+  return AW_OK;
+}
+
+int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const double* HM, const int64_t* t,
+                       const int64_t* dt, const double* X, const int64_t* count, const double* qhat) {
+  if (!c || !Q || !QM || !HM || !t || !dt || !X || !count || !qhat) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  const size_t ne = c->ne;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->d.Q, Q, 4 * ne * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.QM, QM, 4 * ne * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemset(c->d.HM, 0, 4 * ne * sizeof(double)));
+  CK(cudaMemcpy2D(c->d.HM, 4 * sizeof(double), HM, 3 * sizeof(double), 3 * sizeof(double), ne, cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.t, t, ne * sizeof(long long), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.dt, dt, ne * sizeof(long long), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.X, X, 6 * ne * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.count, count, ne * sizeof(long long), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.qhat, qhat, ne * c->tab.Nst * 4 * sizeof(double), cudaMemcpyDefault));
+  int rc0 = reset_sweep_state(c);
+  if (rc0) return rc0;
+  launch_products(c->tab, c->d, c->nsm, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_state = true;
+  c->failed = false;
+  return AW_OK;
+}
+
+int aw_get_node_arrays(aw_ctx* c, double* X, int64_t* t) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  CK(cudaStreamSynchronize(c->stream));
+  if (X) CK(cudaMemcpy(X, c->d.nX, 2 * c->nn * sizeof(double), cudaMemcpyDefault));
+  if (t) CK(cudaMemcpy(t, c->d.nt, c->nn * sizeof(long long), cudaMemcpyDefault));
+  return AW_OK;
+}
+
+int aw_set_node_arrays(aw_ctx* c, const double* X, const int64_t* t) {
+  if (!c || !X || !t) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->d.nX, X, 2 * c->nn * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(c->d.nt, t, c->nn * sizeof(long long), cudaMemcpyDefault));
+  return AW_OK;
+}
+
+int aw_diagnostics(aw_ctx* c, double* out) {
+  if (!c || !out) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  double g;
+  std::memcpy(&g, &c->hcnt->gcl_bits, sizeof g);
+  out[0] = g;
+  out[1] = (double)c->hcnt->updates;
+  out[2] = (double)c->hcnt->sweeps;
+  return AW_OK;
+}
+
+int aw_sizes(aw_ctx* c, int64_t* out) {
+  if (!c || !out) return AW_ERR_INVALID_ARG;
+  out[0] = c->ne; out[1] = c->nn; out[2] = c->ned; out[3] = c->tab.Nst; out[4] = c->sw_total;
+  return AW_OK;
+}
+
+int aw_measure_fp64_peak(double* gflops) {
+  if (!gflops) return AW_ERR_INVALID_ARG;
+  double v = measure_fp64_peak();
+  if (!(v > 0)) return AW_ERR_CUDA;
+  *gflops = v;
+  return AW_OK;
+}
+
+}  // extern "C"

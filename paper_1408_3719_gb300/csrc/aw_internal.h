@@ -1,0 +1,123 @@
+// Internal declarations shared by the host driver and the kernels of the
+// GB300 library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace aw {
+
+constexpr int kMaxM = 3;
+constexpr int kMaxMc = 10;   // (M+1)(M+2)/2
+constexpr int kMaxNt = 4;    // M+1 Gauss-Lobatto times
+constexpr int kMaxNU = 9;    // Mc - 1 non-constant basis functions
+constexpr int kMaxNe = 20;   // stencil size n_e = 2 Mc
+constexpr int kNSten = 7;    // central + 3 primary + 3 reverse sectors
+constexpr int kMaxQ = 4;     // points of the reconstruction-average rule
+
+// Reference tables of one order M, built on the host at context creation and
+// passed to kernels by value (uniform reads broadcast from the parameter bank).
+struct Tab {
+  int M, Mc, Nt, Nst, NU, nq;
+  double gamma, cfl, tick;
+  long long T;          // t_end in ticks
+  int eulerian;         // mesh velocity V = 0
+  int gts;              // global time step
+  int nit;              // Picard iterations
+  double lat[kMaxMc][2];
+  int vnode[3];
+  double Dxi[kMaxMc][kMaxMc], Deta[kMaxMc][kMaxMc];
+  double B[kMaxNt - 1][kMaxNt];   // qhat_t = qhat_0 + dt * sum_t' B[t-1][t'] P_t'
+  double Dtau[kMaxNt][kMaxNt];
+  double VtInv[kMaxNt][kMaxNt];   // monomial coefficients in tau from slice values
+  double Tr[3][kMaxNt][kMaxMc];   // Lagrange basis at the Gauss points of each local edge
+  double wavg[kMaxMc];            // reference-triangle average of each Lagrange function
+  double Bnod[kMaxMc][kMaxNU];    // zero-mean centred monomials at the lattice nodes
+  int mexp[kMaxNU][2];
+  double mbar[kMaxNU];
+  double SigU[kMaxNU][kMaxNU];    // upper Cholesky factor: sigma = |SigU c|^2
+  double qb[kMaxQ][3], qw[kMaxQ];
+  double glx[kMaxNt], glw[kMaxNt];
+};
+
+// Device-resident context data (pointers into one context's allocations).
+struct Dev {
+  int ne, nn, ned, periodic;
+  double period[2];
+  // mesh
+  const int* tri;          // [ne*3]
+  const double* cshift;    // [ne*6] corner image offsets (shift * period)
+  const int* elem_edge;    // [ne*3]
+  const int* edge_nodes;   // [ned*2]
+  const int* edge_elem;    // [ned*2]
+  const signed char* edge_loc;  // [ned*2]
+  const signed char* edge_bc;   // [ned]
+  const int* nbr;          // [ne*3]
+  const double* nbr_shift; // [ne*6]
+  const int* v2e_ptr;      // [nn+1]
+  const int* v2e;          // node -> element
+  const signed char* v2e_loc;
+  const signed char* node_type;
+  const double* node_n;    // [nn*2]
+  const int* sw_ptr;       // [ne+1]
+  const int* sw;
+  const int* u_ptr;        // [ne+1] unique stencil members (without i)
+  const int* u_elem;
+  const double* u_shift;   // [2 per entry]
+  const unsigned char* sten;  // [ne][7][n_e] local member index (0 = i itself)
+  const signed char* sten_ok; // [ne*7]
+  // element state
+  double* Q;     // [ne*4]
+  double* QM;    // [ne*4]
+  double* HM;    // [ne*4] (x, y, t, pad)
+  long long* t;  // [ne]
+  long long* dt; // [ne]
+  double* X;     // [ne*6]
+  long long* count;
+  double* qhat;  // [ne*Nst*4]
+  double* trace; // [ne*3*Nt*Nt*4]: per edge, Gauss point, tau monomial, variable
+  double* avgc;  // [ne*Nt*4]: tau monomial coefficients of the reference average
+  double* vdisp; // [ne*3*2*Nt]: coefficients of int_0^tau V_h(vertex) (powers 1..Nt)
+  // nodes
+  double* nX;    // [nn*2]
+  long long* nt; // [nn]
+  double* nXn;   // [nn*2] new positions in the running sweep
+  long long* ntn;
+  // sweep scratch
+  int* elem_ready;   // [ne] epoch stamp when ready
+  int* elem_touch;   // [ne] epoch stamp when adjacent to an active edge
+  int* node_moved;   // [nn] epoch stamp
+  int* edge_act;     // [ned] epoch stamp
+  int* ready_list;   // [ne]
+  int* moved_list;   // [nn]
+  int* active_list;  // [ned]
+  int* touch_list;   // [ne]
+  double* G;         // [ned*4]
+  double* N;         // [ned*4]
+  double* w0;        // [ne*Mc*4] nodal WENO values, by position in the ready list
+  struct Counters* cnt;
+};
+
+struct Counters {
+  int epoch;
+  int n_ready;
+  int n_moved;
+  int n_active;
+  int n_touched;
+  int n_unfinished;
+  int err_code;
+  int err_elem;
+  unsigned long long gcl_bits;   // max GCL residual (non-negative double bits)
+  long long gts_min;
+  long long updates;             // total element updates
+  long long sweeps;
+  long long updates_since_sync;
+};
+
+// kernel launchers (aw_kernels.cu)
+void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+double measure_fp64_peak();
+
+}  // namespace aw

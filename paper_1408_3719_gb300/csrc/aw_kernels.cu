@@ -1,0 +1,878 @@
+// Kernels of one LTS sweep (Sec. 2.6) on sm_103a, all FP64:
+//   k_begin        reset the per-sweep counters, advance the epoch stamp
+//   k_ready        update criterion on S^W (eq. WENOupdate) + compaction of the
+//                  ready elements and of the nodes they move
+//   k_nodes        node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
+//   k_edges        mark edges with a moved endpoint, compact them and the
+//                  elements they touch
+//   k_flux         space-time fluxes through the swept edge surfaces (eqs.
+//                  spacetimenodes, rusanov, STint) and their GCL normals
+//   k_update       one-step FV update / memory variables (eqs. PDEfinal, Qm2, gcl)
+//   k_commit       node positions and times of the moved nodes
+//   k_recon<M>     virtual projection + WENO + local time step (eqs. virtGeom,
+//                  virtCellaverage, intConsRec, weno, timestep)
+//   k_predict<M>   space-time Galerkin predictor (eqs. PDECG, pdef, CGfinal,
+//                  newVertPos) and its derived tables (edge traces, averages,
+//                  vertex displacement polynomials)
+// Work lists are compacted with warp ballots and one atomic per warp; every
+// per-element and per-node sum runs in a fixed order, so results do not
+// depend on the order of the lists.
+#include <cfloat>
+#include <climits>
+#include <cstdio>
+
+#include "aw_internal.h"
+
+namespace aw {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ double area6(const double* X) {
+  return 0.5 * ((X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0]));
+}
+
+// Warp-aggregated append: returns the slot of this lane (if pred) in list.
+__device__ __forceinline__ int warp_append(int* counter, bool pred) {
+  unsigned mask = __ballot_sync(0xffffffffu, pred);
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  int leader = __ffs(mask) - 1;
+  if (mask && lane == leader) base = atomicAdd(counter, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void set_error(Counters* cnt, int code, int elem) {
+  if (atomicCAS(&cnt->err_code, 0, code) == 0) cnt->err_elem = elem;
+}
+
+__device__ __forceinline__ double pressure(const Tab& T, const double* q) {
+  return (T.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_begin(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    Counters* c = d.cnt;
+    c->epoch += 1;
+    c->n_ready = 0;
+    c->n_moved = 0;
+    c->n_active = 0;
+    c->n_touched = 0;
+    c->n_unfinished = 0;
+    c->gts_min = LLONG_MAX;
+    c->sweeps += 1;
+  }
+}
+
+__global__ void k_ready(Tab T, Dev d) {
+  const int epoch = d.cnt->epoch;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < d.ne; base += stride) {
+    int i = base + threadIdx.x;
+    bool unfinished = false, ready = false;
+    long long tn = 0;
+    if (i < d.ne) {
+      long long ti = d.t[i];
+      if (ti < T.T) {
+        unfinished = true;
+        tn = ti + d.dt[i];
+        ready = true;
+        for (int p = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; p < pe; ++p) {
+          int j = d.sw[p];
+          long long tj = d.t[j];
+          if (tj > tn || tn > tj + d.dt[j]) { ready = false; break; }
+        }
+      }
+    }
+    unsigned um = __ballot_sync(0xffffffffu, unfinished);
+    if ((threadIdx.x & 31) == 0 && um) atomicAdd(&d.cnt->n_unfinished, __popc(um));
+    int slot = warp_append(&d.cnt->n_ready, ready);
+    if (ready) {
+      d.ready_list[slot] = i;
+      d.elem_ready[i] = epoch;
+      for (int k = 0; k < 3; ++k) {
+        int n = d.tri[3 * i + k];
+        d.ntn[n] = tn;
+        if (atomicExch(&d.node_moved[n], epoch) != epoch) {
+          int s2 = atomicAdd(&d.cnt->n_moved, 1);
+          d.moved_list[s2] = n;
+        }
+      }
+    }
+  }
+}
+
+template <int M>
+__global__ void k_nodes(Tab T, Dev d) {
+  constexpr int Nt = M + 1;
+  const int n_moved = d.cnt->n_moved;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_moved; q += gridDim.x * blockDim.x) {
+    int n = d.moved_list[q];
+    long long tk0 = d.nt[n], tk1 = d.ntn[n];
+    double num0 = 0.0, num1 = 0.0, den = 0.0;
+    for (int p = d.v2e_ptr[n], pe = d.v2e_ptr[n + 1]; p < pe; ++p) {
+      int j = d.v2e[p];
+      int k = d.v2e_loc[p];
+      double mu = d.Q[4 * j] * area6(d.X + 6 * j);
+      double D0 = 0.0, D1 = 0.0;
+      long long dtj = d.dt[j];
+      if (dtj > 0) {
+        long long tj = d.t[j];
+        double tau0 = (double)(tk0 - tj) / (double)dtj;
+        double tau1 = (double)(tk1 - tj) / (double)dtj;
+        const double* vd = d.vdisp + ((size_t)j * 3 + k) * 2 * Nt;
+        double a0 = vd[Nt - 1], a1 = vd[Nt - 1], b0 = vd[2 * Nt - 1], b1 = vd[2 * Nt - 1];
+#pragma unroll
+        for (int pp = Nt - 2; pp >= 0; --pp) {
+          a0 = a0 * tau0 + vd[pp];
+          a1 = a1 * tau1 + vd[pp];
+          b0 = b0 * tau0 + vd[Nt + pp];
+          b1 = b1 * tau1 + vd[Nt + pp];
+        }
+        double dts = (double)dtj * T.tick;
+        D0 = dts * (a1 * tau1 - a0 * tau0);
+        D1 = dts * (b1 * tau1 - b0 * tau0);
+      }
+      num0 += mu * D0;
+      num1 += mu * D1;
+      den += mu;
+    }
+    double D0 = num0 / den, D1 = num1 / den;
+    int ty = d.node_type[n];
+    if (ty == 1) {
+      double nx = d.node_n[2 * n], ny = d.node_n[2 * n + 1];
+      double dn = D0 * nx + D1 * ny;
+      D0 -= dn * nx;
+      D1 -= dn * ny;
+    } else if (ty == 2) {
+      D0 = D1 = 0.0;
+    }
+    d.nXn[2 * n] = d.nX[2 * n] + D0;
+    d.nXn[2 * n + 1] = d.nX[2 * n + 1] + D1;
+  }
+}
+
+__global__ void k_edges(Dev d) {
+  const int epoch = d.cnt->epoch;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < d.ned; base += stride) {
+    int ed = base + threadIdx.x;
+    bool act = false;
+    if (ed < d.ned) {
+      int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
+      act = d.node_moved[a] == epoch || d.node_moved[b] == epoch;
+    }
+    int slot = warp_append(&d.cnt->n_active, act);
+    if (act) {
+      d.active_list[slot] = ed;
+      d.edge_act[ed] = epoch;
+      for (int q = 0; q < 2; ++q) {
+        int e = d.edge_elem[2 * ed + q];
+        if (e >= 0 && atomicExch(&d.elem_touch[e], epoch) != epoch) {
+          int s2 = atomicAdd(&d.cnt->n_touched, 1);
+          d.touch_list[s2] = e;
+        }
+      }
+    }
+  }
+}
+
+// Rusanov-type ALE flux through the area-weighted space-time normal n
+// (eq. rusanov): the largest |eigenvalue| of A_n^V times |n_xy| is
+// |v.n_xy + n_t| + c |n_xy|.
+__device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const double* qp, const double* n,
+                                        double* F) {
+  double rim = 1.0 / qm[0], rip = 1.0 / qp[0];
+  double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
+  double pm = (T.gamma - 1.0) * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
+  double pp = (T.gamma - 1.0) * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
+  double nxy = sqrt(n[0] * n[0] + n[1] * n[1]);
+  double cm = sqrt(T.gamma * pm * rim), cp = sqrt(T.gamma * pp * rip);
+  double wm = um * n[0] + vm * n[1] + n[2], wp = up * n[0] + vp * n[1] + n[2];
+  double sm = fabs(wm) + cm * nxy, sp = fabs(wp) + cp * nxy;
+  double smax = fmax(sm, sp);
+  // F~.n = f n_x + g n_y + q n_t = q (v.n_xy + n_t) + p (0, n_x, n_y, v.n_xy)
+  double vnm = um * n[0] + vm * n[1], vnp = up * n[0] + vp * n[1];
+  double Fm[4] = {qm[0] * wm, qm[1] * wm + pm * n[0], qm[2] * wm + pm * n[1], qm[3] * wm + pm * vnm};
+  double Fp[4] = {qp[0] * wp, qp[1] * wp + pp * n[0], qp[2] * wp + pp * n[1], qp[3] * wp + pp * vnp};
+#pragma unroll
+  for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) k_flux(Tab T, Dev d) {
+  constexpr int Nt = M + 1;
+  const int epoch = d.cnt->epoch;
+  const int n_active = d.cnt->n_active;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_active; q += gridDim.x * blockDim.x) {
+    int ed = d.active_list[q];
+    int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
+    int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
+    int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
+    bool ma = d.node_moved[a] == epoch, mb = d.node_moved[b] == epoch;
+    double sax = d.cshift[6 * L + 2 * le], say = d.cshift[6 * L + 2 * le + 1];
+    int le1 = le == 2 ? 0 : le + 1;
+    double sbx = d.cshift[6 * L + 2 * le1], sby = d.cshift[6 * L + 2 * le1 + 1];
+    double P[4][3];
+    long long tk[4];
+    P[0][0] = d.nX[2 * a] + sax; P[0][1] = d.nX[2 * a + 1] + say; tk[0] = d.nt[a];
+    P[1][0] = d.nX[2 * b] + sbx; P[1][1] = d.nX[2 * b + 1] + sby; tk[1] = d.nt[b];
+    if (mb) { P[2][0] = d.nXn[2 * b] + sbx; P[2][1] = d.nXn[2 * b + 1] + sby; tk[2] = d.ntn[b]; }
+    else { P[2][0] = P[1][0]; P[2][1] = P[1][1]; tk[2] = tk[1]; }
+    if (ma) { P[3][0] = d.nXn[2 * a] + sax; P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
+    else { P[3][0] = P[0][0]; P[3][1] = P[0][1]; tk[3] = tk[0]; }
+    for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * T.tick;
+    const long long tL = d.t[L], dtL = d.dt[L];
+    const double* trL = d.trace + (((size_t)L * 3 + le) * Nt) * Nt * 4;
+    long long tR = 0, dtR = 0;
+    const double* trR = nullptr;
+    int bc = d.edge_bc[ed];
+    if (R >= 0) {
+      tR = d.t[R];
+      dtR = d.dt[R];
+      trR = d.trace + (((size_t)R * 3 + lr) * Nt) * Nt * 4;
+    }
+    double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
+    for (int gx = 0; gx < Nt; ++gx) {
+      const double chi = T.glx[gx];
+#pragma unroll
+      for (int gt = 0; gt < Nt; ++gt) {
+        const double tau = T.glx[gt], wq = T.glw[gx] * T.glw[gt];
+        double dchi[3], dtau[3], n[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dchi[c] = (1.0 - tau) * (P[1][c] - P[0][c]) + tau * (P[2][c] - P[3][c]);
+          dtau[c] = (1.0 - chi) * (P[3][c] - P[0][c]) + chi * (P[2][c] - P[1][c]);
+        }
+        n[0] = dchi[1] * dtau[2] - dchi[2] * dtau[1];
+        n[1] = dchi[2] * dtau[0] - dchi[0] * dtau[2];
+        n[2] = dchi[0] * dtau[1] - dchi[1] * dtau[0];
+        double tt = (1 - chi) * (1 - tau) * (double)tk[0] + chi * (1 - tau) * (double)tk[1] +
+                    chi * tau * (double)tk[2] + (1 - chi) * tau * (double)tk[3];
+        double qm[4], qp[4];
+        {
+          double tl = dtL > 0 ? (tt - (double)tL) / (double)dtL : 0.0;
+          const double* c0 = trL + (size_t)gx * Nt * 4;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            double acc = c0[(Nt - 1) * 4 + v];
+#pragma unroll
+            for (int p = Nt - 2; p >= 0; --p) acc = acc * tl + c0[p * 4 + v];
+            qm[v] = acc;
+          }
+        }
+        if (R >= 0) {
+          double tr = dtR > 0 ? (tt - (double)tR) / (double)dtR : 0.0;
+          const double* c0 = trR + (size_t)(Nt - 1 - gx) * Nt * 4;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            double acc = c0[(Nt - 1) * 4 + v];
+#pragma unroll
+            for (int p = Nt - 2; p >= 0; --p) acc = acc * tr + c0[p * 4 + v];
+            qp[v] = acc;
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) qp[v] = qm[v];
+          if (bc == 0) {
+            double nn = n[0] * n[0] + n[1] * n[1];
+            if (nn > 0.0) {
+              double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+              qp[1] = qm[1] - 2.0 * mn * n[0];
+              qp[2] = qm[2] - 2.0 * mn * n[1];
+            }
+          }
+        }
+        double F[4];
+        rusanov(T, qm, qp, n, F);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) G[v] += wq * F[v];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Nn[c] += wq * n[c];
+      }
+    }
+    double* g = d.G + 4 * (size_t)ed;
+    double* nn = d.N + 4 * (size_t)ed;
+    g[0] = G[0]; g[1] = G[1]; g[2] = G[2]; g[3] = G[3];
+    nn[0] = Nn[0]; nn[1] = Nn[1]; nn[2] = Nn[2];
+  }
+}
+
+__global__ void k_update(Tab T, Dev d) {
+  const int epoch = d.cnt->epoch;
+  const int n_touched = d.cnt->n_touched;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n_touched; base += stride) {
+    int q = base + threadIdx.x;
+    bool upd = false;
+    if (q < n_touched) {
+      int i = d.touch_list[q];
+      bool ready = d.elem_ready[i] == epoch;
+      double sg[3];
+      int eds[3];
+      bool act[3];
+      for (int e = 0; e < 3; ++e) {
+        int ed = d.elem_edge[3 * i + e];
+        eds[e] = ed;
+        act[e] = d.edge_act[ed] == epoch;
+        sg[e] = d.edge_elem[2 * ed] == i ? 1.0 : -1.0;
+      }
+      if (ready) {
+        upd = true;
+        double Xn[6];
+        for (int k = 0; k < 3; ++k) {
+          int n = d.tri[3 * i + k];
+          Xn[2 * k] = d.nXn[2 * n] + d.cshift[6 * i + 2 * k];
+          Xn[2 * k + 1] = d.nXn[2 * n + 1] + d.cshift[6 * i + 2 * k + 1];
+        }
+        double Aold = area6(d.X + 6 * i), Anew = area6(Xn);
+        double Qn[4];
+        for (int v = 0; v < 4; ++v) {
+          double acc = Aold * d.Q[4 * i + v];
+          for (int e = 0; e < 3; ++e)
+            if (act[e]) acc -= sg[e] * d.G[4 * (size_t)eds[e] + v];
+          acc += d.QM[4 * i + v];
+          Qn[v] = acc / Anew;
+          d.Q[4 * i + v] = Qn[v];
+          d.QM[4 * i + v] = 0.0;
+        }
+        double res[3];
+        for (int c = 0; c < 3; ++c) {
+          double acc = 0.0;
+          for (int e = 0; e < 3; ++e)
+            if (act[e]) acc += sg[e] * d.N[4 * (size_t)eds[e] + c];
+          res[c] = acc - d.HM[4 * i + c];
+          d.HM[4 * i + c] = 0.0;
+        }
+        res[2] += Anew - Aold;
+        double r = fmax(fabs(res[0]), fmax(fabs(res[1]), fabs(res[2]))) / Aold;
+        atomicMax(&d.cnt->gcl_bits, (unsigned long long)__double_as_longlong(r));
+        for (int k = 0; k < 6; ++k) d.X[6 * i + k] = Xn[k];
+        d.t[i] += d.dt[i];
+        d.count[i] += 1;
+        if (!(Qn[0] > 0.0) || !(pressure(T, Qn) > 0.0) || !(Anew > 0.0)) set_error(d.cnt, -3, i);
+      } else {
+        for (int e = 0; e < 3; ++e) {
+          if (!act[e]) continue;
+          for (int v = 0; v < 4; ++v) d.QM[4 * i + v] -= sg[e] * d.G[4 * (size_t)eds[e] + v];
+          for (int c = 0; c < 3; ++c) d.HM[4 * i + c] -= sg[e] * d.N[4 * (size_t)eds[e] + c];
+        }
+      }
+    }
+    unsigned um = __ballot_sync(0xffffffffu, upd);
+    if ((threadIdx.x & 31) == 0 && um) {
+      atomicAdd((unsigned long long*)&d.cnt->updates, (unsigned long long)__popc(um));
+      atomicAdd((unsigned long long*)&d.cnt->updates_since_sync, (unsigned long long)__popc(um));
+    }
+  }
+}
+
+__global__ void k_commit(Dev d) {
+  const int n_moved = d.cnt->n_moved;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_moved; q += gridDim.x * blockDim.x) {
+    int n = d.moved_list[q];
+    d.nX[2 * n] = d.nXn[2 * n];
+    d.nX[2 * n + 1] = d.nXn[2 * n + 1];
+    d.nt[n] = d.ntn[n];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// virtual data of element j at time ti (ticks): eqs. virtGeom, virtCellaverage
+template <int M>
+__device__ __forceinline__ void virtual_data(const Tab& T, const Dev& d, int j, long long ti, double* Xv, double* Qv) {
+  constexpr int Nt = M + 1;
+  const long long tj = d.t[j], dtj = d.dt[j];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Xv[k] = d.X[6 * j + k];
+  if (tj == ti || dtj == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Qv[v] = d.Q[4 * j + v];
+    return;
+  }
+  const double tau = (double)(ti - tj) / (double)dtj;
+  const double dts = (double)dtj * T.tick;
+  const double* vd = d.vdisp + (size_t)j * 6 * Nt;
+#pragma unroll
+  for (int kc = 0; kc < 6; ++kc) {
+    const double* c0 = vd + kc * Nt;
+    double acc = c0[Nt - 1];
+#pragma unroll
+    for (int p = Nt - 2; p >= 0; --p) acc = acc * tau + c0[p];
+    Xv[kc] += dts * (acc * tau);
+  }
+  const double* av = d.avgc + (size_t)j * Nt * 4;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double acc = av[(Nt - 1) * 4 + v];
+#pragma unroll
+    for (int p = Nt - 2; p >= 0; --p) acc = acc * tau + av[p * 4 + v];
+    Qv[v] = acc;
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void centred_monomials(const Tab& T, double x, double y, double* m) {
+  // graded order: degree 1: x, y; degree 2: x^2, xy, y^2; degree 3: x^3, x^2 y, x y^2, y^3
+  m[0] = x;
+  m[1] = y;
+  if (M >= 2) { m[2] = x * x; m[3] = x * y; m[4] = y * y; }
+  if (M >= 3) { m[5] = m[2] * x; m[6] = m[2] * y; m[7] = m[4] * x; m[8] = m[4] * y; }
+}
+
+template <int M>
+__global__ void __launch_bounds__(64) k_recon(Tab T, Dev d, int initial) {
+  constexpr int Mc = (M + 1) * (M + 2) / 2, NU = Mc - 1, NE = 2 * Mc;
+  constexpr int MaxU = kNSten * (NE - 1);
+  const int n_ready = initial ? d.ne : d.cnt->n_ready;
+  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < n_ready; pos += gridDim.x * blockDim.x) {
+    const int i = initial ? pos : d.ready_list[pos];
+    const long long ti = d.t[i];
+    double Xi[6], Qi[4];
+    for (int k = 0; k < 6; ++k) Xi[k] = d.X[6 * i + k];
+    for (int v = 0; v < 4; ++v) Qi[v] = d.Q[4 * i + v];
+    const double ja = Xi[2] - Xi[0], jb = Xi[4] - Xi[0], jc = Xi[3] - Xi[1], jd = Xi[5] - Xi[1];
+    const double idet = 1.0 / (ja * jd - jb * jc);
+    const double j00 = jd * idet, j01 = -jb * idet, j10 = -jc * idet, j11 = ja * idet;
+    const int u0 = d.u_ptr[i], nU = d.u_ptr[i + 1] - u0;
+    double A[MaxU + 1][NU];
+    double r[MaxU + 1][4];
+    for (int u = 1; u <= nU && u <= MaxU; ++u) {
+      const int j = d.u_elem[u0 + u - 1];
+      double Xv[6], Qv[4];
+      virtual_data<M>(T, d, j, ti, Xv, Qv);
+      const double sx = d.u_shift[2 * (u0 + u - 1)], sy = d.u_shift[2 * (u0 + u - 1) + 1];
+      double xr[3], yr[3];
+      for (int k = 0; k < 3; ++k) {
+        double px = Xv[2 * k] + sx - Xi[0], py = Xv[2 * k + 1] + sy - Xi[1];
+        xr[k] = j00 * px + j01 * py - (1.0 / 3.0);
+        yr[k] = j10 * px + j11 * py - (1.0 / 3.0);
+      }
+      double row[NU];
+      for (int l = 0; l < NU; ++l) row[l] = 0.0;
+      for (int qq = 0; qq < T.nq; ++qq) {
+        double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
+        double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
+        double m[kMaxNU];
+        centred_monomials<M>(T, x, y, m);
+        for (int l = 0; l < NU; ++l) row[l] += T.qw[qq] * m[l];
+      }
+      for (int l = 0; l < NU; ++l) A[u][l] = row[l] - T.mbar[l];
+      for (int v = 0; v < 4; ++v) r[u][v] = Qv[v] - Qi[v];
+    }
+    // constrained least squares per stencil through the normal equations
+    double cs[kNSten][NU][4];
+    bool ok[kNSten];
+    const unsigned char* st = d.sten + (size_t)i * kNSten * NE;
+    for (int s = 0; s < kNSten; ++s) {
+      ok[s] = d.sten_ok[i * kNSten + s] != 0;
+      if (!ok[s]) continue;
+      double Nm[NU][NU], Rh[NU][4];
+      for (int a = 0; a < NU; ++a) {
+        for (int b = 0; b < NU; ++b) Nm[a][b] = 0.0;
+        for (int v = 0; v < 4; ++v) Rh[a][v] = 0.0;
+      }
+      for (int m = 1; m < NE; ++m) {
+        int u = st[s * NE + m];
+        for (int a = 0; a < NU; ++a) {
+          double au = A[u][a];
+          for (int b = 0; b <= a; ++b) Nm[a][b] += au * A[u][b];
+          for (int v = 0; v < 4; ++v) Rh[a][v] += au * r[u][v];
+        }
+      }
+      // Cholesky N = L L^T (lower, in place)
+      for (int a = 0; a < NU; ++a) {
+        double dd = Nm[a][a];
+        for (int k = 0; k < a; ++k) dd -= Nm[a][k] * Nm[a][k];
+        double la = sqrt(dd), il = 1.0 / la;
+        Nm[a][a] = la;
+        for (int b = a + 1; b < NU; ++b) {
+          double v = Nm[b][a];
+          for (int k = 0; k < a; ++k) v -= Nm[b][k] * Nm[a][k];
+          Nm[b][a] = v * il;
+        }
+      }
+      for (int v = 0; v < 4; ++v) {
+        double y[NU];
+        for (int a = 0; a < NU; ++a) {
+          double acc = Rh[a][v];
+          for (int k = 0; k < a; ++k) acc -= Nm[a][k] * y[k];
+          y[a] = acc / Nm[a][a];
+        }
+        for (int a = NU - 1; a >= 0; --a) {
+          double acc = y[a];
+          for (int k = a + 1; k < NU; ++k) acc -= Nm[k][a] * cs[s][k][v];
+          cs[s][a][v] = acc / Nm[a][a];
+        }
+      }
+    }
+    // characteristic fields of dF/dQ.n, n along the density gradient of the
+    // central-stencil polynomial at the centroid (the linear coefficients)
+    double gx = cs[0][0][0] * j00 + cs[0][1][0] * j10;
+    double gy = cs[0][0][0] * j01 + cs[0][1][0] * j11;
+    double gn = sqrt(gx * gx + gy * gy);
+    double nx = 1.0, ny = 0.0;
+    if (gn > 0.0) { nx = gx / gn; ny = gy / gn; }
+    double Rm[4][4], Lm[4][4];
+    {
+      const double g = T.gamma, rho = Qi[0], u = Qi[1] / rho, v = Qi[2] / rho;
+      const double p = (g - 1.0) * (Qi[3] - 0.5 * rho * (u * u + v * v));
+      const double a = sqrt(g * p / rho), H = (Qi[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
+      const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
+      Rm[0][0] = 1; Rm[0][1] = 1; Rm[0][2] = 0; Rm[0][3] = 1;
+      Rm[1][0] = u - a * nx; Rm[1][1] = u; Rm[1][2] = -ny; Rm[1][3] = u + a * nx;
+      Rm[2][0] = v - a * ny; Rm[2][1] = v; Rm[2][2] = nx; Rm[2][3] = v + a * ny;
+      Rm[3][0] = H - a * un; Rm[3][1] = q2; Rm[3][2] = ut; Rm[3][3] = H + a * un;
+      Lm[0][0] = 0.5 * (b2 + un * ia); Lm[0][1] = -0.5 * (b1 * u + nx * ia); Lm[0][2] = -0.5 * (b1 * v + ny * ia); Lm[0][3] = 0.5 * b1;
+      Lm[1][0] = 1.0 - b2; Lm[1][1] = b1 * u; Lm[1][2] = b1 * v; Lm[1][3] = -b1;
+      Lm[2][0] = -ut; Lm[2][1] = -ny; Lm[2][2] = nx; Lm[2][3] = 0.0;
+      Lm[3][0] = 0.5 * (b2 - un * ia); Lm[3][1] = -0.5 * (b1 * u - nx * ia); Lm[3][2] = -0.5 * (b1 * v - ny * ia); Lm[3][3] = 0.5 * b1;
+    }
+    double sig[kNSten][4];
+    for (int s = 0; s < kNSten; ++s) {
+      if (!ok[s]) continue;
+      for (int l = 0; l < NU; ++l) {
+        double cc[4];
+        for (int rr = 0; rr < 4; ++rr)
+          cc[rr] = Lm[rr][0] * cs[s][l][0] + Lm[rr][1] * cs[s][l][1] + Lm[rr][2] * cs[s][l][2] + Lm[rr][3] * cs[s][l][3];
+        for (int rr = 0; rr < 4; ++rr) cs[s][l][rr] = cc[rr];
+      }
+      for (int rr = 0; rr < 4; ++rr) {
+        double sg = 0.0;
+        for (int a = 0; a < NU; ++a) {
+          double acc = 0.0;
+          for (int b = a; b < NU; ++b) acc += T.SigU[a][b] * cs[s][b][rr];
+          sg += acc * acc;
+        }
+        sig[s][rr] = sg;
+      }
+    }
+    double wc[NU][4];
+    for (int rr = 0; rr < 4; ++rr) {
+      double om[kNSten], tot = 0.0;
+      for (int s = 0; s < kNSten; ++s) {
+        om[s] = 0.0;
+        if (!ok[s]) continue;
+        double e1 = sig[s][rr] + 1e-14;
+        double e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
+        om[s] = (s == 0 ? 1e5 : 1.0) / e8;
+        tot += om[s];
+      }
+      double itot = 1.0 / tot;
+      for (int l = 0; l < NU; ++l) {
+        double acc = 0.0;
+        for (int s = 0; s < kNSten; ++s)
+          if (ok[s]) acc += (om[s] * itot) * cs[s][l][rr];
+        wc[l][rr] = acc;
+      }
+    }
+    double* w0 = d.w0 + (size_t)pos * Mc * 4;
+    double cv[NU][4];
+    for (int l = 0; l < NU; ++l)
+      for (int v = 0; v < 4; ++v)
+        cv[l][v] = Rm[v][0] * wc[l][0] + Rm[v][1] * wc[l][1] + Rm[v][2] * wc[l][2] + Rm[v][3] * wc[l][3];
+    for (int s = 0; s < Mc; ++s)
+      for (int v = 0; v < 4; ++v) {
+        double acc = Qi[v];
+        for (int l = 0; l < NU; ++l) acc += T.Bnod[s][l] * cv[l][v];
+        w0[s * 4 + v] = acc;
+      }
+    // local time step (eq. timestep) on the virtual element and its neighbours
+    long long tks = 0;
+    if (ti < T.T) {
+      double best = DBL_MAX;
+      for (int e = -1; e < 3; ++e) {
+        int j = e < 0 ? i : d.nbr[3 * i + e];
+        if (j < 0) continue;
+        double Xv[6], Qv[4];
+        virtual_data<M>(T, d, j, ti, Xv, Qv);
+        double ar = area6(Xv), per = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          int k1 = k == 2 ? 0 : k + 1;
+          double dx = Xv[2 * k1] - Xv[2 * k], dy = Xv[2 * k1 + 1] - Xv[2 * k + 1];
+          per += sqrt(dx * dx + dy * dy);
+        }
+        double dd = 4.0 * ar / per;
+        double uu = Qv[1] / Qv[0], vv = Qv[2] / Qv[0];
+        double lam = sqrt(uu * uu + vv * vv) + sqrt(T.gamma * pressure(T, Qv) / Qv[0]);
+        double dtc = T.cfl * dd / lam;
+        best = fmin(best, dtc);
+      }
+      if (!(best > 0.0)) {
+        set_error(d.cnt, -3, i);
+        best = T.tick;
+      }
+      double rt = floor(best / T.tick);
+      tks = rt > (double)(T.T - ti) ? T.T - ti : (long long)rt;
+      if (tks < 1) tks = 1;
+      atomicMin(&d.cnt->gts_min, tks);
+    }
+    d.dt[i] = tks;
+  }
+}
+
+// predictor-derived tables of element i from qh[Nt][Mc][4]
+template <int M>
+__device__ __forceinline__ void write_products(const Tab& T, const Dev& d, int i, const double (*qh)[(M + 1) * (M + 2) / 2][4]) {
+  constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1;
+  double* tr = d.trace + (size_t)i * 3 * Nt * Nt * 4;
+  for (int e = 0; e < 3; ++e)
+    for (int g = 0; g < Nt; ++g) {
+      double val[Nt][4];
+      for (int t = 0; t < Nt; ++t)
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+          for (int s = 0; s < Mc; ++s) acc += T.Tr[e][g][s] * qh[t][s][v];
+          val[t][v] = acc;
+        }
+      for (int p = 0; p < Nt; ++p)
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+          for (int t = 0; t < Nt; ++t) acc += T.VtInv[p][t] * val[t][v];
+          tr[((e * Nt + g) * Nt + p) * 4 + v] = acc;
+        }
+    }
+  double* av = d.avgc + (size_t)i * Nt * 4;
+  {
+    double val[Nt][4];
+    for (int t = 0; t < Nt; ++t)
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int s = 0; s < Mc; ++s) acc += T.wavg[s] * qh[t][s][v];
+        val[t][v] = acc;
+      }
+    for (int p = 0; p < Nt; ++p)
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int t = 0; t < Nt; ++t) acc += T.VtInv[p][t] * val[t][v];
+        av[p * 4 + v] = acc;
+      }
+  }
+  double* vd = d.vdisp + (size_t)i * 6 * Nt;
+  for (int k = 0; k < 3; ++k) {
+    const int s = T.vnode[k];
+    double vel[Nt][2];
+    for (int t = 0; t < Nt; ++t) {
+      double ir = 1.0 / qh[t][s][0];
+      vel[t][0] = T.eulerian ? 0.0 : qh[t][s][1] * ir;
+      vel[t][1] = T.eulerian ? 0.0 : qh[t][s][2] * ir;
+    }
+    for (int c = 0; c < 2; ++c)
+      for (int p = 0; p < Nt; ++p) {
+        double acc = 0.0;
+        for (int t = 0; t < Nt; ++t) acc += T.VtInv[p][t] * vel[t][c];
+        vd[(k * 2 + c) * Nt + p] = acc / (p + 1);
+      }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(64) k_predict(Tab T, Dev d, int initial, int gts) {
+  constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1;
+  const int n_ready = initial ? d.ne : d.cnt->n_ready;
+  const long long gmin = d.cnt->gts_min;
+  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < n_ready; pos += gridDim.x * blockDim.x) {
+    const int i = initial ? pos : d.ready_list[pos];
+    long long dtk = d.dt[i];
+    if (gts && dtk > 0) {
+      dtk = gmin;
+      d.dt[i] = dtk;
+    }
+    const double dts = (double)dtk * T.tick;
+    const double* w0 = d.w0 + (size_t)pos * Mc * 4;
+    double X[6];
+    for (int k = 0; k < 6; ++k) X[k] = d.X[6 * i + k];
+    double q[Nt][Mc][4], xh[Nt][Mc][2], q0[Mc][4], x0[Mc][2];
+    for (int s = 0; s < Mc; ++s) {
+      x0[s][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
+      x0[s][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
+      for (int v = 0; v < 4; ++v) q0[s][v] = w0[s * 4 + v];
+    }
+    for (int t = 0; t < Nt; ++t)
+      for (int s = 0; s < Mc; ++s) {
+        for (int v = 0; v < 4; ++v) q[t][s][v] = q0[s][v];
+        xh[t][s][0] = x0[s][0];
+        xh[t][s][1] = x0[s][1];
+      }
+    if (dts > 0.0) {
+      const double idt = 1.0 / dts;
+      for (int it = 0; it < T.nit; ++it) {
+        double P[Nt][Mc][4], V[Nt][Mc][2];
+        for (int t = 0; t < Nt; ++t) {
+          double f[Mc][4], g[Mc][4];
+          for (int s = 0; s < Mc; ++s) {
+            const double* qq = q[t][s];
+            double ir = 1.0 / qq[0], u = qq[1] * ir, v = qq[2] * ir;
+            double p = (T.gamma - 1.0) * (qq[3] - 0.5 * (qq[1] * u + qq[2] * v));
+            f[s][0] = qq[1]; f[s][1] = qq[1] * u + p; f[s][2] = qq[1] * v; f[s][3] = u * (qq[3] + p);
+            g[s][0] = qq[2]; g[s][1] = qq[2] * u; g[s][2] = qq[2] * v + p; g[s][3] = v * (qq[3] + p);
+            V[t][s][0] = T.eulerian ? 0.0 : u;
+            V[t][s][1] = T.eulerian ? 0.0 : v;
+          }
+          for (int s = 0; s < Mc; ++s) {
+            double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
+            double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
+            double xx = 0, xe = 0, yx = 0, ye = 0;
+            for (int r = 0; r < Mc; ++r) {
+              const double a = T.Dxi[s][r], b = T.Deta[s][r];
+              for (int v = 0; v < 4; ++v) {
+                Qx[v] += a * q[t][r][v]; Qe[v] += b * q[t][r][v];
+                fx[v] += a * f[r][v]; fe[v] += b * f[r][v];
+                gx[v] += a * g[r][v]; ge[v] += b * g[r][v];
+              }
+              xx += a * xh[t][r][0]; xe += b * xh[t][r][0];
+              yx += a * xh[t][r][1]; ye += b * xh[t][r][1];
+            }
+            double xt = 0.0, yt = 0.0;
+            for (int u = 0; u < Nt; ++u) { xt += T.Dtau[t][u] * xh[u][s][0]; yt += T.Dtau[t][u] * xh[u][s][1]; }
+            xt *= idt;
+            yt *= idt;
+            const double idet = 1.0 / (xx * ye - xe * yx);
+            const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+            const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
+            for (int v = 0; v < 4; ++v)
+              P[t][s][v] = -(Qx[v] * xit + Qe[v] * ett + fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
+          }
+        }
+        for (int t = 1; t < Nt; ++t)
+          for (int s = 0; s < Mc; ++s) {
+            for (int v = 0; v < 4; ++v) {
+              double acc = 0.0;
+              for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * P[u][s][v];
+              q[t][s][v] = q0[s][v] + dts * acc;
+            }
+            for (int c = 0; c < 2; ++c) {
+              double acc = 0.0;
+              for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * V[u][s][c];
+              xh[t][s][c] = x0[s][c] + dts * acc;
+            }
+          }
+      }
+    }
+    double* out = d.qhat + (size_t)i * Mc * Nt * 4;
+    for (int t = 0; t < Nt; ++t)
+      for (int s = 0; s < Mc; ++s)
+        for (int v = 0; v < 4; ++v) out[(t * Mc + s) * 4 + v] = q[t][s][v];
+    write_products<M>(T, d, i, q);
+  }
+}
+
+template <int M>
+__global__ void k_products(Tab T, Dev d) {
+  constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ne; i += gridDim.x * blockDim.x) {
+    double q[Nt][Mc][4];
+    const double* in = d.qhat + (size_t)i * Mc * Nt * 4;
+    for (int t = 0; t < Nt; ++t)
+      for (int s = 0; s < Mc; ++s)
+        for (int v = 0; v < 4; ++v) q[t][s][v] = in[(t * Mc + s) * 4 + v];
+    write_products<M>(T, d, i, q);
+  }
+}
+
+__global__ void k_fill_counters_initial(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    d.cnt->gts_min = LLONG_MAX;
+    d.cnt->err_code = 0;
+  }
+}
+
+template <int M>
+void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
+  const int grid_all_ed = (d.ned + kBlock - 1) / kBlock;
+  const int grid_w = nsm * 8;
+  k_begin<<<1, 32, 0, s>>>(d);
+  k_ready<<<grid_all_e, kBlock, 0, s>>>(T, d);
+  k_nodes<M><<<grid_w, kBlock, 0, s>>>(T, d);
+  k_edges<<<grid_all_ed, kBlock, 0, s>>>(d);
+  k_flux<M><<<grid_w, kBlock, 0, s>>>(T, d);
+  k_update<<<grid_w, kBlock, 0, s>>>(T, d);
+  k_commit<<<grid_w, kBlock, 0, s>>>(d);
+  k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 0);
+  k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 0, T.gts);
+}
+
+template <int M>
+void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  k_fill_counters_initial<<<1, 32, 0, s>>>(d);
+  k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 1);
+  k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 1, T.gts);
+}
+
+__global__ void k_dfma_chain(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  switch (T.M) {
+    case 1: sweep_impl<1>(T, d, nsm, s); break;
+    case 2: sweep_impl<2>(T, d, nsm, s); break;
+    default: sweep_impl<3>(T, d, nsm, s); break;
+  }
+}
+
+void launch_initial(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  switch (T.M) {
+    case 1: initial_impl<1>(T, d, nsm, s); break;
+    case 2: initial_impl<2>(T, d, nsm, s); break;
+    default: initial_impl<3>(T, d, nsm, s); break;
+  }
+}
+
+void launch_products(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  switch (T.M) {
+    case 1: k_products<1><<<nsm * 4, 64, 0, s>>>(T, d); break;
+    case 2: k_products<2><<<nsm * 4, 64, 0, s>>>(T, d); break;
+    default: k_products<3><<<nsm * 4, 64, 0, s>>>(T, d); break;
+  }
+}
+
+// Dependent DFMA chains (8 per thread) over 4 x 256 threads per SM.
+double measure_fp64_peak() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  const int blocks = nsm * 4, threads = 256, iters = 8192;
+  double* out = nullptr;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return -1;
+  if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) { cudaStreamDestroy(s); return -1; }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    k_dfma_chain<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  bool ok = cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  cudaStreamDestroy(s);
+  if (!ok) return -1;
+  return 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e9;
+}
+
+}  // namespace aw
