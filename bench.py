@@ -1,0 +1,313 @@
+"""Benchmark: FP64 element updates per second of the LTS ALE ADER-WENO sweep.
+
+One step = one LTS sweep (update criterion, node motion, space-time fluxes,
+FV update, projection + WENO + time step, predictor) over the resident
+state.  Default workload: the cylindrical explosion (EP1 data: rho, p = 1, 1
+inside r < 0.5, 0.125, 0.1 outside) on a ~500k-triangle disc graded 10x from
+centre to rim, P3 scheme (fourth order), local time stepping.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--order 3] [--hc 0.00114]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload on its
+GPU (the mesh is not partitioned); rank 0 prints one JSON line with the
+aggregate rate over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 element-updates/s, LTS P3: plain vs batched vs adjoint; % HBM roofline"
+UNIT = "element-updates/s"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FP64 operation counts per element update (one flop per add,
+# multiply, divide or square root; an FMA counts two), from the operation
+# counts of the predictor (Sec. 2.3) and the reconstruction (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+def predictor_flops(M: int) -> float:
+    Mc, Nt = (M + 1) * (M + 2) // 2, M + 1
+    nit = M + 1
+    per_node = (2 * 2 * Mc * 14      # d/dxi, d/deta of q (4), f (4), g (4), x (2)
+                + 2 * 2 * Nt         # d/dtau of the two coordinates
+                + 2 + 18             # 1/rho, velocity, pressure, fluxes f and g
+                + 16                 # inverse metric (one division) and xi_t, eta_t
+                + 4 * 6 * 2          # P = -(Q_xi xi_t + ... + g_eta eta_y)
+                + 6 * Nt * 2 * M / Nt)  # Picard update of q (4) and x (2) on the tau > 0 slices
+    products = 3 * Nt * Nt * 4 * 2 * (Mc + Nt) + Nt * 4 * 2 * (Mc + Nt) + 3 * Nt * (1 + 2 * 2 * Nt)
+    return per_node * Mc * Nt * nit + products
+
+
+def recon_flops(M: int, members: float) -> float:
+    Mc, Nt = (M + 1) * (M + 2) // 2, M + 1
+    NU, NE = Mc - 1, 2 * Mc
+    nq = {1: 1, 2: 3, 3: 4}[M]
+    per_member = (6 * 2 * Nt + 4 * 2 * (Nt - 1) + 4   # virtual vertices and average (Horner)
+                  + 3 * 8                              # map to the reference frame of T_i
+                  + nq * (4 + max(NU - 2, 0) + 2 * NU) + NU + 4)
+    per_stencil = ((NE - 1) * (NU * (NU + 1) + 8 * NU)  # normal equations
+                   + NU ** 3 / 3 + 2 * NU               # Cholesky
+                   + 4 * 2 * NU * NU                    # two triangular solves, 4 right-hand sides
+                   + NU * 32                            # characteristic projection
+                   + 4 * (NU * (NU + 1) + NU))          # smoothness indicators
+    weights = 4 * (7 * 8 + NU * 7 * 2) + NU * 32 + Mc * 4 * NU * 2
+    dt = 4 * 60
+    return members * per_member + 7 * per_stencil + weights + dt
+
+
+def flux_flops(M: int) -> float:
+    Nt = M + 1
+    per_point = 30 + 2 * 4 * 2 * (Nt - 1) + 6 + 2 * 25 + 25 + 4 * 4
+    return Nt * Nt * per_point
+
+
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(order: int, hc: float):
+    from paper_1408_3719_gb300 import workloads as W
+    mesh, Q = W.explosion(hc)
+    return mesh, Q, dict(order_M=order, t_end=0.25, time_quantum_log2=20)
+
+
+def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = None):
+    """The oracle on a bounded sample: the same generator and scheme on a
+    ~26k-triangle disc; setup untimed; sweeps timed until `seconds` elapse
+    (or `steps` sweeps)."""
+    from oracle.pyoracle import Oracle
+    from paper_1408_3719_gb300 import workloads as W
+    mesh, Q = W.explosion(0.005)
+    o = Oracle(order_M=order, t_end=0.25)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    for _ in range(warmup):
+        o.sweep()
+    ups, sweeps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        ups += o.sweep()
+        sweeps += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and sweeps >= steps) or (steps is None and el >= seconds):
+            break
+    return ups / el, dict(sweeps=sweeps, updates=ups, seconds=el, n_tris=int(mesh["tri"].shape[0]))
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    rate, info = cpu_sample(args.order, 0, warmup=args.warmup, steps=args.steps)
+    sample = (f"oracle (plain serial C, FP64) on a {info['n_tris']}-triangle graded disc, same EP1 data and "
+              f"P{args.order} LTS scheme; {info['sweeps']} timed sweeps ({info['updates']} updates) after "
+              f"{args.warmup} warm-up sweeps; pre-processing untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * info["seconds"] / info["sweeps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"explosion EP1 disc sample, P{args.order} LTS",
+                                            "n_tris": info["n_tris"]},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1408_3719_gb300 import aleweno
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    aleweno.load()
+    mesh, Q, cfg = workload(args.order, args.hc)
+    n_tris = int(mesh["tri"].shape[0])
+    # a dedicated (non-default) stream: the library launches on it and the
+    # CUDA events below are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = aleweno.Solver(**cfg, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    s.load_mesh(mesh)
+    t_mesh = time.perf_counter() - t0
+    s.load_state(Q)
+    sizes = s.sizes()
+    peak_gflops = aleweno.fp64_peak_gflops()
+    for _ in range(args.warmup):
+        s.sweep()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
+    s.sync()
+    s.profile(True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        s.enqueue(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    updates = s.sync()
+    kms, ksweeps = s.profile_read()
+    s.profile(False)
+    tot = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, updates_all = float(mx[0]), float(sm[1])
+    else:
+        ms_max, updates_all = ms, float(updates)
+    value = updates_all / (ms_max * 1e-3)
+
+    # dominant kernel and its roofline (FP64 pipe: this path is ALU-bound)
+    dom = max(kms, key=kms.get)
+    members = sizes["u_entries"] / max(sizes["n_tris"], 1)
+    model = {"k_predict": predictor_flops(args.order), "k_recon": recon_flops(args.order, members)}
+    roof = None
+    if dom in model and kms[dom] > 0:
+        achieved = model[dom] * updates / (kms[dom] * 1e-3) / 1e12
+        peak = peak_gflops / 1e3
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured FP64 DFMA throughput (aw_measure_fp64_peak, this run)",
+                "flops_per_update": model[dom]}
+
+    # end to end through the C ABI with host buffers: state upload + initial
+    # phase, the same number of sweeps, state download
+    e2e = None
+    if args.e2e:
+        s2 = aleweno.Solver(**cfg)
+        s2.load_mesh(mesh)
+        Qh = np.ascontiguousarray(Q)
+        out = np.empty_like(Qh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.load_state(Qh)
+        ups = 0
+        for _ in range(args.warmup + args.steps):
+            ups += s2.sweep()
+        s2.get_state(out)
+        el = time.perf_counter() - t0
+        nst = args.warmup + args.steps
+        e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": Qh.nbytes / nst,
+               "d2h_bytes_per_step": (out.nbytes + 8 * nst) / nst,
+               "note": "aw_load_state(host Q) + sweeps via aw_lts_sweep + aw_get_state(host Q); mesh pre-processing "
+                       f"({t_mesh:.1f} s, once per mesh) excluded"}
+        s2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        rate, info = cpu_sample(args.order, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle (serial C, FP64) on a {info['n_tris']}-triangle graded disc with the same EP1 "
+                         f"data and P{args.order} LTS scheme, {info['sweeps']} sweeps from t=0 "
+                         f"({info['updates']} updates, {info['seconds']:.1f} s), pre-processing untimed"}
+    if rank == 0:
+        share_tot = sum(kms.values()) or 1.0
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"cylindrical explosion EP1 on a graded disc, {n_tris} triangles, "
+                                       f"P{args.order} LTS, CFL 0.5, t_end 0.25",
+                           "n_tris": n_tris, "order_M": args.order, "parallelism": f"replicas x{world}",
+                           "l2": "256 MiB write between timed sweeps (L2 is 129 MB)",
+                           "updates_timed": int(updates_all), "sw_entries_per_elem": sizes["sw_entries"] / n_tris},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 9 * args.steps,
+                "clocks": clk,
+                "kernels": {k: {"ms": v, "share": v / share_tot} for k, v in kms.items()},
+                "fp64_peak_gflops": peak_gflops}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--hc", type=float, default=0.00114)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

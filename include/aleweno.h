@@ -122,9 +122,20 @@ int aw_set_node_arrays(aw_ctx* ctx, const double* X, const int64_t* t);
 /* out[0] = largest GCL residual |sum of int n dS| / |T| seen in an update
  * (eq. gcl); out[1] = number of element updates; out[2] = sweeps run. */
 int aw_diagnostics(aw_ctx* ctx, double* out);
-/* Sizes: out[0] n_tris, out[1] n_nodes, out[2] n_edges, out[3] N_st,
- * out[4] total S^W entries. */
+/* Sizes (out has 6 entries): out[0] n_tris, out[1] n_nodes, out[2] n_edges,
+ * out[3] N_st, out[4] total S^W entries, out[5] total distinct members of
+ * the seven reconstruction stencils (without the element itself). */
 int aw_sizes(aw_ctx* ctx, int64_t* out);
+
+/* Per-kernel timing of sweeps with CUDA events recorded on the context's
+ * stream between the launches.  aw_profile_enable(ctx, 1) resets and starts
+ * it; aw_profile_read fills ms[k] (total milliseconds of kernel k over the
+ * profiled sweeps, k < the return value) and *sweeps, and returns the number
+ * of kernels per sweep; aw_kernel_name(k) names kernel k (NULL if out of
+ * range).  Recording adds a few microseconds per sweep. */
+int aw_profile_enable(aw_ctx* ctx, int on);
+int aw_profile_read(aw_ctx* ctx, double* ms, int64_t* sweeps);
+const char* aw_kernel_name(int k);
 
 /* Measured FP64 FMA throughput of the current GPU (GFLOP/s), a roofline
  * denominator: a fixed dependent-chain DFMA kernel over all SMs. */

@@ -23,7 +23,8 @@ AW_ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "BAD_MESH", -3: "NONPHYSICAL", -4: 
 EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load_state", "aw_lts_sweep",
             "aw_gts_step", "aw_advance_to", "aw_enqueue_sweeps", "aw_sync", "aw_get_state", "aw_get_nodes",
             "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
-            "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_measure_fp64_peak"]
+            "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_profile_enable", "aw_profile_read",
+            "aw_kernel_name", "aw_measure_fp64_peak"]
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +74,10 @@ def load(path: str | None = None):
             lib.aw_set_node_arrays.argtypes = [P, P, P]
             lib.aw_diagnostics.argtypes = [P, P]
             lib.aw_sizes.argtypes = [P, P]
+            lib.aw_profile_enable.argtypes = [P, C.c_int]
+            lib.aw_profile_read.argtypes = [P, P, C.POINTER(i64)]
+            lib.aw_kernel_name.argtypes = [C.c_int]
+            lib.aw_kernel_name.restype = C.c_char_p
             lib.aw_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
             _lib = lib
     return _lib
@@ -211,8 +216,20 @@ class Solver:
         self._check(self.lib.aw_diagnostics(self.h, _ptr(out)))
         return dict(gcl_max=out[0], updates=out[1], sweeps=out[2])
 
+    def profile(self, on=True):
+        self._check(self.lib.aw_profile_enable(self.h, int(on)))
+
+    def profile_read(self):
+        ms = np.zeros(32)
+        sw = C.c_int64(0)
+        n = self.lib.aw_profile_read(self.h, _ptr(ms), C.byref(sw))
+        if n < 0:
+            self._check(n)
+        names = [self.lib.aw_kernel_name(k).decode() for k in range(n)]
+        return dict(zip(names, ms[:n].tolist())), sw.value
+
     def sizes(self):
-        out = np.zeros(5, np.int64)
+        out = np.zeros(6, np.int64)
         self._check(self.lib.aw_sizes(self.h, _ptr(out)))
         return dict(n_tris=int(out[0]), n_nodes=int(out[1]), n_edges=int(out[2]), n_st=int(out[3]),
-                    sw_entries=int(out[4]))
+                    sw_entries=int(out[4]), u_entries=int(out[5]))

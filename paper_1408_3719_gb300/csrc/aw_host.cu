@@ -26,7 +26,11 @@ struct aw_ctx {
   bool have_mesh = false, have_state = false, failed = false;
   std::vector<void*> allocs;
   Counters* hcnt = nullptr;  // pinned mirror of the device counters
-  long long ne = 0, nn = 0, ned = 0, sw_total = 0;
+  bool prof = false;         // per-kernel CUDA-event timing of sweeps
+  std::vector<std::vector<cudaEvent_t>> prof_pending;
+  double prof_ms[kNumKernels] = {0};
+  long long prof_sweeps = 0;
+  long long ne = 0, nn = 0, ned = 0, sw_total = 0, u_total = 0;
   std::vector<double> xy0;
   double* d_corner0 = nullptr;  // element corners at t = 0
 };
@@ -601,10 +605,25 @@ int reset_sweep_state(aw_ctx* c) {
   return AW_OK;
 }
 
+// fold the events of completed profiled sweeps into the per-kernel totals
+int drain_profile(aw_ctx* c) {
+  for (auto& ev : c->prof_pending) {
+    for (int k = 0; k < kNumKernels; ++k) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      c->prof_ms[k] += ms;
+    }
+    c->prof_sweeps += 1;
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  c->prof_pending.clear();
+  return AW_OK;
+}
+
 int sync_counters(aw_ctx* c) {
   CK(cudaMemcpyAsync(c->hcnt, c->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  return AW_OK;
+  return drain_profile(c);
 }
 
 int check_device_error(aw_ctx* c) {
@@ -650,6 +669,8 @@ int aw_create(const aw_config* cfg, aw_ctx** out) {
 
 void aw_destroy(aw_ctx* c) {
   if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drain_profile(c);
   free_all(c);
   if (c->hcnt) cudaFreeHost(c->hcnt);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -726,6 +747,7 @@ int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
   CK(cudaStreamSynchronize(c->stream));
   c->xy0 = hxy;
   c->ne = m.ne; c->nn = m.nn; c->ned = m.ned; c->sw_total = (long long)m.sw.size();
+  c->u_total = (long long)m.u_elem.size();
   c->have_mesh = true;
   c->have_state = false;
   c->failed = false;
@@ -770,7 +792,16 @@ int aw_load_state(aw_ctx* c, const double* Q) {
 
 static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
-  for (int64_t k = 0; k < n; ++k) launch_sweep(c->tab, c->d, c->nsm, c->stream);
+  for (int64_t k = 0; k < n; ++k) {
+    cudaEvent_t* ev = nullptr;
+    if (c->prof) {
+      std::vector<cudaEvent_t> evs(kNumKernels + 1);
+      for (auto& e : evs) CK(cudaEventCreate(&e));
+      c->prof_pending.push_back(evs);
+      ev = c->prof_pending.back().data();
+    }
+    launch_sweep(c->tab, c->d, c->nsm, c->stream, ev);
+  }
   CK(cudaGetLastError());
   if (!wait) return AW_OK;
   int rc = sync_counters(c);
@@ -944,8 +975,31 @@ int aw_diagnostics(aw_ctx* c, double* out) {
 int aw_sizes(aw_ctx* c, int64_t* out) {
   if (!c || !out) return AW_ERR_INVALID_ARG;
   out[0] = c->ne; out[1] = c->nn; out[2] = c->ned; out[3] = c->tab.Nst; out[4] = c->sw_total;
+  out[5] = c->u_total;
   return AW_OK;
 }
+
+int aw_profile_enable(aw_ctx* c, int on) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  c->prof = on != 0;
+  for (double& v : c->prof_ms) v = 0.0;
+  c->prof_sweeps = 0;
+  return AW_OK;
+}
+
+int aw_profile_read(aw_ctx* c, double* ms, int64_t* sweeps) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if (ms)
+    for (int k = 0; k < kNumKernels; ++k) ms[k] = c->prof_ms[k];
+  if (sweeps) *sweeps = c->prof_sweeps;
+  return kNumKernels;
+}
+
+const char* aw_kernel_name(int k) { return kernel_name(k); }
 
 int aw_measure_fp64_peak(double* gflops) {
   if (!gflops) return AW_ERR_INVALID_ARG;

@@ -115,7 +115,9 @@ struct Counters {
 };
 
 // kernel launchers (aw_kernels.cu)
-void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+constexpr int kNumKernels = 9;  // launches per sweep
+const char* kernel_name(int k);
+void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev);
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 double measure_fp64_peak();

@@ -780,20 +780,25 @@ __global__ void k_fill_counters_initial(Dev d) {
   }
 }
 
+// ev (optional): kNumKernels + 1 events recorded on s around the launches,
+// for per-kernel CUDA-event timing on the launching stream.
 template <int M>
-void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev) {
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
   const int grid_all_ed = (d.ned + kBlock - 1) / kBlock;
   const int grid_w = nsm * 8;
-  k_begin<<<1, 32, 0, s>>>(d);
-  k_ready<<<grid_all_e, kBlock, 0, s>>>(T, d);
-  k_nodes<M><<<grid_w, kBlock, 0, s>>>(T, d);
-  k_edges<<<grid_all_ed, kBlock, 0, s>>>(d);
-  k_flux<M><<<grid_w, kBlock, 0, s>>>(T, d);
-  k_update<<<grid_w, kBlock, 0, s>>>(T, d);
-  k_commit<<<grid_w, kBlock, 0, s>>>(d);
-  k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 0);
-  k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 0, T.gts);
+  int k = 0;
+  auto mark = [&]() { if (ev) cudaEventRecord(ev[k++], s); };
+  mark(); k_begin<<<1, 32, 0, s>>>(d);
+  mark(); k_ready<<<grid_all_e, kBlock, 0, s>>>(T, d);
+  mark(); k_nodes<M><<<grid_w, kBlock, 0, s>>>(T, d);
+  mark(); k_edges<<<grid_all_ed, kBlock, 0, s>>>(d);
+  mark(); k_flux<M><<<grid_w, kBlock, 0, s>>>(T, d);
+  mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
+  mark(); k_commit<<<grid_w, kBlock, 0, s>>>(d);
+  mark(); k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 0);
+  mark(); k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 0, T.gts);
+  mark();
 }
 
 template <int M>
@@ -819,11 +824,17 @@ __global__ void k_dfma_chain(double* out, int iters, double a, double b) {
 
 }  // namespace
 
-void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+const char* kernel_name(int k) {
+  static const char* names[kNumKernels] = {"k_begin", "k_ready", "k_nodes", "k_edges", "k_flux",
+                                           "k_update", "k_commit", "k_recon", "k_predict"};
+  return (k >= 0 && k < kNumKernels) ? names[k] : nullptr;
+}
+
+void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev) {
   switch (T.M) {
-    case 1: sweep_impl<1>(T, d, nsm, s); break;
-    case 2: sweep_impl<2>(T, d, nsm, s); break;
-    default: sweep_impl<3>(T, d, nsm, s); break;
+    case 1: sweep_impl<1>(T, d, nsm, s, ev); break;
+    case 2: sweep_impl<2>(T, d, nsm, s, ev); break;
+    default: sweep_impl<3>(T, d, nsm, s, ev); break;
   }
 }
 
