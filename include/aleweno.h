@@ -137,6 +137,25 @@ int aw_profile_enable(aw_ctx* ctx, int on);
 int aw_profile_read(aw_ctx* ctx, double* ms, int64_t* sweeps);
 const char* aw_kernel_name(int k);
 
+/* The set of elements that satisfy the update criterion in the context's
+ * current state (the elements the next aw_lts_sweep will update), computed
+ * without allocating any memory.  No counterpart in the paper: it exists for
+ * callers that cannot call cudaMalloc -- code running between the launches of
+ * an application that owns all device memory through its own pool, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  The caller passes the outputs: ready_out, a device array
+ * with room for n_tris int32, receives the ready element indices in ascending
+ * order; n_ready_out, a device int64, receives their number.  The work is
+ * enqueued on the context's stream and not waited for.  Scratch is a fixed
+ * 16 KB array in device memory that every GPU loading the library holds until
+ * the process exits; the first call on a device looks its address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other contexts) race and must be serialised by the caller.  Meshes with more
+ * than 1,048,576 triangles are rejected with AW_ERR_INVALID_ARG; STATE without
+ * a loaded state. */
+int aw_ready_set_noalloc(aw_ctx* ctx, int32_t* ready_out, int64_t* n_ready_out);
+
 /* Measured FP64 FMA throughput of the current GPU (GFLOP/s), a roofline
  * denominator: a fixed dependent-chain DFMA kernel over all SMs. */
 int aw_measure_fp64_peak(double* gflops);

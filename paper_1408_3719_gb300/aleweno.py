@@ -24,7 +24,7 @@ EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load
             "aw_gts_step", "aw_advance_to", "aw_enqueue_sweeps", "aw_sync", "aw_get_state", "aw_get_nodes",
             "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
             "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_profile_enable", "aw_profile_read",
-            "aw_kernel_name", "aw_measure_fp64_peak"]
+            "aw_kernel_name", "aw_ready_set_noalloc", "aw_measure_fp64_peak"]
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +78,7 @@ def load(path: str | None = None):
             lib.aw_profile_read.argtypes = [P, P, C.POINTER(i64)]
             lib.aw_kernel_name.argtypes = [C.c_int]
             lib.aw_kernel_name.restype = C.c_char_p
+            lib.aw_ready_set_noalloc.argtypes = [P, P, P]
             lib.aw_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
             _lib = lib
     return _lib

@@ -636,6 +636,20 @@ int check_device_error(aw_ctx* c) {
 
 }  // namespace
 
+// read-only access to a context for the allocation-free entry point
+namespace aw {
+bool ctx_view(aw_ctx* c, CtxView* v) {
+  if (!c || !c->have_state || c->failed) return false;
+  v->d = &c->d;
+  v->T = c->tab.T;
+  v->stream = c->stream;
+  return true;
+}
+void ctx_error(aw_ctx* c, const char* msg) {
+  if (c) c->err = msg;
+}
+}  // namespace aw
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

@@ -123,3 +123,15 @@ void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 double measure_fp64_peak();
 
 }  // namespace aw
+
+struct aw_ctx;
+namespace aw {
+struct CtxView {
+  const Dev* d;
+  long long T;
+  cudaStream_t stream;
+};
+// false if the context has no valid state
+bool ctx_view(aw_ctx* c, CtxView* v);
+void ctx_error(aw_ctx* c, const char* msg);
+}  // namespace aw
