@@ -19,6 +19,7 @@
 // depend on the order of the lists.
 #include <cfloat>
 #include <climits>
+#include <algorithm>
 #include <cstdio>
 
 #include "aw_internal.h"
@@ -773,11 +774,569 @@ __global__ void k_products(Tab T, Dev d) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cooperative predictor: one thread per (element, space-time node), G
+// elements per 128-thread block, the element's nodal arrays in shared memory.
+// ---------------------------------------------------------------------------
+template <int M>
+struct PredShape {
+  static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, Nst = Mc * Nt;
+  static constexpr int kThreads = 128;
+  static constexpr int G = kThreads / Nst;
+};
+
+template <int M>
+__global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial, int gts) {
+  using S = PredShape<M>;
+  constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst, G = S::G;
+  __shared__ double sq[G][Nst][4], sf[G][Nst][4], sg[G][Nst][4], sP[G][Nst][4];
+  __shared__ double sx[G][Nst][2], sV[G][Nst][2];
+  __shared__ double sDxi[Mc][Mc], sDeta[Mc][Mc], sB[Nt - 1][Nt], sDtau[Nt][Nt], sTr[3][Nt][Mc], sVt[Nt][Nt];
+  __shared__ double sdts[G];
+  __shared__ int sidx[G];
+  for (int k = threadIdx.x; k < Mc * Mc; k += blockDim.x) {
+    sDxi[k / Mc][k % Mc] = T.Dxi[k / Mc][k % Mc];
+    sDeta[k / Mc][k % Mc] = T.Deta[k / Mc][k % Mc];
+  }
+  for (int k = threadIdx.x; k < (Nt - 1) * Nt; k += blockDim.x) sB[k / Nt][k % Nt] = T.B[k / Nt][k % Nt];
+  for (int k = threadIdx.x; k < Nt * Nt; k += blockDim.x) {
+    sDtau[k / Nt][k % Nt] = T.Dtau[k / Nt][k % Nt];
+    sVt[k / Nt][k % Nt] = T.VtInv[k / Nt][k % Nt];
+  }
+  for (int k = threadIdx.x; k < 3 * Nt * Mc; k += blockDim.x) sTr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc] = T.Tr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc];
+  const int n_ready = initial ? d.ne : d.cnt->n_ready;
+  const long long gmin = d.cnt->gts_min;
+  const int e = threadIdx.x / Nst, l = threadIdx.x % Nst;
+  const int t = l / Mc, s = l % Mc;
+  const double gm1 = T.gamma - 1.0;
+  for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
+    const int pos = base + e;
+    const bool live = e < G && pos < n_ready;
+    if (live && l == 0) {
+      const int i = initial ? pos : d.ready_list[pos];
+      long long dtk = d.dt[i];
+      if (gts && dtk > 0) {
+        dtk = gmin;
+        d.dt[i] = dtk;
+      }
+      sidx[e] = i;
+      sdts[e] = (double)dtk * T.tick;
+    }
+    __syncthreads();
+    const int i = live ? sidx[e] : 0;
+    const double dts = live ? sdts[e] : 0.0;
+    const bool work = live && dts > 0.0;
+    if (live) {
+      const double* w0 = d.w0 + (size_t)pos * Mc * 4;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sq[e][l][v] = w0[s * 4 + v];
+      const double* X = d.X + 6 * (size_t)i;
+      sx[e][l][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
+      sx[e][l][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
+    }
+    __syncthreads();
+    const double idt = work ? 1.0 / dts : 0.0;
+    for (int it = 0; it < T.nit; ++it) {
+      if (work) {  // nodal fluxes and mesh velocity at the own node
+        const double* q = sq[e][l];
+        const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+        const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+        sf[e][l][0] = q[1]; sf[e][l][1] = q[1] * u + p; sf[e][l][2] = q[1] * v; sf[e][l][3] = u * (q[3] + p);
+        sg[e][l][0] = q[2]; sg[e][l][1] = q[2] * u; sg[e][l][2] = q[2] * v + p; sg[e][l][3] = v * (q[3] + p);
+        sV[e][l][0] = T.eulerian ? 0.0 : u;
+        sV[e][l][1] = T.eulerian ? 0.0 : v;
+      }
+      __syncthreads();
+      if (work) {  // P at the own node (eq. pdef) with the isoparametric metric (eq. Jac)
+        double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
+        double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
+        double xx = 0, xe = 0, yx = 0, ye = 0;
+#pragma unroll
+        for (int r = 0; r < Mc; ++r) {
+          const double a = sDxi[s][r], b = sDeta[s][r];
+          const int lr = t * Mc + r;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const double qv = sq[e][lr][v], fv = sf[e][lr][v], gv = sg[e][lr][v];
+            Qx[v] += a * qv; Qe[v] += b * qv;
+            fx[v] += a * fv; fe[v] += b * fv;
+            gx[v] += a * gv; ge[v] += b * gv;
+          }
+          xx += a * sx[e][lr][0]; xe += b * sx[e][lr][0];
+          yx += a * sx[e][lr][1]; ye += b * sx[e][lr][1];
+        }
+        double xt = 0.0, yt = 0.0;
+#pragma unroll
+        for (int u = 0; u < Nt; ++u) {
+          xt += sDtau[t][u] * sx[e][u * Mc + s][0];
+          yt += sDtau[t][u] * sx[e][u * Mc + s][1];
+        }
+        xt *= idt;
+        yt *= idt;
+        const double idet = 1.0 / (xx * ye - xe * yx);
+        const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+        const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          sP[e][l][v] = -(Qx[v] * xit + Qe[v] * ett + fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
+      }
+      __syncthreads();
+      if (work && t > 0) {  // K_tau qhat = dt M P with the tau = 0 dofs known (eqs. CGfinal, newVertPos)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+#pragma unroll
+          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sP[e][u * Mc + s][v];
+          sq[e][l][v] = sq[e][s][v] + dts * acc;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          double acc = 0.0;
+#pragma unroll
+          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sV[e][u * Mc + s][c];
+          sx[e][l][c] = sx[e][s][c] + dts * acc;
+        }
+      }
+      __syncthreads();
+    }
+    if (live) {
+      double* out = d.qhat + ((size_t)i * Nst + l) * 4;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = sq[e][l][v];
+      // derived tables: edge traces, reference averages, vertex displacements
+      constexpr int nTr = 3 * Nt * 4, nItems = nTr + 4 + 6;
+      for (int item = l; item < nItems; item += Nst) {
+        if (item < nTr) {
+          const int le = item / (Nt * 4), g = (item / 4) % Nt, v = item % 4;
+          double val[Nt];
+#pragma unroll
+          for (int tt = 0; tt < Nt; ++tt) {
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < Mc; ++r) acc += sTr[le][g][r] * sq[e][tt * Mc + r][v];
+            val[tt] = acc;
+          }
+          double* tr = d.trace + (((size_t)i * 3 + le) * Nt + g) * Nt * 4;
+#pragma unroll
+          for (int p = 0; p < Nt; ++p) {
+            double acc = 0.0;
+#pragma unroll
+            for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * val[tt];
+            tr[p * 4 + v] = acc;
+          }
+        } else if (item < nTr + 4) {
+          const int v = item - nTr;
+          double val[Nt];
+#pragma unroll
+          for (int tt = 0; tt < Nt; ++tt) {
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < Mc; ++r) acc += T.wavg[r] * sq[e][tt * Mc + r][v];
+            val[tt] = acc;
+          }
+          double* av = d.avgc + (size_t)i * Nt * 4;
+#pragma unroll
+          for (int p = 0; p < Nt; ++p) {
+            double acc = 0.0;
+#pragma unroll
+            for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * val[tt];
+            av[p * 4 + v] = acc;
+          }
+        } else {
+          const int kc = item - nTr - 4, k = kc / 2, c = kc % 2;
+          const int sn = k == 0 ? 0 : (k == 1 ? M : Mc - 1);
+          double vel[Nt];
+#pragma unroll
+          for (int tt = 0; tt < Nt; ++tt) {
+            const double* q = sq[e][tt * Mc + sn];
+            vel[tt] = T.eulerian ? 0.0 : q[1 + c] / q[0];
+          }
+          double* vd = d.vdisp + ((size_t)i * 6 + kc) * Nt;
+#pragma unroll
+          for (int p = 0; p < Nt; ++p) {
+            double acc = 0.0;
+#pragma unroll
+            for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * vel[tt];
+            vd[p] = acc / (p + 1);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cooperative reconstruction: G ready elements per 256-thread block; each
+// phase flattens its work items over the block (stencil members, normal-
+// equation entries, stencils, characteristic fields, output nodes).
+// ---------------------------------------------------------------------------
+template <int M>
+struct ReconShape {
+  static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, NU = Mc - 1, NE = 2 * Mc;
+  static constexpr int MaxU = kNSten * (NE - 1);
+  static constexpr int G = M == 1 ? 16 : (M == 2 ? 8 : 4);
+  static constexpr int kThreads = 256;
+  static constexpr int NL = NU * (NU + 1) / 2;      // lower triangle of the normal matrix
+  static constexpr int NN = NL + 4 * NU;           // + right-hand sides
+  static constexpr int RW = NU + 4;                 // row: basis averages, then Q~ - Q_i
+  static constexpr size_t oRow = 0;
+  static constexpr size_t oNrm = oRow + (size_t)G * (MaxU + 1) * RW;
+  static constexpr size_t oC = oNrm + (size_t)G * kNSten * NN;
+  static constexpr size_t oCh = oC + (size_t)G * kNSten * NU * 4;
+  static constexpr size_t oSig = oCh + (size_t)G * kNSten * NU * 4;
+  static constexpr size_t oWc = oSig + (size_t)G * kNSten * 4;
+  static constexpr size_t oCv = oWc + (size_t)G * NU * 4;
+  static constexpr size_t oRL = oCv + (size_t)G * NU * 4;
+  static constexpr size_t oEl = oRL + (size_t)G * 32;   // X(6), Q(4), Jinv(4)
+  static constexpr size_t oDt = oEl + (size_t)G * 16;
+  static constexpr size_t oBn = oDt + (size_t)G * 4;    // Bnod [Mc][NU]
+  static constexpr size_t nDbl = oBn + (size_t)Mc * NU;
+  static constexpr size_t nInt = 5 * G + 1 + G * kNSten;  // i, pos-valid, u0, nU, prefix[G+1], ok[G][7]
+  static constexpr size_t bytes = nDbl * 8 + nInt * 4 + (size_t)G * kNSten * NE;
+};
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial) {
+  using S = ReconShape<M>;
+  constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE, MaxU = S::MaxU, G = S::G, NL = S::NL, NN = S::NN, RW = S::RW;
+  extern __shared__ double smem[];
+  double* sRow = smem + S::oRow;
+  double* sNrm = smem + S::oNrm;
+  double* sC = smem + S::oC;
+  double* sCh = smem + S::oCh;
+  double* sSig = smem + S::oSig;
+  double* sWc = smem + S::oWc;
+  double* sCv = smem + S::oCv;
+  double* sRL = smem + S::oRL;
+  double* sEl = smem + S::oEl;
+  double* sDt = smem + S::oDt;
+  double* sBn = smem + S::oBn;
+  int* sI = reinterpret_cast<int*>(smem + S::nDbl);
+  int* sVal = sI + G;
+  int* sU0 = sVal + G;
+  int* sNU = sU0 + G;
+  int* sPre = sNU + G;            // G + 1
+  int* sOk = sPre + G + 1;        // G * 7
+  unsigned char* sSt = reinterpret_cast<unsigned char*>(sOk + G * kNSten);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int k = tid; k < Mc * NU; k += nth) sBn[k] = T.Bnod[k / NU][k % NU];
+  const int n_ready = initial ? d.ne : d.cnt->n_ready;
+  for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
+    // P0: element set-up
+    if (tid < G) {
+      const int e = tid, pos = base + e;
+      const bool v = pos < n_ready;
+      sVal[e] = v;
+      int nU = 0;
+      if (v) {
+        const int i = initial ? pos : d.ready_list[pos];
+        sI[e] = i;
+        double* el = sEl + e * 16;
+        for (int k = 0; k < 6; ++k) el[k] = d.X[6 * (size_t)i + k];
+        for (int k = 0; k < 4; ++k) el[6 + k] = d.Q[4 * (size_t)i + k];
+        const double ja = el[2] - el[0], jb = el[4] - el[0], jc = el[3] - el[1], jd = el[5] - el[1];
+        const double idet = 1.0 / (ja * jd - jb * jc);
+        el[10] = jd * idet; el[11] = -jb * idet; el[12] = -jc * idet; el[13] = ja * idet;
+        sU0[e] = d.u_ptr[i];
+        nU = d.u_ptr[i + 1] - sU0[e];
+        for (int s = 0; s < kNSten; ++s) sOk[e * kNSten + s] = d.sten_ok[(size_t)i * kNSten + s];
+      }
+      sNU[e] = nU;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sPre[0] = 0;
+      for (int e = 0; e < G; ++e) sPre[e + 1] = sPre[e] + (sVal[e] ? sNU[e] + 4 : 0);
+    }
+    for (int k = tid; k < G * kNSten * NE; k += nth) {
+      const int e = k / (kNSten * NE);
+      sSt[k] = sVal[e] ? d.sten[(size_t)sI[e] * kNSten * NE + k % (kNSten * NE)] : 0;
+    }
+    __syncthreads();
+    // P1: rows of the least-squares systems (virtual data, eqs. virtGeom,
+    // virtCellaverage, intConsRec) and the time-step candidates (eq. timestep)
+    for (int item = tid; item < sPre[G]; item += nth) {
+      int e = 0;
+      while (item >= sPre[e + 1]) ++e;
+      const int u = item - sPre[e];
+      const double* el = sEl + e * 16;
+      const int i = sI[e];
+      const long long ti = d.t[i];
+      double Xv[6], Qv[4];
+      if (u < sNU[e]) {
+        const int q = sU0[e] + u;
+        const int j = d.u_elem[q];
+        virtual_data<M>(T, d, j, ti, Xv, Qv);
+        const double sx = d.u_shift[2 * (size_t)q], sy = d.u_shift[2 * (size_t)q + 1];
+        double xr[3], yr[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double px = Xv[2 * k] + sx - el[0], py = Xv[2 * k + 1] + sy - el[1];
+          xr[k] = el[10] * px + el[11] * py - (1.0 / 3.0);
+          yr[k] = el[12] * px + el[13] * py - (1.0 / 3.0);
+        }
+        double row[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) row[a] = 0.0;
+        for (int qq = 0; qq < T.nq; ++qq) {
+          const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
+          const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
+          double m[kMaxNU];
+          centred_monomials<M>(T, x, y, m);
+#pragma unroll
+          for (int a = 0; a < NU; ++a) row[a] += T.qw[qq] * m[a];
+        }
+        double* dst = sRow + ((size_t)e * (MaxU + 1) + u + 1) * RW;
+#pragma unroll
+        for (int a = 0; a < NU; ++a) dst[a] = row[a] - T.mbar[a];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[NU + v] = Qv[v] - el[6 + v];
+      } else {
+        const int k = u - sNU[e];
+        const int j = k == 0 ? i : d.nbr[3 * (size_t)i + k - 1];
+        double dtc = DBL_MAX;
+        if (j >= 0 && ti < T.T) {
+          virtual_data<M>(T, d, j, ti, Xv, Qv);
+          double per = 0.0;
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const int k1 = kk == 2 ? 0 : kk + 1;
+            const double dx = Xv[2 * k1] - Xv[2 * kk], dy = Xv[2 * k1 + 1] - Xv[2 * kk + 1];
+            per += sqrt(dx * dx + dy * dy);
+          }
+          const double dd = 4.0 * area6(Xv) / per;
+          const double uu = Qv[1] / Qv[0], vv = Qv[2] / Qv[0];
+          const double lam = sqrt(uu * uu + vv * vv) + sqrt(T.gamma * pressure(T, Qv) / Qv[0]);
+          dtc = T.cfl * dd / lam;
+          if (!(dtc > 0.0)) dtc = -1.0;
+        }
+        sDt[e * 4 + k] = dtc;
+      }
+    }
+    __syncthreads();
+    // P2: normal equations of every stencil
+    for (int item = tid; item < G * kNSten * NN; item += nth) {
+      const int e = item / (kNSten * NN), s = (item / NN) % kNSten, q = item % NN;
+      if (!sVal[e] || !sOk[e * kNSten + s]) continue;
+      int a, b, v = -1;
+      if (q < NL) {
+        a = 0;
+        while ((a + 1) * (a + 2) / 2 <= q) ++a;
+        b = q - a * (a + 1) / 2;
+      } else {
+        a = (q - NL) / 4;
+        v = (q - NL) % 4;
+        b = NU + v;
+      }
+      const unsigned char* st = sSt + (e * kNSten + s) * NE;
+      const double* R0 = sRow + (size_t)e * (MaxU + 1) * RW;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 1; m < NE; ++m) {
+        const double* r = R0 + (size_t)st[m] * RW;
+        acc += r[a] * r[b];
+      }
+      sNrm[(e * kNSten + s) * NN + q] = acc;
+    }
+    __syncthreads();
+    // P3: Cholesky factorisation and the two triangular solves per stencil
+    for (int item = tid; item < G * kNSten; item += nth) {
+      const int e = item / kNSten, s = item % kNSten;
+      if (!sVal[e] || !sOk[e * kNSten + s]) continue;
+      const double* nm = sNrm + (size_t)item * NN;
+      double L[NU][NU];
+#pragma unroll
+      for (int a = 0; a < NU; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) L[a][b] = nm[a * (a + 1) / 2 + b];
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        double dd = L[a][a];
+#pragma unroll
+        for (int k = 0; k < a; ++k) dd -= L[a][k] * L[a][k];
+        const double la = sqrt(dd), il = 1.0 / la;
+        L[a][a] = la;
+#pragma unroll
+        for (int b = a + 1; b < NU; ++b) {
+          double v = L[b][a];
+#pragma unroll
+          for (int k = 0; k < a; ++k) v -= L[b][k] * L[a][k];
+          L[b][a] = v * il;
+        }
+      }
+      double* cs = sC + (size_t)item * NU * 4;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double y[NU];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+          double acc = nm[NL + a * 4 + v];
+#pragma unroll
+          for (int k = 0; k < a; ++k) acc -= L[a][k] * y[k];
+          y[a] = acc / L[a][a];
+        }
+#pragma unroll
+        for (int a = NU - 1; a >= 0; --a) {
+          double acc = y[a];
+#pragma unroll
+          for (int k = a + 1; k < NU; ++k) acc -= L[k][a] * cs[k * 4 + v];
+          cs[a * 4 + v] = acc / L[a][a];
+        }
+      }
+    }
+    __syncthreads();
+    // P4: characteristic fields of dF/dQ.n, n along the density gradient of
+    // the central-stencil polynomial at the centroid (its linear coefficients)
+    if (tid < G && sVal[tid]) {
+      const int e = tid;
+      const double* el = sEl + e * 16;
+      const double* c0 = sC + (size_t)(e * kNSten) * NU * 4;
+      const double gx = c0[0 * 4] * el[10] + c0[1 * 4] * el[12];
+      const double gy = c0[0 * 4] * el[11] + c0[1 * 4] * el[13];
+      const double gn = sqrt(gx * gx + gy * gy);
+      double nx = 1.0, ny = 0.0;
+      if (gn > 0.0) { nx = gx / gn; ny = gy / gn; }
+      const double g = T.gamma, rho = el[6], u = el[7] / rho, v = el[8] / rho;
+      const double p = (g - 1.0) * (el[9] - 0.5 * rho * (u * u + v * v));
+      const double a = sqrt(g * p / rho), H = (el[9] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
+      const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
+      double* R = sRL + e * 32;
+      double* Lm = R + 16;
+      R[0] = 1; R[1] = 1; R[2] = 0; R[3] = 1;
+      R[4] = u - a * nx; R[5] = u; R[6] = -ny; R[7] = u + a * nx;
+      R[8] = v - a * ny; R[9] = v; R[10] = nx; R[11] = v + a * ny;
+      R[12] = H - a * un; R[13] = q2; R[14] = ut; R[15] = H + a * un;
+      Lm[0] = 0.5 * (b2 + un * ia); Lm[1] = -0.5 * (b1 * u + nx * ia); Lm[2] = -0.5 * (b1 * v + ny * ia); Lm[3] = 0.5 * b1;
+      Lm[4] = 1.0 - b2; Lm[5] = b1 * u; Lm[6] = b1 * v; Lm[7] = -b1;
+      Lm[8] = -ut; Lm[9] = -ny; Lm[10] = nx; Lm[11] = 0.0;
+      Lm[12] = 0.5 * (b2 - un * ia); Lm[13] = -0.5 * (b1 * u - nx * ia); Lm[14] = -0.5 * (b1 * v - ny * ia); Lm[15] = 0.5 * b1;
+    }
+    __syncthreads();
+    // P5: characteristic coefficients and oscillation indicators (eq. weno)
+    for (int item = tid; item < G * kNSten * 4; item += nth) {
+      const int e = item / (kNSten * 4), s = (item / 4) % kNSten, r = item % 4;
+      if (!sVal[e] || !sOk[e * kNSten + s]) continue;
+      const double* Lr = sRL + e * 32 + 16 + r * 4;
+      const double* cs = sC + (size_t)(e * kNSten + s) * NU * 4;
+      double* ch = sCh + (size_t)(e * kNSten + s) * NU * 4;
+      double cc[NU];
+#pragma unroll
+      for (int l = 0; l < NU; ++l) {
+        cc[l] = Lr[0] * cs[l * 4] + Lr[1] * cs[l * 4 + 1] + Lr[2] * cs[l * 4 + 2] + Lr[3] * cs[l * 4 + 3];
+        ch[l * 4 + r] = cc[l];
+      }
+      double sg = 0.0;
+#pragma unroll
+      for (int a = 0; a < NU; ++a) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = a; b < NU; ++b) acc += T.SigU[a][b] * cc[b];
+        sg += acc * acc;
+      }
+      sSig[(e * kNSten + s) * 4 + r] = sg;
+    }
+    __syncthreads();
+    // P6: nonlinear weights and the weighted characteristic coefficients
+    for (int item = tid; item < G * 4; item += nth) {
+      const int e = item / 4, r = item % 4;
+      if (!sVal[e]) continue;
+      double om[kNSten], tot = 0.0;
+#pragma unroll
+      for (int s = 0; s < kNSten; ++s) {
+        om[s] = 0.0;
+        if (!sOk[e * kNSten + s]) continue;
+        const double e1 = sSig[(e * kNSten + s) * 4 + r] + 1e-14;
+        const double e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
+        om[s] = (s == 0 ? 1e5 : 1.0) / e8;
+        tot += om[s];
+      }
+      const double itot = 1.0 / tot;
+#pragma unroll
+      for (int l = 0; l < NU; ++l) {
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < kNSten; ++s)
+          if (sOk[e * kNSten + s]) acc += (om[s] * itot) * sCh[((size_t)(e * kNSten + s) * NU + l) * 4 + r];
+        sWc[(e * NU + l) * 4 + r] = acc;
+      }
+    }
+    __syncthreads();
+    // P7: back to conserved variables
+    for (int item = tid; item < G * NU * 4; item += nth) {
+      const int e = item / (NU * 4), l = (item / 4) % NU, v = item % 4;
+      if (!sVal[e]) continue;
+      const double* Rv = sRL + e * 32 + v * 4;
+      const double* wc = sWc + (e * NU + l) * 4;
+      sCv[(e * NU + l) * 4 + v] = Rv[0] * wc[0] + Rv[1] * wc[1] + Rv[2] * wc[2] + Rv[3] * wc[3];
+    }
+    __syncthreads();
+    // P8: nodal values of w_h for the predictor, and the new local time step
+    for (int item = tid; item < G * (Mc * 4 + 1); item += nth) {
+      const int e = item / (Mc * 4 + 1), k = item % (Mc * 4 + 1);
+      if (!sVal[e]) continue;
+      const int i = sI[e];
+      if (k < Mc * 4) {
+        const int s = k / 4, v = k % 4;
+        double acc = sEl[e * 16 + 6 + v];
+#pragma unroll
+        for (int l = 0; l < NU; ++l) acc += sBn[s * NU + l] * sCv[(e * NU + l) * 4 + v];
+        d.w0[((size_t)(base + e) * Mc + s) * 4 + v] = acc;
+      } else {
+        const long long ti = d.t[i];
+        long long tks = 0;
+        if (ti < T.T) {
+          double best = DBL_MAX;
+          bool bad = false;
+          for (int c = 0; c < 4; ++c) {
+            const double v = sDt[e * 4 + c];
+            if (v < 0.0) bad = true;
+            best = fmin(best, v);
+          }
+          if (bad || !(best > 0.0)) {
+            set_error(d.cnt, -3, i);
+            best = T.tick;
+          }
+          const double rt = floor(best / T.tick);
+          tks = rt > (double)(T.T - ti) ? T.T - ti : (long long)rt;
+          if (tks < 1) tks = 1;
+          atomicMin(&d.cnt->gts_min, tks);
+        }
+        d.dt[i] = tks;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_fill_counters_initial(Dev d) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     d.cnt->gts_min = LLONG_MAX;
     d.cnt->err_code = 0;
   }
+}
+
+// The reconstruction and predictor grids cover every element (the pre-
+// processing phase) or a few blocks per SM that loop over the ready list.
+template <int M>
+void launch_recon(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial) {
+  using S = ReconShape<M>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_recon_coop<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    attr = true;
+  }
+  const int need = (d.ne + S::G - 1) / S::G;
+  const int grid = initial ? need : std::min(need, nsm * 4);
+  k_recon_coop<M><<<grid, S::kThreads, S::bytes, s>>>(T, d, initial);
+}
+
+template <int M>
+void launch_predict(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial) {
+  using S = PredShape<M>;
+  const int need = (d.ne + S::G - 1) / S::G;
+  const int grid = initial ? need : std::min(need, nsm * 8);
+  k_predict_coop<M><<<grid, S::kThreads, 0, s>>>(T, d, initial, T.gts);
 }
 
 // ev (optional): kNumKernels + 1 events recorded on s around the launches,
@@ -796,16 +1355,16 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   mark(); k_flux<M><<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); k_commit<<<grid_w, kBlock, 0, s>>>(d);
-  mark(); k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 0);
-  mark(); k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 0, T.gts);
+  mark(); launch_recon<M>(T, d, nsm, s, 0);
+  mark(); launch_predict<M>(T, d, nsm, s, 0);
   mark();
 }
 
 template <int M>
 void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
   k_fill_counters_initial<<<1, 32, 0, s>>>(d);
-  k_recon<M><<<nsm * 4, 64, 0, s>>>(T, d, 1);
-  k_predict<M><<<nsm * 4, 64, 0, s>>>(T, d, 1, T.gts);
+  launch_recon<M>(T, d, nsm, s, 1);
+  launch_predict<M>(T, d, nsm, s, 1);
 }
 
 __global__ void k_dfma_chain(double* out, int iters, double a, double b) {
