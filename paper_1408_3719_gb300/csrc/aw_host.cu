@@ -601,6 +601,7 @@ int reset_sweep_state(aw_ctx* c) {
   CK(cudaMemsetAsync(d.elem_touch, 0, c->ne * sizeof(int), c->stream));
   CK(cudaMemsetAsync(d.node_moved, 0, c->nn * sizeof(int), c->stream));
   CK(cudaMemsetAsync(d.edge_act, 0, c->ned * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(d.cand_stamp, 0, c->ne * sizeof(int), c->stream));
   CK(cudaMemsetAsync(d.cnt, 0, sizeof(Counters), c->stream));
   return AW_OK;
 }
@@ -749,7 +750,8 @@ int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
       (rc = dalloc(c, &d.nXn, 2 * nn)) || (rc = dalloc(c, &d.ntn, nn)) || (rc = dalloc(c, &d.elem_ready, ne)) ||
       (rc = dalloc(c, &d.elem_touch, ne)) || (rc = dalloc(c, &d.node_moved, nn)) || (rc = dalloc(c, &d.edge_act, ned)) ||
       (rc = dalloc(c, &d.ready_list, ne)) || (rc = dalloc(c, &d.moved_list, nn)) || (rc = dalloc(c, &d.active_list, ned)) ||
-      (rc = dalloc(c, &d.touch_list, ne)) || (rc = dalloc(c, &d.G, 4 * ned)) || (rc = dalloc(c, &d.N, 4 * ned)) ||
+      (rc = dalloc(c, &d.touch_list, ne)) || (rc = dalloc(c, &d.cand_stamp, ne)) ||
+      (rc = dalloc(c, &d.cand_list, 2 * ne)) || (rc = dalloc(c, &d.G, 4 * ned)) || (rc = dalloc(c, &d.N, 4 * ned)) ||
       (rc = dalloc(c, &d.w0, ne * T.Mc * 4)) || (rc = dalloc(c, &d.cnt, 1)))
     return rc;
   CK(cudaMemsetAsync(d.elem_ready, 0, ne * sizeof(int), c->stream));
@@ -794,6 +796,12 @@ int aw_load_state(aw_ctx* c, const double* Q) {
   CK(cudaMemsetAsync(d.nt, 0, nn * sizeof(long long), c->stream));
   int rc0 = reset_sweep_state(c);
   if (rc0) return rc0;
+  {
+    int unf = (int)ne;
+    CK(cudaMemcpyAsync(&d.cnt->n_unfinished, &unf, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+
   launch_initial(c->tab, d, c->nsm, c->stream);
   CK(cudaGetLastError());
   int rc = sync_counters(c);
@@ -947,6 +955,14 @@ int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const doubl
   CK(cudaMemcpy(c->d.qhat, qhat, ne * c->tab.Nst * 4 * sizeof(double), cudaMemcpyDefault));
   int rc0 = reset_sweep_state(c);
   if (rc0) return rc0;
+  {
+    std::vector<long long> th(ne);
+    CK(cudaMemcpy(th.data(), t, ne * sizeof(long long), cudaMemcpyDefault));
+    int unf = 0;
+    for (long long v : th) unf += v < c->tab.T;
+    CK(cudaMemcpy(&c->d.cnt->n_unfinished, &unf, sizeof(int), cudaMemcpyHostToDevice));
+  }
+
   launch_products(c->tab, c->d, c->nsm, c->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));

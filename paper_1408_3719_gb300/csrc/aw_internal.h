@@ -92,6 +92,8 @@ struct Dev {
   int* moved_list;   // [nn]
   int* active_list;  // [ned]
   int* touch_list;   // [ne]
+  int* cand_stamp;   // [ne] epoch stamp when listed as a candidate
+  int* cand_list;    // [2][ne] ready candidates of the next sweep (double buffer)
   double* G;         // [ned*4]
   double* N;         // [ned*4]
   double* w0;        // [ne*Mc*4] nodal WENO values, by position in the ready list
@@ -104,7 +106,9 @@ struct Counters {
   int n_moved;
   int n_active;
   int n_touched;
-  int n_unfinished;
+  int n_unfinished;  // elements with t < t_end (maintained across sweeps)
+  int n_cand[2];
+  int cand_valid;    // 0: the next sweep checks every element
   int err_code;
   int err_elem;
   unsigned long long gcl_bits;   // max GCL residual (non-negative double bits)
@@ -115,7 +119,7 @@ struct Counters {
 };
 
 // kernel launchers (aw_kernels.cu)
-constexpr int kNumKernels = 9;  // launches per sweep
+constexpr int kNumKernels = 10;  // launches per sweep
 const char* kernel_name(int k);
 void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev);
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);

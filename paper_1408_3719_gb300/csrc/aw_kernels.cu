@@ -62,23 +62,31 @@ __global__ void k_begin(Dev d) {
     c->n_moved = 0;
     c->n_active = 0;
     c->n_touched = 0;
-    c->n_unfinished = 0;
+    c->n_cand[(c->epoch + 1) & 1] = 0;
     c->gts_min = LLONG_MAX;
     c->sweeps += 1;
   }
 }
 
+// Candidates: every element in the first sweep after a state is loaded;
+// afterwards the total stencils of the previous sweep's ready elements (the
+// criterion of any other element reads only unchanged times).
 __global__ void k_ready(Tab T, Dev d) {
   const int epoch = d.cnt->epoch;
+  const int par = epoch & 1;
+  const bool listed = d.cnt->cand_valid != 0 && !T.gts;
+  const int n_items = listed ? d.cnt->n_cand[par] : d.ne;
+  const int* clist = d.cand_list + (size_t)par * d.ne;
   const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < d.ne; base += stride) {
-    int i = base + threadIdx.x;
-    bool unfinished = false, ready = false;
+  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
+    const int q = base + threadIdx.x;
+    int i = -1;
+    bool ready = false;
     long long tn = 0;
-    if (i < d.ne) {
+    if (q < n_items) {
+      i = listed ? clist[q] : q;
       long long ti = d.t[i];
       if (ti < T.T) {
-        unfinished = true;
         tn = ti + d.dt[i];
         ready = true;
         for (int p = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; p < pe; ++p) {
@@ -88,8 +96,6 @@ __global__ void k_ready(Tab T, Dev d) {
         }
       }
     }
-    unsigned um = __ballot_sync(0xffffffffu, unfinished);
-    if ((threadIdx.x & 31) == 0 && um) atomicAdd(&d.cnt->n_unfinished, __popc(um));
     int slot = warp_append(&d.cnt->n_ready, ready);
     if (ready) {
       d.ready_list[slot] = i;
@@ -104,6 +110,28 @@ __global__ void k_ready(Tab T, Dev d) {
       }
     }
   }
+}
+
+// ready candidates of the next sweep: S^W of this sweep's ready elements
+__global__ void k_cand(Tab T, Dev d) {
+  if (T.gts) return;
+  const int epoch = d.cnt->epoch;
+  const int par = (epoch + 1) & 1;
+  const int n_ready = d.cnt->n_ready;
+  int* clist = d.cand_list + (size_t)par * d.ne;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = warp; q < n_ready; q += nwarps) {
+    const int i = d.ready_list[q];
+    for (int p = d.sw_ptr[i] + lane, pe = d.sw_ptr[i + 1]; p < pe; p += 32) {
+      const int j = d.sw[p];
+      if (atomicExch(&d.cand_stamp[j], epoch) != epoch) {
+        const int s2 = atomicAdd(&d.cnt->n_cand[par], 1);
+        clist[s2] = j;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->cand_valid = 1;
 }
 
 template <int M>
@@ -302,6 +330,111 @@ __global__ void __launch_bounds__(kBlock) k_flux(Tab T, Dev d) {
   }
 }
 
+// One lane per Gauss point: GS lanes (a power of two >= (M+1)^2) per swept
+// edge, the point contributions summed by a fixed xor-shuffle tree.
+template <int M>
+__global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
+  constexpr int Nt = M + 1, NP = Nt * Nt, GS = NP <= 4 ? 4 : 16;
+  const int epoch = d.cnt->epoch;
+  const int n_items = d.cnt->n_active * GS;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
+    const int item = base + threadIdx.x;
+    const int q = item / GS, pt = item % GS;
+    double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
+    int ed = -1;
+    if (item < n_items && pt < NP) {
+      ed = d.active_list[q];
+      const int gx = pt / Nt, gt = pt % Nt;
+      const int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
+      const int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
+      const int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
+      const bool ma = d.node_moved[a] == epoch, mb = d.node_moved[b] == epoch;
+      const int le1 = le == 2 ? 0 : le + 1;
+      const double sax = d.cshift[6 * L + 2 * le], say = d.cshift[6 * L + 2 * le + 1];
+      const double sbx = d.cshift[6 * L + 2 * le1], sby = d.cshift[6 * L + 2 * le1 + 1];
+      double P[4][3];
+      long long tk[4];
+      P[0][0] = d.nX[2 * a] + sax; P[0][1] = d.nX[2 * a + 1] + say; tk[0] = d.nt[a];
+      P[1][0] = d.nX[2 * b] + sbx; P[1][1] = d.nX[2 * b + 1] + sby; tk[1] = d.nt[b];
+      if (mb) { P[2][0] = d.nXn[2 * b] + sbx; P[2][1] = d.nXn[2 * b + 1] + sby; tk[2] = d.ntn[b]; }
+      else { P[2][0] = P[1][0]; P[2][1] = P[1][1]; tk[2] = tk[1]; }
+      if (ma) { P[3][0] = d.nXn[2 * a] + sax; P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
+      else { P[3][0] = P[0][0]; P[3][1] = P[0][1]; tk[3] = tk[0]; }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * T.tick;
+      const double chi = T.glx[gx], tau = T.glx[gt], wq = T.glw[gx] * T.glw[gt];
+      double dchi[3], dtau[3], n[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dchi[c] = (1.0 - tau) * (P[1][c] - P[0][c]) + tau * (P[2][c] - P[3][c]);
+        dtau[c] = (1.0 - chi) * (P[3][c] - P[0][c]) + chi * (P[2][c] - P[1][c]);
+      }
+      n[0] = dchi[1] * dtau[2] - dchi[2] * dtau[1];
+      n[1] = dchi[2] * dtau[0] - dchi[0] * dtau[2];
+      n[2] = dchi[0] * dtau[1] - dchi[1] * dtau[0];
+      const double tt = (1 - chi) * (1 - tau) * (double)tk[0] + chi * (1 - tau) * (double)tk[1] +
+                        chi * tau * (double)tk[2] + (1 - chi) * tau * (double)tk[3];
+      double qm[4], qp[4];
+      {
+        const long long tL = d.t[L], dtL = d.dt[L];
+        const double tl = dtL > 0 ? (tt - (double)tL) / (double)dtL : 0.0;
+        const double* c0 = d.trace + ((((size_t)L * 3 + le) * Nt + gx) * Nt) * 4;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double acc = c0[(Nt - 1) * 4 + v];
+#pragma unroll
+          for (int p = Nt - 2; p >= 0; --p) acc = acc * tl + c0[p * 4 + v];
+          qm[v] = acc;
+        }
+      }
+      if (R >= 0) {
+        const long long tR = d.t[R], dtR = d.dt[R];
+        const double tr = dtR > 0 ? (tt - (double)tR) / (double)dtR : 0.0;
+        const double* c0 = d.trace + ((((size_t)R * 3 + lr) * Nt + (Nt - 1 - gx)) * Nt) * 4;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double acc = c0[(Nt - 1) * 4 + v];
+#pragma unroll
+          for (int p = Nt - 2; p >= 0; --p) acc = acc * tr + c0[p * 4 + v];
+          qp[v] = acc;
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qp[v] = qm[v];
+        if (d.edge_bc[ed] == 0) {
+          const double nn = n[0] * n[0] + n[1] * n[1];
+          if (nn > 0.0) {
+            const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+            qp[1] = qm[1] - 2.0 * mn * n[0];
+            qp[2] = qm[2] - 2.0 * mn * n[1];
+          }
+        }
+      }
+      double F[4];
+      rusanov(T, qm, qp, n, F);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) G[v] = wq * F[v];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Nn[c] = wq * n[c];
+    }
+#pragma unroll
+    for (int off = GS / 2; off > 0; off >>= 1) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) G[v] += __shfl_xor_sync(0xffffffffu, G[v], off, GS);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Nn[c] += __shfl_xor_sync(0xffffffffu, Nn[c], off, GS);
+    }
+    if (pt == 0 && item < n_items) {
+      ed = d.active_list[q];
+      double* g = d.G + 4 * (size_t)ed;
+      double* nn = d.N + 4 * (size_t)ed;
+      g[0] = G[0]; g[1] = G[1]; g[2] = G[2]; g[3] = G[3];
+      nn[0] = Nn[0]; nn[1] = Nn[1]; nn[2] = Nn[2];
+    }
+  }
+}
+
 __global__ void k_update(Tab T, Dev d) {
   const int epoch = d.cnt->epoch;
   const int n_touched = d.cnt->n_touched;
@@ -353,6 +486,7 @@ __global__ void k_update(Tab T, Dev d) {
         atomicMax(&d.cnt->gcl_bits, (unsigned long long)__double_as_longlong(r));
         for (int k = 0; k < 6; ++k) d.X[6 * i + k] = Xn[k];
         d.t[i] += d.dt[i];
+        if (d.t[i] >= T.T) atomicSub(&d.cnt->n_unfinished, 1);
         d.count[i] += 1;
         if (!(Qn[0] > 0.0) || !(pressure(T, Qn) > 0.0) || !(Anew > 0.0)) set_error(d.cnt, -3, i);
       } else {
@@ -1352,9 +1486,10 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   mark(); k_ready<<<grid_all_e, kBlock, 0, s>>>(T, d);
   mark(); k_nodes<M><<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); k_edges<<<grid_all_ed, kBlock, 0, s>>>(d);
-  mark(); k_flux<M><<<grid_w, kBlock, 0, s>>>(T, d);
+  mark(); k_flux_grp<M><<<grid_w * 4, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); k_commit<<<grid_w, kBlock, 0, s>>>(d);
+  mark(); k_cand<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); launch_recon<M>(T, d, nsm, s, 0);
   mark(); launch_predict<M>(T, d, nsm, s, 0);
   mark();
@@ -1385,7 +1520,7 @@ __global__ void k_dfma_chain(double* out, int iters, double a, double b) {
 
 const char* kernel_name(int k) {
   static const char* names[kNumKernels] = {"k_begin", "k_ready", "k_nodes", "k_edges", "k_flux",
-                                           "k_update", "k_commit", "k_recon", "k_predict"};
+                                           "k_update", "k_commit", "k_cand", "k_recon", "k_predict"};
   return (k >= 0 && k < kNumKernels) ? names[k] : nullptr;
 }
 
