@@ -33,6 +33,7 @@ struct aw_ctx {
   long long ne = 0, nn = 0, ned = 0, sw_total = 0, u_total = 0;
   std::vector<double> xy0;
   double* d_corner0 = nullptr;  // element corners at t = 0
+  cudaGraphExec_t graph_exec = nullptr;  // one captured sweep
 };
 
 namespace {
@@ -308,7 +309,7 @@ struct HostMesh {
   std::vector<int> elem_edge, edge_nodes, edge_elem, nbr;
   std::vector<signed char> edge_loc, edge_bc, v2e_loc, node_type, sten_ok;
   std::vector<double> nbr_shift, node_n, u_shift;
-  std::vector<int> v2e_ptr, v2e, sw_ptr, sw, u_ptr, u_elem;
+  std::vector<int> v2e_ptr, v2e, sw_ptr, sw, u_ptr, u_elem, n2e_ptr, n2e;
   std::vector<unsigned char> sten;
 };
 
@@ -406,6 +407,17 @@ int preprocess(aw_ctx* c, HostMesh& m, const double* xy, int ne_s, int M) {
       m.edge_bc.push_back(j >= 0 ? (signed char)-1 : m.bc[3 * i + e]);
     }
   m.ned = ned;
+  // node -> incident edges
+  m.n2e_ptr.assign(nn + 1, 0);
+  for (int ed = 0; ed < ned; ++ed)
+    for (int q = 0; q < 2; ++q) m.n2e_ptr[m.edge_nodes[2 * ed + q] + 1]++;
+  std::partial_sum(m.n2e_ptr.begin(), m.n2e_ptr.end(), m.n2e_ptr.begin());
+  m.n2e.resize(2 * (size_t)ned);
+  {
+    std::vector<int> fill(m.n2e_ptr.begin(), m.n2e_ptr.end() - 1);
+    for (int ed = 0; ed < ned; ++ed)
+      for (int q = 0; q < 2; ++q) m.n2e[fill[m.edge_nodes[2 * ed + q]]++] = ed;
+  }
   // neighbour image offsets
   m.nbr_shift.assign(6 * (size_t)ne, 0.0);
   for (int i = 0; i < ne; ++i)
@@ -588,6 +600,10 @@ int dupload(aw_ctx* c, const T** out, const std::vector<T>& v) {
 
 void free_all(aw_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->have_mesh = c->have_state = false;
@@ -736,7 +752,8 @@ int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
       (rc = dupload(c, &d.edge_nodes, m.edge_nodes)) || (rc = dupload(c, &d.edge_elem, m.edge_elem)) ||
       (rc = dupload(c, &d.edge_loc, m.edge_loc)) || (rc = dupload(c, &d.edge_bc, m.edge_bc)) || (rc = dupload(c, &d.nbr, m.nbr)) ||
       (rc = dupload(c, &d.nbr_shift, m.nbr_shift)) || (rc = dupload(c, &d.v2e_ptr, m.v2e_ptr)) || (rc = dupload(c, &d.v2e, m.v2e)) ||
-      (rc = dupload(c, &d.v2e_loc, m.v2e_loc)) || (rc = dupload(c, &d.node_type, m.node_type)) ||
+      (rc = dupload(c, &d.v2e_loc, m.v2e_loc)) || (rc = dupload(c, &d.n2e_ptr, m.n2e_ptr)) ||
+      (rc = dupload(c, &d.n2e, m.n2e)) || (rc = dupload(c, &d.node_type, m.node_type)) ||
       (rc = dupload(c, &d.node_n, m.node_n)) || (rc = dupload(c, &d.sw_ptr, m.sw_ptr)) || (rc = dupload(c, &d.sw, m.sw)) ||
       (rc = dupload(c, &d.u_ptr, m.u_ptr)) || (rc = dupload(c, &d.u_elem, m.u_elem)) || (rc = dupload(c, &d.u_shift, m.u_shift)) ||
       (rc = dupload(c, &d.sten, m.sten)) || (rc = dupload(c, &d.sten_ok, m.sten_ok)))
@@ -814,15 +831,26 @@ int aw_load_state(aw_ctx* c, const double* Q) {
 
 static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  // Without profiling a sweep is one CUDA-graph launch (captured once per
+  // loaded mesh); with profiling the kernels are launched one by one with
+  // events between them.
+  if (!c->prof && !c->graph_exec) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    launch_sweep(c->tab, c->d, c->nsm, c->stream, nullptr);
+    CK(cudaStreamEndCapture(c->stream, &g));
+    CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+    cudaGraphDestroy(g);
+  }
   for (int64_t k = 0; k < n; ++k) {
-    cudaEvent_t* ev = nullptr;
     if (c->prof) {
       std::vector<cudaEvent_t> evs(kNumKernels + 1);
       for (auto& e : evs) CK(cudaEventCreate(&e));
       c->prof_pending.push_back(evs);
-      ev = c->prof_pending.back().data();
+      launch_sweep(c->tab, c->d, c->nsm, c->stream, c->prof_pending.back().data());
+    } else {
+      CK(cudaGraphLaunch(c->graph_exec, c->stream));
     }
-    launch_sweep(c->tab, c->d, c->nsm, c->stream, ev);
   }
   CK(cudaGetLastError());
   if (!wait) return AW_OK;

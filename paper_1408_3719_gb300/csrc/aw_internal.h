@@ -54,6 +54,8 @@ struct Dev {
   const signed char* edge_bc;   // [ned]
   const int* nbr;          // [ne*3]
   const double* nbr_shift; // [ne*6]
+  const int* n2e_ptr;      // [nn+1] node -> incident edges
+  const int* n2e;
   const int* v2e_ptr;      // [nn+1]
   const int* v2e;          // node -> element
   const signed char* v2e_loc;

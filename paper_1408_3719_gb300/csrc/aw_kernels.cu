@@ -72,41 +72,45 @@ __global__ void k_begin(Dev d) {
 // afterwards the total stencils of the previous sweep's ready elements (the
 // criterion of any other element reads only unchanged times).
 __global__ void k_ready(Tab T, Dev d) {
+  // one warp per candidate element, lanes over its total stencil
   const int epoch = d.cnt->epoch;
   const int par = epoch & 1;
   const bool listed = d.cnt->cand_valid != 0 && !T.gts;
   const int n_items = listed ? d.cnt->n_cand[par] : d.ne;
   const int* clist = d.cand_list + (size_t)par * d.ne;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
-    const int q = base + threadIdx.x;
-    int i = -1;
-    bool ready = false;
-    long long tn = 0;
-    if (q < n_items) {
-      i = listed ? clist[q] : q;
-      long long ti = d.t[i];
-      if (ti < T.T) {
-        tn = ti + d.dt[i];
-        ready = true;
-        for (int p = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; p < pe; ++p) {
-          int j = d.sw[p];
-          long long tj = d.t[j];
-          if (tj > tn || tn > tj + d.dt[j]) { ready = false; break; }
-        }
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n_items; q += nwarps) {
+    const int i = listed ? clist[q] : q;
+    const long long ti = d.t[i];
+    if (ti >= T.T) continue;
+    const long long tn = ti + d.dt[i];
+    bool ready = true;
+    for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += 32) {
+      const int p = base + lane;
+      bool bad = false;
+      if (p < pe) {
+        const int j = d.sw[p];
+        const long long tj = d.t[j];
+        bad = tj > tn || tn > tj + d.dt[j];
+      }
+      if (__any_sync(0xffffffffu, bad)) {
+        ready = false;
+        break;
       }
     }
-    int slot = warp_append(&d.cnt->n_ready, ready);
-    if (ready) {
+    if (!ready) continue;
+    if (lane == 0) {
+      const int slot = atomicAdd(&d.cnt->n_ready, 1);
       d.ready_list[slot] = i;
       d.elem_ready[i] = epoch;
-      for (int k = 0; k < 3; ++k) {
-        int n = d.tri[3 * i + k];
-        d.ntn[n] = tn;
-        if (atomicExch(&d.node_moved[n], epoch) != epoch) {
-          int s2 = atomicAdd(&d.cnt->n_moved, 1);
-          d.moved_list[s2] = n;
-        }
+    }
+    if (lane < 3) {
+      const int n = d.tri[3 * i + lane];
+      d.ntn[n] = tn;
+      if (atomicExch(&d.node_moved[n], epoch) != epoch) {
+        const int s2 = atomicAdd(&d.cnt->n_moved, 1);
+        d.moved_list[s2] = n;
       }
     }
   }
@@ -184,24 +188,90 @@ __global__ void k_nodes(Tab T, Dev d) {
   }
 }
 
-__global__ void k_edges(Dev d) {
-  const int epoch = d.cnt->epoch;
+// Node solver with 8 lanes per moved node, one Voronoi element per lane
+// (strided), partial sums combined by a fixed xor-shuffle tree.
+template <int M>
+__global__ void k_nodes_grp(Tab T, Dev d) {
+  constexpr int Nt = M + 1, GS = 8;
+  const int n_items = d.cnt->n_moved * GS;
   const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < d.ned; base += stride) {
-    int ed = base + threadIdx.x;
-    bool act = false;
-    if (ed < d.ned) {
-      int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
-      act = d.node_moved[a] == epoch || d.node_moved[b] == epoch;
+  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
+    const int item = base + threadIdx.x;
+    const int q = item / GS, lane = item % GS;
+    double num0 = 0.0, num1 = 0.0, den = 0.0;
+    int n = -1;
+    if (item < n_items) {
+      n = d.moved_list[q];
+      const long long tk0 = d.nt[n], tk1 = d.ntn[n];
+      for (int p = d.v2e_ptr[n] + lane, pe = d.v2e_ptr[n + 1]; p < pe; p += GS) {
+        const int j = d.v2e[p];
+        const int k = d.v2e_loc[p];
+        const double mu = d.Q[4 * (size_t)j] * area6(d.X + 6 * (size_t)j);
+        double D0 = 0.0, D1 = 0.0;
+        const long long dtj = d.dt[j];
+        if (dtj > 0) {
+          const long long tj = d.t[j];
+          const double idtj = 1.0 / (double)dtj;
+          const double tau0 = (double)(tk0 - tj) * idtj;
+          const double tau1 = (double)(tk1 - tj) * idtj;
+          const double* vd = d.vdisp + ((size_t)j * 3 + k) * 2 * Nt;
+          double a0 = vd[Nt - 1], a1 = vd[Nt - 1], b0 = vd[2 * Nt - 1], b1 = vd[2 * Nt - 1];
+#pragma unroll
+          for (int pp = Nt - 2; pp >= 0; --pp) {
+            a0 = a0 * tau0 + vd[pp];
+            a1 = a1 * tau1 + vd[pp];
+            b0 = b0 * tau0 + vd[Nt + pp];
+            b1 = b1 * tau1 + vd[Nt + pp];
+          }
+          const double dts = (double)dtj * T.tick;
+          D0 = dts * (a1 * tau1 - a0 * tau0);
+          D1 = dts * (b1 * tau1 - b0 * tau0);
+        }
+        num0 += mu * D0;
+        num1 += mu * D1;
+        den += mu;
+      }
     }
-    int slot = warp_append(&d.cnt->n_active, act);
-    if (act) {
+#pragma unroll
+    for (int off = GS / 2; off > 0; off >>= 1) {
+      num0 += __shfl_xor_sync(0xffffffffu, num0, off, GS);
+      num1 += __shfl_xor_sync(0xffffffffu, num1, off, GS);
+      den += __shfl_xor_sync(0xffffffffu, den, off, GS);
+    }
+    if (item < n_items && lane == 0) {
+      const double iden = 1.0 / den;
+      double D0 = num0 * iden, D1 = num1 * iden;
+      const int ty = d.node_type[n];
+      if (ty == 1) {
+        const double nx = d.node_n[2 * n], ny = d.node_n[2 * n + 1];
+        const double dn = D0 * nx + D1 * ny;
+        D0 -= dn * nx;
+        D1 -= dn * ny;
+      } else if (ty == 2) {
+        D0 = D1 = 0.0;
+      }
+      d.nXn[2 * n] = d.nX[2 * n] + D0;
+      d.nXn[2 * n + 1] = d.nX[2 * n + 1] + D1;
+    }
+  }
+}
+
+// edges with a moved endpoint, found through the moved nodes' incident edges
+__global__ void k_edges(Dev d) {
+  // 8 lanes per moved node, one incident edge per lane (strided)
+  const int epoch = d.cnt->epoch;
+  const int n_items = d.cnt->n_moved * 8;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < n_items; item += gridDim.x * blockDim.x) {
+    const int n = d.moved_list[item >> 3];
+    for (int p = d.n2e_ptr[n] + (item & 7), pe = d.n2e_ptr[n + 1]; p < pe; p += 8) {
+      const int ed = d.n2e[p];
+      if (atomicExch(&d.edge_act[ed], epoch) == epoch) continue;
+      const int slot = atomicAdd(&d.cnt->n_active, 1);
       d.active_list[slot] = ed;
-      d.edge_act[ed] = epoch;
-      for (int q = 0; q < 2; ++q) {
-        int e = d.edge_elem[2 * ed + q];
+      for (int k = 0; k < 2; ++k) {
+        const int e = d.edge_elem[2 * ed + k];
         if (e >= 0 && atomicExch(&d.elem_touch[e], epoch) != epoch) {
-          int s2 = atomicAdd(&d.cnt->n_touched, 1);
+          const int s2 = atomicAdd(&d.cnt->n_touched, 1);
           d.touch_list[s2] = e;
         }
       }
@@ -218,10 +288,11 @@ __device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const do
   double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
   double pm = (T.gamma - 1.0) * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
   double pp = (T.gamma - 1.0) * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
-  double nxy = sqrt(n[0] * n[0] + n[1] * n[1]);
-  double cm = sqrt(T.gamma * pm * rim), cp = sqrt(T.gamma * pp * rip);
+  // c |n_xy| as one square root per side
+  double nn2 = n[0] * n[0] + n[1] * n[1];
+  double cmn = sqrt(T.gamma * pm * rim * nn2), cpn = sqrt(T.gamma * pp * rip * nn2);
   double wm = um * n[0] + vm * n[1] + n[2], wp = up * n[0] + vp * n[1] + n[2];
-  double sm = fabs(wm) + cm * nxy, sp = fabs(wp) + cp * nxy;
+  double sm = fabs(wm) + cmn, sp = fabs(wp) + cpn;
   double smax = fmax(sm, sp);
   // F~.n = f n_x + g n_y + q n_t = q (v.n_xy + n_t) + p (0, n_x, n_y, v.n_xy)
   double vnm = um * n[0] + vm * n[1], vnp = up * n[0] + vp * n[1];
@@ -940,8 +1011,12 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
   for (int k = threadIdx.x; k < 3 * Nt * Mc; k += blockDim.x) sTr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc] = T.Tr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc];
   const int n_ready = initial ? d.ne : d.cnt->n_ready;
   const long long gmin = d.cnt->gts_min;
-  const int e = threadIdx.x / Nst, l = threadIdx.x % Nst;
-  const int t = l / Mc, s = l % Mc;
+  // thread -> (time slice t, element e, lattice node s): the tau = 0 nodes of
+  // all G elements are the first threads, so the warps that only hold them go
+  // quiet where the tau = 0 work is cheap or already done
+  const int t = threadIdx.x / (G * Mc), rr = threadIdx.x % (G * Mc);
+  const int e = t < Nt ? rr / Mc : G;
+  const int s = rr % Mc, l = t * Mc + s;
   const double gm1 = T.gamma - 1.0;
   for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
     const int pos = base + e;
@@ -970,8 +1045,15 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
     }
     __syncthreads();
     const double idt = work ? 1.0 / dts : 0.0;
+    // tau = 0 node: its data and spatial metric never change, so after the
+    // first iteration only the xi_t, eta_t terms of P are recomputed there
+    double c_fs[4] = {0, 0, 0, 0}, c_Qx[4] = {0, 0, 0, 0}, c_Qe[4] = {0, 0, 0, 0};
+    double c_xix = 0, c_xiy = 0, c_etx = 0, c_ety = 0;
     for (int it = 0; it < T.nit; ++it) {
-      if (work) {  // nodal fluxes and mesh velocity at the own node
+      // Iteration 0 starts from w_h at every slice and a static geometry, so P
+      // is the same on every slice: it is computed on the tau = 0 slice only.
+      const bool full = work && (it == 0 ? t == 0 : t > 0);
+      if (full) {  // nodal fluxes and mesh velocity at the own node
         const double* q = sq[e][l];
         const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
         const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
@@ -981,7 +1063,7 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
         sV[e][l][1] = T.eulerian ? 0.0 : v;
       }
       __syncthreads();
-      if (work) {  // P at the own node (eq. pdef) with the isoparametric metric (eq. Jac)
+      if (full) {  // P at the own node (eq. pdef) with the isoparametric metric (eq. Jac)
         double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
         double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
         double xx = 0, xe = 0, yx = 0, ye = 0;
@@ -1000,19 +1082,43 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
           yx += a * sx[e][lr][1]; ye += b * sx[e][lr][1];
         }
         double xt = 0.0, yt = 0.0;
+        if (it > 0) {
 #pragma unroll
-        for (int u = 0; u < Nt; ++u) {
-          xt += sDtau[t][u] * sx[e][u * Mc + s][0];
-          yt += sDtau[t][u] * sx[e][u * Mc + s][1];
+          for (int u = 0; u < Nt; ++u) {
+            xt += sDtau[t][u] * sx[e][u * Mc + s][0];
+            yt += sDtau[t][u] * sx[e][u * Mc + s][1];
+          }
+          xt *= idt;
+          yt *= idt;
         }
-        xt *= idt;
-        yt *= idt;
         const double idet = 1.0 / (xx * ye - xe * yx);
         const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
         const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          sP[e][l][v] = -(Qx[v] * xit + Qe[v] * ett + fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
+        for (int v = 0; v < 4; ++v) {
+          const double fs = -(fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
+          sP[e][l][v] = fs - (Qx[v] * xit + Qe[v] * ett);
+          if (t == 0) {
+            c_fs[v] = fs;
+            c_Qx[v] = Qx[v];
+            c_Qe[v] = Qe[v];
+          }
+        }
+        if (t == 0) {
+          c_xix = xix; c_xiy = xiy; c_etx = etx; c_ety = ety;
+        }
+      } else if (work && t == 0) {  // tau = 0 node after the first iteration
+        double xt = 0.0, yt = 0.0;
+#pragma unroll
+        for (int u = 0; u < Nt; ++u) {
+          xt += sDtau[0][u] * sx[e][u * Mc + s][0];
+          yt += sDtau[0][u] * sx[e][u * Mc + s][1];
+        }
+        xt *= idt;
+        yt *= idt;
+        const double xit = -(c_xix * xt + c_xiy * yt), ett = -(c_etx * xt + c_ety * yt);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sP[e][l][v] = c_fs[v] - (c_Qx[v] * xit + c_Qe[v] * ett);
       }
       __syncthreads();
       if (work && t > 0) {  // K_tau qhat = dt M P with the tau = 0 dofs known (eqs. CGfinal, newVertPos)
@@ -1020,14 +1126,14 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
         for (int v = 0; v < 4; ++v) {
           double acc = 0.0;
 #pragma unroll
-          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sP[e][u * Mc + s][v];
+          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sP[e][(it == 0 ? 0 : u) * Mc + s][v];
           sq[e][l][v] = sq[e][s][v] + dts * acc;
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           double acc = 0.0;
 #pragma unroll
-          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sV[e][u * Mc + s][c];
+          for (int u = 0; u < Nt; ++u) acc += sB[t - 1][u] * sV[e][(it == 0 ? 0 : u) * Mc + s][c];
           sx[e][l][c] = sx[e][s][c] + dts * acc;
         }
       }
@@ -1274,11 +1380,12 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
       sNrm[(e * kNSten + s) * NN + q] = acc;
     }
     __syncthreads();
-    // P3: Cholesky factorisation and the two triangular solves per stencil
+    // P3a: Cholesky factorisation N = L L^T per stencil, in place; the
+    // diagonal keeps 1 / L_aa
     for (int item = tid; item < G * kNSten; item += nth) {
       const int e = item / kNSten, s = item % kNSten;
       if (!sVal[e] || !sOk[e * kNSten + s]) continue;
-      const double* nm = sNrm + (size_t)item * NN;
+      double* nm = sNrm + (size_t)item * NN;
       double L[NU][NU];
 #pragma unroll
       for (int a = 0; a < NU; ++a)
@@ -1289,8 +1396,8 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
         double dd = L[a][a];
 #pragma unroll
         for (int k = 0; k < a; ++k) dd -= L[a][k] * L[a][k];
-        const double la = sqrt(dd), il = 1.0 / la;
-        L[a][a] = la;
+        const double il = 1.0 / sqrt(dd);
+        L[a][a] = il;
 #pragma unroll
         for (int b = a + 1; b < NU; ++b) {
           double v = L[b][a];
@@ -1299,25 +1406,35 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
           L[b][a] = v * il;
         }
       }
-      double* cs = sC + (size_t)item * NU * 4;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        double y[NU];
+      for (int a = 0; a < NU; ++a)
 #pragma unroll
-        for (int a = 0; a < NU; ++a) {
-          double acc = nm[NL + a * 4 + v];
+        for (int b = 0; b <= a; ++b) nm[a * (a + 1) / 2 + b] = L[a][b];
+    }
+    __syncthreads();
+    // P3b: the two triangular solves, one right-hand side per item
+    for (int item = tid; item < G * kNSten * 4; item += nth) {
+      const int es = item / 4, v = item % 4, e = es / kNSten, s = es % kNSten;
+      if (!sVal[e] || !sOk[e * kNSten + s]) continue;
+      const double* nm = sNrm + (size_t)es * NN;
+      double* cs = sC + (size_t)es * NU * 4;
+      double y[NU];
 #pragma unroll
-          for (int k = 0; k < a; ++k) acc -= L[a][k] * y[k];
-          y[a] = acc / L[a][a];
-        }
+      for (int a = 0; a < NU; ++a) {
+        double acc = nm[NL + a * 4 + v];
 #pragma unroll
-        for (int a = NU - 1; a >= 0; --a) {
-          double acc = y[a];
-#pragma unroll
-          for (int k = a + 1; k < NU; ++k) acc -= L[k][a] * cs[k * 4 + v];
-          cs[a * 4 + v] = acc / L[a][a];
-        }
+        for (int k = 0; k < a; ++k) acc -= nm[a * (a + 1) / 2 + k] * y[k];
+        y[a] = acc * nm[a * (a + 1) / 2 + a];
       }
+#pragma unroll
+      for (int a = NU - 1; a >= 0; --a) {
+        double acc = y[a];
+#pragma unroll
+        for (int k = a + 1; k < NU; ++k) acc -= nm[k * (k + 1) / 2 + a] * y[k];
+        y[a] = acc * nm[a * (a + 1) / 2 + a];
+      }
+#pragma unroll
+      for (int a = 0; a < NU; ++a) cs[a * 4 + v] = y[a];
     }
     __syncthreads();
     // P4: characteristic fields of dF/dQ.n, n along the density gradient of
@@ -1478,14 +1595,13 @@ void launch_predict(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int ini
 template <int M>
 void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev) {
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
-  const int grid_all_ed = (d.ned + kBlock - 1) / kBlock;
   const int grid_w = nsm * 8;
   int k = 0;
   auto mark = [&]() { if (ev) cudaEventRecord(ev[k++], s); };
   mark(); k_begin<<<1, 32, 0, s>>>(d);
-  mark(); k_ready<<<grid_all_e, kBlock, 0, s>>>(T, d);
-  mark(); k_nodes<M><<<grid_w, kBlock, 0, s>>>(T, d);
-  mark(); k_edges<<<grid_all_ed, kBlock, 0, s>>>(d);
+  mark(); k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
+  mark(); k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
+  mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
   mark(); k_flux_grp<M><<<grid_w * 4, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); k_commit<<<grid_w, kBlock, 0, s>>>(d);
