@@ -77,6 +77,19 @@ int aw_load_mesh(aw_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris,
                  const int32_t* tri, const int8_t* bc, const int8_t* shift,
                  const double* period);
 
+/* Load n_inst independent, non-periodic meshes as one batch: every sweep then
+ * advances all instances together (their stencils never meet, so each
+ * instance evolves exactly as it would alone).  Instance k owns nodes
+ * [node_offsets[k], node_offsets[k+1]) and triangles [tri_offsets[k],
+ * tri_offsets[k+1]) of the concatenated xy [n_nodes][2], tri [n_tris][3] and
+ * bc [n_tris][3]; tri holds node indices local to the instance; offsets start
+ * at 0 (n_inst + 1 entries each).  t_end [n_inst] is the final time of each
+ * instance; its tick is t_end[k] / 2^time_quantum_log2 (cfg.t_end is not
+ * used).  aw_load_state then takes the concatenated averages.  Errors as
+ * aw_load_mesh. */
+int aw_load_batch(aw_ctx* ctx, int n_inst, const int64_t* node_offsets, const int64_t* tri_offsets,
+                  const double* t_end, const double* xy, const int32_t* tri, const int8_t* bc);
+
 /* Pre-processing phase of Sec. 2.6: cell averages Q [n_tris][4] at t = 0,
  * first WENO reconstruction, local time steps (eq. timestep), predictor;
  * all node and element times set to 0.  NONPHYSICAL if rho or p <= 0. */

@@ -1237,6 +1237,16 @@ static void predictor(const oc_ctx* c, const double* X, double dtsec, const doub
 }
 
 /* WENO polynomial at the lattice nodes, then the predictor of element i */
+/* R11 positivity safeguards (not in the paper).  (a) If the WENO polynomial
+   has a density or pressure below 1e-8 of the cell's own value at a lattice
+   node, its non-constant part is scaled by the largest theta in [0,1] that
+   keeps every node above that floor (the scaling of Zhang and Shu, 2010; for
+   the pressure, which is concave in the conserved variables, theta comes from
+   the chord bound p(Q + theta (w - Q)) >= (1 - theta) p(Q) + theta p(w)).
+   (b) If the predictor ends with a non-positive density or pressure at a
+   space-time node, the element keeps w_h at every time slice instead. */
+static int physical(const oc_ctx* c, const double* q) { return q[0] > 0.0 && pressure(c, q) > 0.0; }
+
 static void element_predictor(const oc_ctx* c, int64_t i, const double* w) {
   double w0[MAXMC * 4];
   for (int s = 0; s < c->Mc; ++s) {
@@ -1248,7 +1258,36 @@ static void element_predictor(const oc_ctx* c, int64_t i, const double* w) {
       w0[s * 4 + v] = acc;
     }
   }
-  predictor(c, c->X + 6 * i, (double)c->dt[i] * c->tick, w0, c->qhat + (size_t)i * c->Nst * 4);
+  const double* Qi = c->Q + 4 * i;
+  const double rho_min = 1e-8 * Qi[0], p_i = pressure(c, Qi), p_min = 1e-8 * p_i;
+  for (int pass = 0; pass < 2; ++pass) {  /* density first, then pressure */
+    double theta = 1.0;
+    for (int s = 0; s < c->Mc; ++s) {
+      const double* ws = w0 + 4 * s;
+      if (pass == 0 && ws[0] < rho_min) {
+        double th = (Qi[0] - rho_min) / (Qi[0] - ws[0]);
+        if (th < theta) theta = th;
+      }
+      if (pass == 1) {
+        double ps = pressure(c, ws);
+        if (ps < p_min) {
+          double th = (p_i - p_min) / (p_i - ps);
+          if (th < theta) theta = th;
+        }
+      }
+    }
+    if (theta < 1.0)
+      for (int s = 0; s < c->Mc; ++s)
+        for (int v = 0; v < 4; ++v) w0[s * 4 + v] = Qi[v] + theta * (w0[s * 4 + v] - Qi[v]);
+  }
+  double* qh = c->qhat + (size_t)i * c->Nst * 4;
+  predictor(c, c->X + 6 * i, (double)c->dt[i] * c->tick, w0, qh);
+  int ok = 1;
+  for (int l = 0; l < c->Nst && ok; ++l) ok = physical(c, qh + 4 * l);
+  if (!ok)
+    for (int t = 0; t < c->Nt; ++t)
+      for (int s = 0; s < c->Mc; ++s)
+        for (int v = 0; v < 4; ++v) qh[(t * c->Mc + s) * 4 + v] = w0[s * 4 + v];
 }
 
 /* ------------------------------------------------------------------------

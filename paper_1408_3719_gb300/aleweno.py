@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libaleweno.so")
 AW_ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "BAD_MESH", -3: "NONPHYSICAL", -4: "DEADLOCK", -5: "TIMEOUT",
              -6: "CUDA", -7: "STATE"}
 
-EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load_state", "aw_lts_sweep",
+EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load_batch", "aw_load_state",
+            "aw_lts_sweep",
             "aw_gts_step", "aw_advance_to", "aw_enqueue_sweeps", "aw_sync", "aw_get_state", "aw_get_nodes",
             "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
             "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_profile_enable", "aw_profile_read",
@@ -59,6 +60,7 @@ def load(path: str | None = None):
             lib.aw_last_error.argtypes = [P]
             lib.aw_last_error.restype = C.c_char_p
             lib.aw_load_mesh.argtypes = [P, i64, P, i64, P, P, P, P]
+            lib.aw_load_batch.argtypes = [P, C.c_int, P, P, P, P, P, P]
             lib.aw_load_state.argtypes = [P, P]
             lib.aw_lts_sweep.argtypes = [P, C.POINTER(i64)]
             lib.aw_gts_step.argtypes = [P, C.POINTER(i64)]
@@ -147,6 +149,25 @@ class Solver:
                                           _ptr(shift), _ptr(period)))
         self.n_tris = tri.shape[0]
         self.n_nodes = xy.shape[0]
+
+    def load_batch(self, meshes, t_ends):
+        """Independent non-periodic meshes advanced together (see aw_load_batch)."""
+        node_off = np.zeros(len(meshes) + 1, np.int64)
+        tri_off = np.zeros(len(meshes) + 1, np.int64)
+        for k, m in enumerate(meshes):
+            if m.get("period") is not None:
+                raise ValueError("batched meshes must not be periodic")
+            node_off[k + 1] = node_off[k] + m["xy"].shape[0]
+            tri_off[k + 1] = tri_off[k] + m["tri"].shape[0]
+        xy = np.ascontiguousarray(np.concatenate([m["xy"] for m in meshes]), dtype=np.float64)
+        tri = np.ascontiguousarray(np.concatenate([m["tri"] for m in meshes]), dtype=np.int32)
+        bc = np.ascontiguousarray(np.concatenate([m["bc"] for m in meshes]), dtype=np.int8)
+        te = np.ascontiguousarray(t_ends, dtype=np.float64)
+        self._check(self.lib.aw_load_batch(self.h, len(meshes), _ptr(node_off), _ptr(tri_off), _ptr(te), _ptr(xy),
+                                           _ptr(tri), _ptr(bc)))
+        self.n_tris = int(tri_off[-1])
+        self.n_nodes = int(node_off[-1])
+        self.node_offsets, self.tri_offsets = node_off, tri_off
 
     def load_state(self, Q):
         if not hasattr(Q, "data_ptr"):

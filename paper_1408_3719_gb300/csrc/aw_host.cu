@@ -33,6 +33,7 @@ struct aw_ctx {
   long long ne = 0, nn = 0, ned = 0, sw_total = 0, u_total = 0;
   std::vector<double> xy0;
   double* d_corner0 = nullptr;  // element corners at t = 0
+  std::vector<double> etick_h, ntick_h;  // seconds per tick of each element / node
   cudaGraphExec_t graph_exec = nullptr;  // one captured sweep
 };
 
@@ -710,8 +711,10 @@ void aw_destroy(aw_ctx* c) {
 
 const char* aw_last_error(const aw_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri,
-                 const int8_t* bc, const int8_t* shift, const double* period) {
+// Shared by aw_load_mesh and aw_load_batch; etick (host, may be NULL for a
+// uniform tick) gives each element's seconds per tick.
+static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri,
+                       const int8_t* bc, const int8_t* shift, const double* period, const double* etick) {
   if (!c) return AW_ERR_INVALID_ARG;
   if (n_nodes < 3 || n_tris < 1 || !xy || !tri || !bc || n_nodes > (1LL << 30) || n_tris > (1LL << 29))
     return set_err(c, AW_ERR_INVALID_ARG, "bad mesh sizes or null arrays");
@@ -758,6 +761,12 @@ int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
       (rc = dupload(c, &d.u_ptr, m.u_ptr)) || (rc = dupload(c, &d.u_elem, m.u_elem)) || (rc = dupload(c, &d.u_shift, m.u_shift)) ||
       (rc = dupload(c, &d.sten, m.sten)) || (rc = dupload(c, &d.sten_ok, m.sten_ok)))
     return rc;
+  c->etick_h.assign(m.ne, T.tick);
+  if (etick) std::copy(etick, etick + m.ne, c->etick_h.begin());
+  c->ntick_h.assign(m.nn, T.tick);
+  for (int i = 0; i < m.ne; ++i)
+    for (int k = 0; k < 3; ++k) c->ntick_h[m.tri[3 * i + k]] = c->etick_h[i];
+  if ((rc = dupload(c, &d.etick, c->etick_h))) return rc;
   const size_t ne = m.ne, nn = m.nn, ned = m.ned;
   if ((rc = dalloc(c, &d.Q, 4 * ne)) || (rc = dalloc(c, &d.QM, 4 * ne)) || (rc = dalloc(c, &d.HM, 4 * ne)) ||
       (rc = dalloc(c, &d.t, ne)) || (rc = dalloc(c, &d.dt, ne)) || (rc = dalloc(c, &d.X, 6 * ne)) ||
@@ -787,6 +796,41 @@ int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
   if ((rc = dalloc(c, &c->d_corner0, 6 * ne))) return rc;
   CK(cudaMemcpy(c->d_corner0, m.corner0.data(), 6 * ne * sizeof(double), cudaMemcpyHostToDevice));
   return AW_OK;
+}
+
+int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri,
+                 const int8_t* bc, const int8_t* shift, const double* period) {
+  return load_common(c, n_nodes, xy, n_tris, tri, bc, shift, period, nullptr);
+}
+
+int aw_load_batch(aw_ctx* c, int n_inst, const int64_t* node_offsets, const int64_t* tri_offsets,
+                  const double* t_end, const double* xy, const int32_t* tri, const int8_t* bc) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (n_inst < 1 || !node_offsets || !tri_offsets || !t_end || !xy || !tri || !bc)
+    return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: null arrays or no instance");
+  std::vector<int64_t> no(node_offsets, node_offsets + n_inst + 1), to(tri_offsets, tri_offsets + n_inst + 1);
+  if (no[0] != 0 || to[0] != 0) return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: offsets must start at 0");
+  for (int k = 0; k < n_inst; ++k)
+    if (no[k + 1] <= no[k] || to[k + 1] <= to[k] || !(t_end[k] > 0))
+      return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: instance %d is empty or has t_end <= 0", k);
+  const int64_t nn = no[n_inst], ne = to[n_inst];
+  std::vector<int32_t> gtri(3 * ne);
+  if (cudaMemcpy(gtri.data(), tri, gtri.size() * sizeof(int32_t), cudaMemcpyDefault) != cudaSuccess)
+    return set_err(c, AW_ERR_CUDA, "aw_load_batch: copying tri failed");
+  std::vector<double> et(ne);
+  for (int k = 0; k < n_inst; ++k) {
+    const double tick = std::ldexp(t_end[k], -c->cfg.time_quantum_log2);
+    for (int64_t i = to[k]; i < to[k + 1]; ++i) {
+      et[i] = tick;
+      for (int q = 0; q < 3; ++q) {
+        const int64_t v = gtri[3 * i + q];
+        if (v < 0 || v >= no[k + 1] - no[k])
+          return set_err(c, AW_ERR_BAD_MESH, "aw_load_batch: instance %d has a node index out of range", k);
+        gtri[3 * i + q] = (int32_t)(v + no[k]);
+      }
+    }
+  }
+  return load_common(c, nn, xy, ne, gtri.data(), bc, nullptr, nullptr, et.data());
 }
 
 int aw_load_state(aw_ctx* c, const double* Q) {
@@ -918,7 +962,7 @@ int aw_get_state(aw_ctx* c, double* Q, double* t_elem) {
     std::vector<long long> t(c->ne);
     CK(cudaMemcpy(t.data(), c->d.t, c->ne * sizeof(long long), cudaMemcpyDeviceToHost));
     std::vector<double> td(c->ne);
-    for (long long i = 0; i < c->ne; ++i) td[i] = (double)t[i] * c->tab.tick;
+    for (long long i = 0; i < c->ne; ++i) td[i] = (double)t[i] * c->etick_h[i];
     CK(cudaMemcpy(t_elem, td.data(), c->ne * sizeof(double), cudaMemcpyDefault));
   }
   return AW_OK;
@@ -933,7 +977,7 @@ int aw_get_nodes(aw_ctx* c, double* xy, double* t_node) {
     std::vector<long long> t(c->nn);
     CK(cudaMemcpy(t.data(), c->d.nt, c->nn * sizeof(long long), cudaMemcpyDeviceToHost));
     std::vector<double> td(c->nn);
-    for (long long i = 0; i < c->nn; ++i) td[i] = (double)t[i] * c->tab.tick;
+    for (long long i = 0; i < c->nn; ++i) td[i] = (double)t[i] * c->ntick_h[i];
     CK(cudaMemcpy(t_node, td.data(), c->nn * sizeof(double), cudaMemcpyDefault));
   }
   return AW_OK;

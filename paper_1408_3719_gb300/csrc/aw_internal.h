@@ -68,6 +68,7 @@ struct Dev {
   const double* u_shift;   // [2 per entry]
   const unsigned char* sten;  // [ne][7][n_e] local member index (0 = i itself)
   const signed char* sten_ok; // [ne*7]
+  const double* etick;     // [ne] seconds per tick of the element's instance
   // element state
   double* Q;     // [ne*4]
   double* QM;    // [ne*4]

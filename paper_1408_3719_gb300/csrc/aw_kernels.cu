@@ -138,56 +138,6 @@ __global__ void k_cand(Tab T, Dev d) {
   if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->cand_valid = 1;
 }
 
-template <int M>
-__global__ void k_nodes(Tab T, Dev d) {
-  constexpr int Nt = M + 1;
-  const int n_moved = d.cnt->n_moved;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_moved; q += gridDim.x * blockDim.x) {
-    int n = d.moved_list[q];
-    long long tk0 = d.nt[n], tk1 = d.ntn[n];
-    double num0 = 0.0, num1 = 0.0, den = 0.0;
-    for (int p = d.v2e_ptr[n], pe = d.v2e_ptr[n + 1]; p < pe; ++p) {
-      int j = d.v2e[p];
-      int k = d.v2e_loc[p];
-      double mu = d.Q[4 * j] * area6(d.X + 6 * j);
-      double D0 = 0.0, D1 = 0.0;
-      long long dtj = d.dt[j];
-      if (dtj > 0) {
-        long long tj = d.t[j];
-        double tau0 = (double)(tk0 - tj) / (double)dtj;
-        double tau1 = (double)(tk1 - tj) / (double)dtj;
-        const double* vd = d.vdisp + ((size_t)j * 3 + k) * 2 * Nt;
-        double a0 = vd[Nt - 1], a1 = vd[Nt - 1], b0 = vd[2 * Nt - 1], b1 = vd[2 * Nt - 1];
-#pragma unroll
-        for (int pp = Nt - 2; pp >= 0; --pp) {
-          a0 = a0 * tau0 + vd[pp];
-          a1 = a1 * tau1 + vd[pp];
-          b0 = b0 * tau0 + vd[Nt + pp];
-          b1 = b1 * tau1 + vd[Nt + pp];
-        }
-        double dts = (double)dtj * T.tick;
-        D0 = dts * (a1 * tau1 - a0 * tau0);
-        D1 = dts * (b1 * tau1 - b0 * tau0);
-      }
-      num0 += mu * D0;
-      num1 += mu * D1;
-      den += mu;
-    }
-    double D0 = num0 / den, D1 = num1 / den;
-    int ty = d.node_type[n];
-    if (ty == 1) {
-      double nx = d.node_n[2 * n], ny = d.node_n[2 * n + 1];
-      double dn = D0 * nx + D1 * ny;
-      D0 -= dn * nx;
-      D1 -= dn * ny;
-    } else if (ty == 2) {
-      D0 = D1 = 0.0;
-    }
-    d.nXn[2 * n] = d.nX[2 * n] + D0;
-    d.nXn[2 * n + 1] = d.nX[2 * n + 1] + D1;
-  }
-}
-
 // Node solver with 8 lanes per moved node, one Voronoi element per lane
 // (strided), partial sums combined by a fixed xor-shuffle tree.
 template <int M>
@@ -223,7 +173,7 @@ __global__ void k_nodes_grp(Tab T, Dev d) {
             b0 = b0 * tau0 + vd[Nt + pp];
             b1 = b1 * tau1 + vd[Nt + pp];
           }
-          const double dts = (double)dtj * T.tick;
+          const double dts = (double)dtj * d.etick[j];
           D0 = dts * (a1 * tau1 - a0 * tau0);
           D1 = dts * (b1 * tau1 - b0 * tau0);
         }
@@ -302,105 +252,6 @@ __device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const do
   for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
 }
 
-template <int M>
-__global__ void __launch_bounds__(kBlock) k_flux(Tab T, Dev d) {
-  constexpr int Nt = M + 1;
-  const int epoch = d.cnt->epoch;
-  const int n_active = d.cnt->n_active;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_active; q += gridDim.x * blockDim.x) {
-    int ed = d.active_list[q];
-    int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
-    int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
-    int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
-    bool ma = d.node_moved[a] == epoch, mb = d.node_moved[b] == epoch;
-    double sax = d.cshift[6 * L + 2 * le], say = d.cshift[6 * L + 2 * le + 1];
-    int le1 = le == 2 ? 0 : le + 1;
-    double sbx = d.cshift[6 * L + 2 * le1], sby = d.cshift[6 * L + 2 * le1 + 1];
-    double P[4][3];
-    long long tk[4];
-    P[0][0] = d.nX[2 * a] + sax; P[0][1] = d.nX[2 * a + 1] + say; tk[0] = d.nt[a];
-    P[1][0] = d.nX[2 * b] + sbx; P[1][1] = d.nX[2 * b + 1] + sby; tk[1] = d.nt[b];
-    if (mb) { P[2][0] = d.nXn[2 * b] + sbx; P[2][1] = d.nXn[2 * b + 1] + sby; tk[2] = d.ntn[b]; }
-    else { P[2][0] = P[1][0]; P[2][1] = P[1][1]; tk[2] = tk[1]; }
-    if (ma) { P[3][0] = d.nXn[2 * a] + sax; P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
-    else { P[3][0] = P[0][0]; P[3][1] = P[0][1]; tk[3] = tk[0]; }
-    for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * T.tick;
-    const long long tL = d.t[L], dtL = d.dt[L];
-    const double* trL = d.trace + (((size_t)L * 3 + le) * Nt) * Nt * 4;
-    long long tR = 0, dtR = 0;
-    const double* trR = nullptr;
-    int bc = d.edge_bc[ed];
-    if (R >= 0) {
-      tR = d.t[R];
-      dtR = d.dt[R];
-      trR = d.trace + (((size_t)R * 3 + lr) * Nt) * Nt * 4;
-    }
-    double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
-    for (int gx = 0; gx < Nt; ++gx) {
-      const double chi = T.glx[gx];
-#pragma unroll
-      for (int gt = 0; gt < Nt; ++gt) {
-        const double tau = T.glx[gt], wq = T.glw[gx] * T.glw[gt];
-        double dchi[3], dtau[3], n[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          dchi[c] = (1.0 - tau) * (P[1][c] - P[0][c]) + tau * (P[2][c] - P[3][c]);
-          dtau[c] = (1.0 - chi) * (P[3][c] - P[0][c]) + chi * (P[2][c] - P[1][c]);
-        }
-        n[0] = dchi[1] * dtau[2] - dchi[2] * dtau[1];
-        n[1] = dchi[2] * dtau[0] - dchi[0] * dtau[2];
-        n[2] = dchi[0] * dtau[1] - dchi[1] * dtau[0];
-        double tt = (1 - chi) * (1 - tau) * (double)tk[0] + chi * (1 - tau) * (double)tk[1] +
-                    chi * tau * (double)tk[2] + (1 - chi) * tau * (double)tk[3];
-        double qm[4], qp[4];
-        {
-          double tl = dtL > 0 ? (tt - (double)tL) / (double)dtL : 0.0;
-          const double* c0 = trL + (size_t)gx * Nt * 4;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            double acc = c0[(Nt - 1) * 4 + v];
-#pragma unroll
-            for (int p = Nt - 2; p >= 0; --p) acc = acc * tl + c0[p * 4 + v];
-            qm[v] = acc;
-          }
-        }
-        if (R >= 0) {
-          double tr = dtR > 0 ? (tt - (double)tR) / (double)dtR : 0.0;
-          const double* c0 = trR + (size_t)(Nt - 1 - gx) * Nt * 4;
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            double acc = c0[(Nt - 1) * 4 + v];
-#pragma unroll
-            for (int p = Nt - 2; p >= 0; --p) acc = acc * tr + c0[p * 4 + v];
-            qp[v] = acc;
-          }
-        } else {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) qp[v] = qm[v];
-          if (bc == 0) {
-            double nn = n[0] * n[0] + n[1] * n[1];
-            if (nn > 0.0) {
-              double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
-              qp[1] = qm[1] - 2.0 * mn * n[0];
-              qp[2] = qm[2] - 2.0 * mn * n[1];
-            }
-          }
-        }
-        double F[4];
-        rusanov(T, qm, qp, n, F);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) G[v] += wq * F[v];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Nn[c] += wq * n[c];
-      }
-    }
-    double* g = d.G + 4 * (size_t)ed;
-    double* nn = d.N + 4 * (size_t)ed;
-    g[0] = G[0]; g[1] = G[1]; g[2] = G[2]; g[3] = G[3];
-    nn[0] = Nn[0]; nn[1] = Nn[1]; nn[2] = Nn[2];
-  }
-}
-
 // One lane per Gauss point: GS lanes (a power of two >= (M+1)^2) per swept
 // edge, the point contributions summed by a fixed xor-shuffle tree.
 template <int M>
@@ -433,7 +284,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       if (ma) { P[3][0] = d.nXn[2 * a] + sax; P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
       else { P[3][0] = P[0][0]; P[3][1] = P[0][1]; tk[3] = tk[0]; }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * T.tick;
+      for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * d.etick[L];
       const double chi = T.glx[gx], tau = T.glx[gt], wq = T.glw[gx] * T.glw[gt];
       double dchi[3], dtau[3], n[3];
 #pragma unroll
@@ -600,7 +451,7 @@ __device__ __forceinline__ void virtual_data(const Tab& T, const Dev& d, int j, 
     return;
   }
   const double tau = (double)(ti - tj) / (double)dtj;
-  const double dts = (double)dtj * T.tick;
+  const double dts = (double)dtj * d.etick[j];
   const double* vd = d.vdisp + (size_t)j * 6 * Nt;
 #pragma unroll
   for (int kc = 0; kc < 6; ++kc) {
@@ -627,197 +478,6 @@ __device__ __forceinline__ void centred_monomials(const Tab& T, double x, double
   m[1] = y;
   if (M >= 2) { m[2] = x * x; m[3] = x * y; m[4] = y * y; }
   if (M >= 3) { m[5] = m[2] * x; m[6] = m[2] * y; m[7] = m[4] * x; m[8] = m[4] * y; }
-}
-
-template <int M>
-__global__ void __launch_bounds__(64) k_recon(Tab T, Dev d, int initial) {
-  constexpr int Mc = (M + 1) * (M + 2) / 2, NU = Mc - 1, NE = 2 * Mc;
-  constexpr int MaxU = kNSten * (NE - 1);
-  const int n_ready = initial ? d.ne : d.cnt->n_ready;
-  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < n_ready; pos += gridDim.x * blockDim.x) {
-    const int i = initial ? pos : d.ready_list[pos];
-    const long long ti = d.t[i];
-    double Xi[6], Qi[4];
-    for (int k = 0; k < 6; ++k) Xi[k] = d.X[6 * i + k];
-    for (int v = 0; v < 4; ++v) Qi[v] = d.Q[4 * i + v];
-    const double ja = Xi[2] - Xi[0], jb = Xi[4] - Xi[0], jc = Xi[3] - Xi[1], jd = Xi[5] - Xi[1];
-    const double idet = 1.0 / (ja * jd - jb * jc);
-    const double j00 = jd * idet, j01 = -jb * idet, j10 = -jc * idet, j11 = ja * idet;
-    const int u0 = d.u_ptr[i], nU = d.u_ptr[i + 1] - u0;
-    double A[MaxU + 1][NU];
-    double r[MaxU + 1][4];
-    for (int u = 1; u <= nU && u <= MaxU; ++u) {
-      const int j = d.u_elem[u0 + u - 1];
-      double Xv[6], Qv[4];
-      virtual_data<M>(T, d, j, ti, Xv, Qv);
-      const double sx = d.u_shift[2 * (u0 + u - 1)], sy = d.u_shift[2 * (u0 + u - 1) + 1];
-      double xr[3], yr[3];
-      for (int k = 0; k < 3; ++k) {
-        double px = Xv[2 * k] + sx - Xi[0], py = Xv[2 * k + 1] + sy - Xi[1];
-        xr[k] = j00 * px + j01 * py - (1.0 / 3.0);
-        yr[k] = j10 * px + j11 * py - (1.0 / 3.0);
-      }
-      double row[NU];
-      for (int l = 0; l < NU; ++l) row[l] = 0.0;
-      for (int qq = 0; qq < T.nq; ++qq) {
-        double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
-        double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
-        double m[kMaxNU];
-        centred_monomials<M>(T, x, y, m);
-        for (int l = 0; l < NU; ++l) row[l] += T.qw[qq] * m[l];
-      }
-      for (int l = 0; l < NU; ++l) A[u][l] = row[l] - T.mbar[l];
-      for (int v = 0; v < 4; ++v) r[u][v] = Qv[v] - Qi[v];
-    }
-    // constrained least squares per stencil through the normal equations
-    double cs[kNSten][NU][4];
-    bool ok[kNSten];
-    const unsigned char* st = d.sten + (size_t)i * kNSten * NE;
-    for (int s = 0; s < kNSten; ++s) {
-      ok[s] = d.sten_ok[i * kNSten + s] != 0;
-      if (!ok[s]) continue;
-      double Nm[NU][NU], Rh[NU][4];
-      for (int a = 0; a < NU; ++a) {
-        for (int b = 0; b < NU; ++b) Nm[a][b] = 0.0;
-        for (int v = 0; v < 4; ++v) Rh[a][v] = 0.0;
-      }
-      for (int m = 1; m < NE; ++m) {
-        int u = st[s * NE + m];
-        for (int a = 0; a < NU; ++a) {
-          double au = A[u][a];
-          for (int b = 0; b <= a; ++b) Nm[a][b] += au * A[u][b];
-          for (int v = 0; v < 4; ++v) Rh[a][v] += au * r[u][v];
-        }
-      }
-      // Cholesky N = L L^T (lower, in place)
-      for (int a = 0; a < NU; ++a) {
-        double dd = Nm[a][a];
-        for (int k = 0; k < a; ++k) dd -= Nm[a][k] * Nm[a][k];
-        double la = sqrt(dd), il = 1.0 / la;
-        Nm[a][a] = la;
-        for (int b = a + 1; b < NU; ++b) {
-          double v = Nm[b][a];
-          for (int k = 0; k < a; ++k) v -= Nm[b][k] * Nm[a][k];
-          Nm[b][a] = v * il;
-        }
-      }
-      for (int v = 0; v < 4; ++v) {
-        double y[NU];
-        for (int a = 0; a < NU; ++a) {
-          double acc = Rh[a][v];
-          for (int k = 0; k < a; ++k) acc -= Nm[a][k] * y[k];
-          y[a] = acc / Nm[a][a];
-        }
-        for (int a = NU - 1; a >= 0; --a) {
-          double acc = y[a];
-          for (int k = a + 1; k < NU; ++k) acc -= Nm[k][a] * cs[s][k][v];
-          cs[s][a][v] = acc / Nm[a][a];
-        }
-      }
-    }
-    // characteristic fields of dF/dQ.n, n along the density gradient of the
-    // central-stencil polynomial at the centroid (the linear coefficients)
-    double gx = cs[0][0][0] * j00 + cs[0][1][0] * j10;
-    double gy = cs[0][0][0] * j01 + cs[0][1][0] * j11;
-    double gn = sqrt(gx * gx + gy * gy);
-    double nx = 1.0, ny = 0.0;
-    if (gn > 0.0) { nx = gx / gn; ny = gy / gn; }
-    double Rm[4][4], Lm[4][4];
-    {
-      const double g = T.gamma, rho = Qi[0], u = Qi[1] / rho, v = Qi[2] / rho;
-      const double p = (g - 1.0) * (Qi[3] - 0.5 * rho * (u * u + v * v));
-      const double a = sqrt(g * p / rho), H = (Qi[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
-      const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
-      Rm[0][0] = 1; Rm[0][1] = 1; Rm[0][2] = 0; Rm[0][3] = 1;
-      Rm[1][0] = u - a * nx; Rm[1][1] = u; Rm[1][2] = -ny; Rm[1][3] = u + a * nx;
-      Rm[2][0] = v - a * ny; Rm[2][1] = v; Rm[2][2] = nx; Rm[2][3] = v + a * ny;
-      Rm[3][0] = H - a * un; Rm[3][1] = q2; Rm[3][2] = ut; Rm[3][3] = H + a * un;
-      Lm[0][0] = 0.5 * (b2 + un * ia); Lm[0][1] = -0.5 * (b1 * u + nx * ia); Lm[0][2] = -0.5 * (b1 * v + ny * ia); Lm[0][3] = 0.5 * b1;
-      Lm[1][0] = 1.0 - b2; Lm[1][1] = b1 * u; Lm[1][2] = b1 * v; Lm[1][3] = -b1;
-      Lm[2][0] = -ut; Lm[2][1] = -ny; Lm[2][2] = nx; Lm[2][3] = 0.0;
-      Lm[3][0] = 0.5 * (b2 - un * ia); Lm[3][1] = -0.5 * (b1 * u - nx * ia); Lm[3][2] = -0.5 * (b1 * v - ny * ia); Lm[3][3] = 0.5 * b1;
-    }
-    double sig[kNSten][4];
-    for (int s = 0; s < kNSten; ++s) {
-      if (!ok[s]) continue;
-      for (int l = 0; l < NU; ++l) {
-        double cc[4];
-        for (int rr = 0; rr < 4; ++rr)
-          cc[rr] = Lm[rr][0] * cs[s][l][0] + Lm[rr][1] * cs[s][l][1] + Lm[rr][2] * cs[s][l][2] + Lm[rr][3] * cs[s][l][3];
-        for (int rr = 0; rr < 4; ++rr) cs[s][l][rr] = cc[rr];
-      }
-      for (int rr = 0; rr < 4; ++rr) {
-        double sg = 0.0;
-        for (int a = 0; a < NU; ++a) {
-          double acc = 0.0;
-          for (int b = a; b < NU; ++b) acc += T.SigU[a][b] * cs[s][b][rr];
-          sg += acc * acc;
-        }
-        sig[s][rr] = sg;
-      }
-    }
-    double wc[NU][4];
-    for (int rr = 0; rr < 4; ++rr) {
-      double om[kNSten], tot = 0.0;
-      for (int s = 0; s < kNSten; ++s) {
-        om[s] = 0.0;
-        if (!ok[s]) continue;
-        double e1 = sig[s][rr] + 1e-14;
-        double e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
-        om[s] = (s == 0 ? 1e5 : 1.0) / e8;
-        tot += om[s];
-      }
-      double itot = 1.0 / tot;
-      for (int l = 0; l < NU; ++l) {
-        double acc = 0.0;
-        for (int s = 0; s < kNSten; ++s)
-          if (ok[s]) acc += (om[s] * itot) * cs[s][l][rr];
-        wc[l][rr] = acc;
-      }
-    }
-    double* w0 = d.w0 + (size_t)pos * Mc * 4;
-    double cv[NU][4];
-    for (int l = 0; l < NU; ++l)
-      for (int v = 0; v < 4; ++v)
-        cv[l][v] = Rm[v][0] * wc[l][0] + Rm[v][1] * wc[l][1] + Rm[v][2] * wc[l][2] + Rm[v][3] * wc[l][3];
-    for (int s = 0; s < Mc; ++s)
-      for (int v = 0; v < 4; ++v) {
-        double acc = Qi[v];
-        for (int l = 0; l < NU; ++l) acc += T.Bnod[s][l] * cv[l][v];
-        w0[s * 4 + v] = acc;
-      }
-    // local time step (eq. timestep) on the virtual element and its neighbours
-    long long tks = 0;
-    if (ti < T.T) {
-      double best = DBL_MAX;
-      for (int e = -1; e < 3; ++e) {
-        int j = e < 0 ? i : d.nbr[3 * i + e];
-        if (j < 0) continue;
-        double Xv[6], Qv[4];
-        virtual_data<M>(T, d, j, ti, Xv, Qv);
-        double ar = area6(Xv), per = 0.0;
-        for (int k = 0; k < 3; ++k) {
-          int k1 = k == 2 ? 0 : k + 1;
-          double dx = Xv[2 * k1] - Xv[2 * k], dy = Xv[2 * k1 + 1] - Xv[2 * k + 1];
-          per += sqrt(dx * dx + dy * dy);
-        }
-        double dd = 4.0 * ar / per;
-        double uu = Qv[1] / Qv[0], vv = Qv[2] / Qv[0];
-        double lam = sqrt(uu * uu + vv * vv) + sqrt(T.gamma * pressure(T, Qv) / Qv[0]);
-        double dtc = T.cfl * dd / lam;
-        best = fmin(best, dtc);
-      }
-      if (!(best > 0.0)) {
-        set_error(d.cnt, -3, i);
-        best = T.tick;
-      }
-      double rt = floor(best / T.tick);
-      tks = rt > (double)(T.T - ti) ? T.T - ti : (long long)rt;
-      if (tks < 1) tks = 1;
-      atomicMin(&d.cnt->gts_min, tks);
-    }
-    d.dt[i] = tks;
-  }
 }
 
 // predictor-derived tables of element i from qh[Nt][Mc][4]
@@ -876,97 +536,6 @@ __device__ __forceinline__ void write_products(const Tab& T, const Dev& d, int i
 }
 
 template <int M>
-__global__ void __launch_bounds__(64) k_predict(Tab T, Dev d, int initial, int gts) {
-  constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1;
-  const int n_ready = initial ? d.ne : d.cnt->n_ready;
-  const long long gmin = d.cnt->gts_min;
-  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < n_ready; pos += gridDim.x * blockDim.x) {
-    const int i = initial ? pos : d.ready_list[pos];
-    long long dtk = d.dt[i];
-    if (gts && dtk > 0) {
-      dtk = gmin;
-      d.dt[i] = dtk;
-    }
-    const double dts = (double)dtk * T.tick;
-    const double* w0 = d.w0 + (size_t)pos * Mc * 4;
-    double X[6];
-    for (int k = 0; k < 6; ++k) X[k] = d.X[6 * i + k];
-    double q[Nt][Mc][4], xh[Nt][Mc][2], q0[Mc][4], x0[Mc][2];
-    for (int s = 0; s < Mc; ++s) {
-      x0[s][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
-      x0[s][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
-      for (int v = 0; v < 4; ++v) q0[s][v] = w0[s * 4 + v];
-    }
-    for (int t = 0; t < Nt; ++t)
-      for (int s = 0; s < Mc; ++s) {
-        for (int v = 0; v < 4; ++v) q[t][s][v] = q0[s][v];
-        xh[t][s][0] = x0[s][0];
-        xh[t][s][1] = x0[s][1];
-      }
-    if (dts > 0.0) {
-      const double idt = 1.0 / dts;
-      for (int it = 0; it < T.nit; ++it) {
-        double P[Nt][Mc][4], V[Nt][Mc][2];
-        for (int t = 0; t < Nt; ++t) {
-          double f[Mc][4], g[Mc][4];
-          for (int s = 0; s < Mc; ++s) {
-            const double* qq = q[t][s];
-            double ir = 1.0 / qq[0], u = qq[1] * ir, v = qq[2] * ir;
-            double p = (T.gamma - 1.0) * (qq[3] - 0.5 * (qq[1] * u + qq[2] * v));
-            f[s][0] = qq[1]; f[s][1] = qq[1] * u + p; f[s][2] = qq[1] * v; f[s][3] = u * (qq[3] + p);
-            g[s][0] = qq[2]; g[s][1] = qq[2] * u; g[s][2] = qq[2] * v + p; g[s][3] = v * (qq[3] + p);
-            V[t][s][0] = T.eulerian ? 0.0 : u;
-            V[t][s][1] = T.eulerian ? 0.0 : v;
-          }
-          for (int s = 0; s < Mc; ++s) {
-            double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
-            double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
-            double xx = 0, xe = 0, yx = 0, ye = 0;
-            for (int r = 0; r < Mc; ++r) {
-              const double a = T.Dxi[s][r], b = T.Deta[s][r];
-              for (int v = 0; v < 4; ++v) {
-                Qx[v] += a * q[t][r][v]; Qe[v] += b * q[t][r][v];
-                fx[v] += a * f[r][v]; fe[v] += b * f[r][v];
-                gx[v] += a * g[r][v]; ge[v] += b * g[r][v];
-              }
-              xx += a * xh[t][r][0]; xe += b * xh[t][r][0];
-              yx += a * xh[t][r][1]; ye += b * xh[t][r][1];
-            }
-            double xt = 0.0, yt = 0.0;
-            for (int u = 0; u < Nt; ++u) { xt += T.Dtau[t][u] * xh[u][s][0]; yt += T.Dtau[t][u] * xh[u][s][1]; }
-            xt *= idt;
-            yt *= idt;
-            const double idet = 1.0 / (xx * ye - xe * yx);
-            const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
-            const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
-            for (int v = 0; v < 4; ++v)
-              P[t][s][v] = -(Qx[v] * xit + Qe[v] * ett + fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
-          }
-        }
-        for (int t = 1; t < Nt; ++t)
-          for (int s = 0; s < Mc; ++s) {
-            for (int v = 0; v < 4; ++v) {
-              double acc = 0.0;
-              for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * P[u][s][v];
-              q[t][s][v] = q0[s][v] + dts * acc;
-            }
-            for (int c = 0; c < 2; ++c) {
-              double acc = 0.0;
-              for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * V[u][s][c];
-              xh[t][s][c] = x0[s][c] + dts * acc;
-            }
-          }
-      }
-    }
-    double* out = d.qhat + (size_t)i * Mc * Nt * 4;
-    for (int t = 0; t < Nt; ++t)
-      for (int s = 0; s < Mc; ++s)
-        for (int v = 0; v < 4; ++v) out[(t * Mc + s) * 4 + v] = q[t][s][v];
-    write_products<M>(T, d, i, q);
-  }
-}
-
-template <int M>
 __global__ void k_products(Tab T, Dev d) {
   constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ne; i += gridDim.x * blockDim.x) {
@@ -998,7 +567,7 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
   __shared__ double sx[G][Nst][2], sV[G][Nst][2];
   __shared__ double sDxi[Mc][Mc], sDeta[Mc][Mc], sB[Nt - 1][Nt], sDtau[Nt][Nt], sTr[3][Nt][Mc], sVt[Nt][Nt];
   __shared__ double sdts[G];
-  __shared__ int sidx[G];
+  __shared__ int sidx[G], sbad[G];
   for (int k = threadIdx.x; k < Mc * Mc; k += blockDim.x) {
     sDxi[k / Mc][k % Mc] = T.Dxi[k / Mc][k % Mc];
     sDeta[k / Mc][k % Mc] = T.Deta[k / Mc][k % Mc];
@@ -1029,7 +598,8 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
         d.dt[i] = dtk;
       }
       sidx[e] = i;
-      sdts[e] = (double)dtk * T.tick;
+      sdts[e] = (double)dtk * d.etick[i];
+      sbad[e] = 0;
     }
     __syncthreads();
     const int i = live ? sidx[e] : 0;
@@ -1139,6 +709,18 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
       }
       __syncthreads();
     }
+    // a non-positive density or pressure at any space-time node sends the
+    // element back to w_h on every time slice
+    if (work) {
+      const double* q = sq[e][l];
+      if (!(q[0] > 0.0) || !(gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]) > 0.0)) sbad[e] = 1;
+    }
+    __syncthreads();
+    if (work && t > 0 && sbad[e]) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sq[e][l][v] = sq[e][s][v];
+    }
+    __syncthreads();
     if (live) {
       double* out = d.qhat + ((size_t)i * Nst + l) * 4;
 #pragma unroll
@@ -1523,6 +1105,7 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
     }
     __syncthreads();
     // P8: nodal values of w_h for the predictor, and the new local time step
+    double* sW0 = sCh;  // free after P6: [G][Mc][4]
     for (int item = tid; item < G * (Mc * 4 + 1); item += nth) {
       const int e = item / (Mc * 4 + 1), k = item % (Mc * 4 + 1);
       if (!sVal[e]) continue;
@@ -1532,7 +1115,7 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
         double acc = sEl[e * 16 + 6 + v];
 #pragma unroll
         for (int l = 0; l < NU; ++l) acc += sBn[s * NU + l] * sCv[(e * NU + l) * 4 + v];
-        d.w0[((size_t)(base + e) * Mc + s) * 4 + v] = acc;
+        sW0[(e * Mc + s) * 4 + v] = acc;
       } else {
         const long long ti = d.t[i];
         long long tks = 0;
@@ -1546,15 +1129,44 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
           }
           if (bad || !(best > 0.0)) {
             set_error(d.cnt, -3, i);
-            best = T.tick;
+            best = d.etick[i];
           }
-          const double rt = floor(best / T.tick);
+          const double rt = floor(best / d.etick[i]);
           tks = rt > (double)(T.T - ti) ? T.T - ti : (long long)rt;
           if (tks < 1) tks = 1;
           atomicMin(&d.cnt->gts_min, tks);
         }
         d.dt[i] = tks;
       }
+    }
+    __syncthreads();
+    // P9: positivity scaling of w_h at the lattice nodes (density first, then
+    // pressure through its chord bound; the scaling of Zhang and Shu), then
+    // the nodal values go to the predictor
+    if (tid < G && sVal[tid]) {
+      const int e = tid;
+      const double* Qi = sEl + e * 16 + 6;
+      double* w = sW0 + (size_t)e * Mc * 4;
+      const double rho_min = 1e-8 * Qi[0], p_i = pressure(T, Qi), p_min = 1e-8 * p_i;
+      for (int pass = 0; pass < 2; ++pass) {
+        double theta = 1.0;
+        for (int s = 0; s < Mc; ++s) {
+          const double* ws = w + 4 * s;
+          if (pass == 0 && ws[0] < rho_min) theta = fmin(theta, (Qi[0] - rho_min) / (Qi[0] - ws[0]));
+          if (pass == 1) {
+            const double ps = pressure(T, ws);
+            if (ps < p_min) theta = fmin(theta, (p_i - p_min) / (p_i - ps));
+          }
+        }
+        if (theta < 1.0)
+          for (int k = 0; k < Mc * 4; ++k) w[k] = Qi[k % 4] + theta * (w[k] - Qi[k % 4]);
+      }
+    }
+    __syncthreads();
+    for (int item = tid; item < G * Mc * 4; item += nth) {
+      const int e = item / (Mc * 4);
+      if (!sVal[e]) continue;
+      d.w0[(size_t)(base + e) * Mc * 4 + item % (Mc * 4)] = sW0[item];
     }
     __syncthreads();
   }
