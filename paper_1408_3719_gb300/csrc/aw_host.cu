@@ -924,17 +924,25 @@ int aw_advance_to(aw_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done,
   if (!c) return AW_ERR_INVALID_ARG;
   if (!(t >= c->cfg.t_end))
     return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to runs to t_end (element times are local; pass t >= t_end)");
-  int64_t sweeps = 0, updates = 0;
-  while (sweeps < max_sweeps) {
-    int64_t n = 0;
-    int rc = do_sweeps(c, 1, &n, true);
-    if (rc) return rc;
-    if (n == 0) break;
-    ++sweeps;
-    updates += n;
+  // sweeps go out in chunks between host checks; a sweep with an empty ready
+  // set changes nothing, so overshooting the end of the run is harmless
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  const long long u0 = c->hcnt->updates, p0 = c->hcnt->productive;
+  int64_t issued = 0, chunk = 8;
+  while (issued < max_sweeps) {
+    const int64_t n = std::min<int64_t>(chunk, max_sweeps - issued);
+    if ((rc = do_sweeps(c, n, nullptr, true))) return rc;
+    issued += n;
+    if (c->hcnt->n_unfinished == 0) break;
+    if (c->hcnt->n_ready == 0) {
+      c->failed = true;
+      return set_err(c, AW_ERR_DEADLOCK, "no element satisfies the update criterion (%d unfinished)", c->hcnt->n_unfinished);
+    }
+    chunk = std::min<int64_t>(chunk * 2, 256);
   }
-  if (sweeps_done) *sweeps_done = sweeps;
-  if (updates_done) *updates_done = updates;
+  if (sweeps_done) *sweeps_done = c->hcnt->productive - p0;
+  if (updates_done) *updates_done = c->hcnt->updates - u0;
   return AW_OK;
 }
 

@@ -118,6 +118,7 @@ struct Counters {
   long long gts_min;
   long long updates;             // total element updates
   long long sweeps;
+  long long productive;           // sweeps that updated at least one element
   long long updates_since_sync;
 };
 

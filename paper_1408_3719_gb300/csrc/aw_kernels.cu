@@ -118,7 +118,10 @@ __global__ void k_ready(Tab T, Dev d) {
 
 // ready candidates of the next sweep: S^W of this sweep's ready elements
 __global__ void k_cand(Tab T, Dev d) {
-  if (T.gts) return;
+  if (T.gts) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d.cnt->n_ready > 0) d.cnt->productive += 1;
+    return;
+  }
   const int epoch = d.cnt->epoch;
   const int par = (epoch + 1) & 1;
   const int n_ready = d.cnt->n_ready;
@@ -135,7 +138,10 @@ __global__ void k_cand(Tab T, Dev d) {
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->cand_valid = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.cnt->cand_valid = 1;
+    if (n_ready > 0) d.cnt->productive += 1;
+  }
 }
 
 // Node solver with 8 lanes per moved node, one Voronoi element per lane

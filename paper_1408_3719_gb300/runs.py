@@ -1,0 +1,123 @@
+"""Full runs of the paper's test configurations on the GPU library.
+
+    python -m paper_1408_3719_gb300.runs sod [--gts] [--order 1]
+    python -m paper_1408_3719_gb300.runs vortex --n 45 90 179 [--order 3]
+    python -m paper_1408_3719_gb300.runs explosion [--order 2] [--hc 0.00114] [--gts]
+
+Each prints one JSON line per run: element updates, productive sweeps, wall
+time, updates/s, and the accuracy measure of the configuration (density L1
+error against the exact Riemann solution for the shock tube, Sec. 3.2; L2
+error of the density cell averages against the exact stationary vortex,
+Sec. 3.1).  The inputs are the seeded synthetic workloads of
+``paper_1408_3719_gb300.workloads``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import aleweno
+from . import exact
+from . import workloads as W
+
+
+def _areas(X):
+    return 0.5 * ((X[:, 2] - X[:, 0]) * (X[:, 5] - X[:, 1]) - (X[:, 3] - X[:, 1]) * (X[:, 4] - X[:, 0]))
+
+
+def _run(mesh, Q, **cfg):
+    s = aleweno.Solver(**cfg)
+    t0 = time.perf_counter()
+    s.load_mesh(mesh)
+    t1 = time.perf_counter()
+    s.load_state(Q)
+    try:
+        sweeps, updates = s.advance()
+    except aleweno.AwError as err:
+        e = s.get_elem()
+        fail = dict(error=str(err), t_min=float(e["t"].min() * s.tick), t_max=float(e["t"].max() * s.tick),
+                    updates=int(e["count"].sum()))
+        if "element" in str(err):
+            i = int(str(err).split("element ")[1].split()[0])
+            X = e["X"][i]
+            fail.update(elem=i, t_elem=float(e["t"][i] * s.tick), Q=e["Q"][i].tolist(), X=X.tolist(),
+                        area=float(_areas(X[None])[0]), r=float(np.linalg.norm(X.reshape(3, 2).mean(0))))
+        s.close()
+        raise RuntimeError(json.dumps(fail)) from err
+    t2 = time.perf_counter()
+    e = s.get_elem()
+    info = dict(n_tris=int(mesh["tri"].shape[0]), order_M=cfg.get("order_M"), gts=bool(cfg.get("gts", False)),
+                sweeps=sweeps, updates=updates, setup_s=t1 - t0, run_s=t2 - t1,
+                updates_per_s=updates / max(t2 - t1, 1e-12), gcl_max=s.diag()["gcl_max"])
+    s.close()
+    return e, info
+
+
+def sod(order=1, gts=True, nx=100, ny=10):
+    mesh, Q = W.sod_tube(nx, ny)
+    e, info = _run(mesh, Q, order_M=order, t_end=0.2, gts=gts)
+    A = _areas(e["X"])
+    cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
+    ex = exact.sample(cx, 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1))
+    info.update(config="Sod tube", l1_rho=float(np.sum(np.abs(e["Q"][:, 0] - ex[:, 0]) * A) / A.sum()))
+    return info
+
+
+def vortex(n, order=3, gts=False):
+    mesh, Q = W.vortex(n)
+    e, info = _run(mesh, Q, order_M=order, t_end=1.0, gts=gts)
+    x, w = np.polynomial.legendre.leggauss(6)
+    x, w = 0.5 * (x + 1), 0.5 * w
+    u, v = np.meshgrid(x, x, indexing="ij")
+    wu, wv = np.meshgrid(w, w, indexing="ij")
+    s_, t_, w_ = (u * (1 - v)).ravel(), v.ravel(), (2 * wu * wv * (1 - v)).ravel()
+    P = e["X"].reshape(-1, 3, 2)
+    pts = P[:, 0][:, None] + s_[None, :, None] * (P[:, 1] - P[:, 0])[:, None] + t_[None, :, None] * (P[:, 2] - P[:, 0])[:, None]
+    ex = np.einsum("nqv,q->nv", W.vortex_state(pts[..., 0], pts[..., 1], 1.4, mesh["period"]), w_)
+    A = _areas(e["X"])
+    Pd = P[:, [0, 1, 2, 0]]
+    d = np.linalg.norm(np.diff(Pd, axis=1), axis=2)
+    circ = d.prod(1) / (2.0 * A)  # circumcircle diameter a b c / (2 |T|)
+    info.update(config="isentropic vortex", n=n, l2_rho=float(math.sqrt(np.sum(A * (e["Q"][:, 0] - ex[:, 0]) ** 2))),
+                h_max_circumdiameter=float(circ.max()))
+    return info
+
+
+def explosion(order=2, hc=0.00114, gts=False):
+    mesh, Q = W.explosion(hc)
+    e, info = _run(mesh, Q, order_M=order, t_end=0.25, gts=gts)
+    r = np.linalg.norm(e["X"].reshape(-1, 3, 2).mean(1), axis=1)
+    info.update(config="explosion EP1", rho_max=float(e["Q"][:, 0].max()), r_max=float(r.max()))
+    return info
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["sod", "vortex", "explosion"])
+    ap.add_argument("--order", type=int, default=None)
+    ap.add_argument("--gts", action="store_true")
+    ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
+    ap.add_argument("--hc", type=float, default=0.00114)
+    a = ap.parse_args()
+    aleweno.load()
+    if a.case == "sod":
+        print(json.dumps(sod(a.order or 1, a.gts)), flush=True)
+    elif a.case == "vortex":
+        prev = None
+        for n in a.n:
+            r = vortex(n, a.order or 3, a.gts)
+            if prev:
+                r["order_vs_previous"] = math.log(prev["l2_rho"] / r["l2_rho"]) / math.log(
+                    r["h_max_circumdiameter"] / prev["h_max_circumdiameter"]) * -1
+            print(json.dumps(r), flush=True)
+            prev = r
+    else:
+        print(json.dumps(explosion(a.order or 2, a.hc, a.gts)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

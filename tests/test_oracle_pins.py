@@ -14,7 +14,7 @@ import pytest
 
 from oracle.pyoracle import Oracle
 from paper_1408_3719_gb300 import workloads as W
-from tests import riemann_exact
+from paper_1408_3719_gb300 import exact as riemann_exact
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
