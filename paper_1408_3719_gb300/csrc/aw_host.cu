@@ -620,6 +620,9 @@ int reset_sweep_state(aw_ctx* c) {
   CK(cudaMemsetAsync(d.edge_act, 0, c->ned * sizeof(int), c->stream));
   CK(cudaMemsetAsync(d.cand_stamp, 0, c->ne * sizeof(int), c->stream));
   CK(cudaMemsetAsync(d.cnt, 0, sizeof(Counters), c->stream));
+  static const int one = 1;  // stamps are 0: the first sweep must be epoch 1
+  CK(cudaMemcpyAsync(&d.cnt->epoch, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return AW_OK;
 }
 
@@ -901,8 +904,8 @@ static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   int rc = sync_counters(c);
   if (rc) return rc;
   if ((rc = check_device_error(c))) return rc;
-  if (n_updated) *n_updated = c->hcnt->n_ready;
-  if (c->hcnt->n_ready == 0 && c->hcnt->n_unfinished > 0) {
+  if (n_updated) *n_updated = c->hcnt->last_ready;
+  if (c->hcnt->last_ready == 0 && c->hcnt->n_unfinished > 0) {
     c->failed = true;
     return set_err(c, AW_ERR_DEADLOCK, "no element satisfies the update criterion (%d unfinished)", c->hcnt->n_unfinished);
   }
@@ -935,7 +938,7 @@ int aw_advance_to(aw_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done,
     if ((rc = do_sweeps(c, n, nullptr, true))) return rc;
     issued += n;
     if (c->hcnt->n_unfinished == 0) break;
-    if (c->hcnt->n_ready == 0) {
+    if (c->hcnt->last_ready == 0) {
       c->failed = true;
       return set_err(c, AW_ERR_DEADLOCK, "no element satisfies the update criterion (%d unfinished)", c->hcnt->n_unfinished);
     }

@@ -119,11 +119,13 @@ struct Counters {
   long long updates;             // total element updates
   long long sweeps;
   long long productive;           // sweeps that updated at least one element
+  int last_ready;                 // ready elements of the last completed sweep
+  int finish_blocks;
   long long updates_since_sync;
 };
 
 // kernel launchers (aw_kernels.cu)
-constexpr int kNumKernels = 10;  // launches per sweep
+constexpr int kNumKernels = 8;  // launches per sweep
 const char* kernel_name(int k);
 void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev);
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);

@@ -1,25 +1,25 @@
-// Kernels of one LTS sweep (Sec. 2.6) on sm_103a, all FP64:
-//   k_begin        reset the per-sweep counters, advance the epoch stamp
-//   k_ready        update criterion on S^W (eq. WENOupdate) + compaction of the
-//                  ready elements and of the nodes they move
-//   k_nodes        node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
-//   k_edges        mark edges with a moved endpoint, compact them and the
-//                  elements they touch
-//   k_flux         space-time fluxes through the swept edge surfaces (eqs.
+// Kernels of one LTS sweep (Sec. 2.6) on sm_103a, all FP64, launched in this
+// order (one captured CUDA graph per sweep):
+//   k_ready        update criterion on S^W (eq. WENOupdate) for the candidate
+//                  elements; compaction of the ready elements and their nodes
+//   k_nodes_grp    node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
+//   k_edges        edges with a moved endpoint and the elements they touch
+//   k_flux_grp     space-time fluxes through the swept edge surfaces (eqs.
 //                  spacetimenodes, rusanov, STint) and their GCL normals
 //   k_update       one-step FV update / memory variables (eqs. PDEfinal, Qm2, gcl)
-//   k_commit       node positions and times of the moved nodes
-//   k_recon<M>     virtual projection + WENO + local time step (eqs. virtGeom,
+//   k_recon_coop   virtual projection + WENO + local time step (eqs. virtGeom,
 //                  virtCellaverage, intConsRec, weno, timestep)
-//   k_predict<M>   space-time Galerkin predictor (eqs. PDECG, pdef, CGfinal,
+//   k_predict_coop space-time Galerkin predictor (eqs. PDECG, pdef, CGfinal,
 //                  newVertPos) and its derived tables (edge traces, averages,
 //                  vertex displacement polynomials)
-// Work lists are compacted with warp ballots and one atomic per warp; every
+//   k_finish       commit the moved nodes, list the next sweep's candidates,
+//                  reset the per-sweep counters
+// Work lists are compacted with atomics on warp-aggregated slots; every
 // per-element and per-node sum runs in a fixed order, so results do not
 // depend on the order of the lists.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
-#include <algorithm>
 #include <cstdio>
 
 #include "aw_internal.h"
@@ -34,17 +34,6 @@ __device__ __forceinline__ double area6(const double* X) {
   return 0.5 * ((X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0]));
 }
 
-// Warp-aggregated append: returns the slot of this lane (if pred) in list.
-__device__ __forceinline__ int warp_append(int* counter, bool pred) {
-  unsigned mask = __ballot_sync(0xffffffffu, pred);
-  int lane = threadIdx.x & 31;
-  int base = 0;
-  int leader = __ffs(mask) - 1;
-  if (mask && lane == leader) base = atomicAdd(counter, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
-  return base + __popc(mask & ((1u << lane) - 1u));
-}
-
 __device__ __forceinline__ void set_error(Counters* cnt, int code, int elem) {
   if (atomicCAS(&cnt->err_code, 0, code) == 0) cnt->err_elem = elem;
 }
@@ -54,20 +43,6 @@ __device__ __forceinline__ double pressure(const Tab& T, const double* q) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_begin(Dev d) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    Counters* c = d.cnt;
-    c->epoch += 1;
-    c->n_ready = 0;
-    c->n_moved = 0;
-    c->n_active = 0;
-    c->n_touched = 0;
-    c->n_cand[(c->epoch + 1) & 1] = 0;
-    c->gts_min = LLONG_MAX;
-    c->sweeps += 1;
-  }
-}
-
 // Candidates: every element in the first sweep after a state is loaded;
 // afterwards the total stencils of the previous sweep's ready elements (the
 // criterion of any other element reads only unchanged times).
@@ -80,6 +55,7 @@ __global__ void k_ready(Tab T, Dev d) {
   const int* clist = d.cand_list + (size_t)par * d.ne;
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->gts_min = LLONG_MAX;
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n_items; q += nwarps) {
     const int i = listed ? clist[q] : q;
     const long long ti = d.t[i];
@@ -116,31 +92,54 @@ __global__ void k_ready(Tab T, Dev d) {
   }
 }
 
-// ready candidates of the next sweep: S^W of this sweep's ready elements
-__global__ void k_cand(Tab T, Dev d) {
-  if (T.gts) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && d.cnt->n_ready > 0) d.cnt->productive += 1;
-    return;
-  }
+// End of a sweep: commit the moved nodes, list the next sweep's ready
+// candidates (the total stencils of this sweep's ready elements), and in the
+// last block to finish reset the per-sweep counters and advance the epoch.
+__global__ void k_finish(Tab T, Dev d) {
   const int epoch = d.cnt->epoch;
-  const int par = (epoch + 1) & 1;
+  const int n_moved = d.cnt->n_moved;
   const int n_ready = d.cnt->n_ready;
-  int* clist = d.cand_list + (size_t)par * d.ne;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int q = warp; q < n_ready; q += nwarps) {
-    const int i = d.ready_list[q];
-    for (int p = d.sw_ptr[i] + lane, pe = d.sw_ptr[i + 1]; p < pe; p += 32) {
-      const int j = d.sw[p];
-      if (atomicExch(&d.cand_stamp[j], epoch) != epoch) {
-        const int s2 = atomicAdd(&d.cnt->n_cand[par], 1);
-        clist[s2] = j;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int q = gtid; q < n_moved; q += nth) {
+    const int n = d.moved_list[q];
+    d.nX[2 * n] = d.nXn[2 * n];
+    d.nX[2 * n + 1] = d.nXn[2 * n + 1];
+    d.nt[n] = d.ntn[n];
+  }
+  if (!T.gts) {
+    const int par = (epoch + 1) & 1;
+    int* clist = d.cand_list + (size_t)par * d.ne;
+    const int lane = threadIdx.x & 31;
+    for (int q = gtid >> 5; q < n_ready; q += nth >> 5) {
+      const int i = d.ready_list[q];
+      for (int p = d.sw_ptr[i] + lane, pe = d.sw_ptr[i + 1]; p < pe; p += 32) {
+        const int j = d.sw[p];
+        if (atomicExch(&d.cand_stamp[j], epoch) != epoch) {
+          const int s2 = atomicAdd(&d.cnt->n_cand[par], 1);
+          clist[s2] = j;
+        }
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    d.cnt->cand_valid = 1;
-    if (n_ready > 0) d.cnt->productive += 1;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&d.cnt->finish_blocks, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    Counters* c = d.cnt;
+    if (!T.gts) c->cand_valid = 1;
+    if (n_ready > 0) c->productive += 1;
+    c->last_ready = n_ready;
+    c->n_cand[epoch & 1] = 0;  // consumed by this sweep; refilled by the next one's finish
+    c->n_ready = 0;
+    c->n_moved = 0;
+    c->n_active = 0;
+    c->n_touched = 0;
+    c->sweeps += 1;
+    c->finish_blocks = 0;
+    c->epoch = epoch + 1;
   }
 }
 
@@ -430,16 +429,6 @@ __global__ void k_update(Tab T, Dev d) {
       atomicAdd((unsigned long long*)&d.cnt->updates, (unsigned long long)__popc(um));
       atomicAdd((unsigned long long*)&d.cnt->updates_since_sync, (unsigned long long)__popc(um));
     }
-  }
-}
-
-__global__ void k_commit(Dev d) {
-  const int n_moved = d.cnt->n_moved;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_moved; q += gridDim.x * blockDim.x) {
-    int n = d.moved_list[q];
-    d.nX[2 * n] = d.nXn[2 * n];
-    d.nX[2 * n + 1] = d.nXn[2 * n + 1];
-    d.nt[n] = d.ntn[n];
   }
 }
 
@@ -801,7 +790,7 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
 // ---------------------------------------------------------------------------
 template <int M>
 struct ReconShape {
-  static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, NU = Mc - 1, NE = 2 * Mc;
+  static constexpr int Mc = (M + 1) * (M + 2) / 2, NU = Mc - 1, NE = 2 * Mc;
   static constexpr int MaxU = kNSten * (NE - 1);
   static constexpr int G = M == 1 ? 16 : (M == 2 ? 8 : 4);
   static constexpr int kThreads = 256;
@@ -1196,7 +1185,7 @@ void launch_recon(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initi
     attr = true;
   }
   const int need = (d.ne + S::G - 1) / S::G;
-  const int grid = initial ? need : std::min(need, nsm * 4);
+  const int grid = initial ? need : std::min(need, nsm * 8);
   k_recon_coop<M><<<grid, S::kThreads, S::bytes, s>>>(T, d, initial);
 }
 
@@ -1216,16 +1205,14 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   const int grid_w = nsm * 8;
   int k = 0;
   auto mark = [&]() { if (ev) cudaEventRecord(ev[k++], s); };
-  mark(); k_begin<<<1, 32, 0, s>>>(d);
   mark(); k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
   mark(); k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
   mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
   mark(); k_flux_grp<M><<<grid_w * 4, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
-  mark(); k_commit<<<grid_w, kBlock, 0, s>>>(d);
-  mark(); k_cand<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); launch_recon<M>(T, d, nsm, s, 0);
   mark(); launch_predict<M>(T, d, nsm, s, 0);
+  mark(); k_finish<<<grid_w, kBlock, 0, s>>>(T, d);
   mark();
 }
 
@@ -1253,8 +1240,8 @@ __global__ void k_dfma_chain(double* out, int iters, double a, double b) {
 }  // namespace
 
 const char* kernel_name(int k) {
-  static const char* names[kNumKernels] = {"k_begin", "k_ready", "k_nodes", "k_edges", "k_flux",
-                                           "k_update", "k_commit", "k_cand", "k_recon", "k_predict"};
+  static const char* names[kNumKernels] = {"k_ready", "k_nodes", "k_edges", "k_flux",
+                                           "k_update", "k_recon", "k_predict", "k_finish"};
   return (k >= 0 && k < kNumKernels) ? names[k] : nullptr;
 }
 
