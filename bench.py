@@ -119,6 +119,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms: float, updates: int, dist=None, device="cpu"):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    all ranks' element updates (each rank runs its own replica)."""
+    if dist is None:
+        return ms, float(updates)
+    import torch
+    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def workload(order: int, hc: float):
     from paper_1408_3719_gb300 import workloads as W
     mesh, Q = W.explosion(hc)
@@ -221,15 +234,7 @@ def run_ours(args, rank, world):
     prof_updates = s.sync()
     kms, ksweeps = s.profile_read()
     s.profile(False)
-    tot = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(mx[0]), float(sm[1])
-    else:
-        ms_max, updates_all = ms, float(updates)
+    ms_max, updates_all = aggregate(ms, updates, dist, "cuda")
     value = updates_all / (ms_max * 1e-3)
 
     # dominant kernel and its roofline (FP64 pipe: this path is ALU-bound)
@@ -257,11 +262,11 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         s2.load_state(Qh)
         ups = 0
-        for _ in range(args.warmup + args.steps):
+        for _ in range(args.e2e_sweeps):
             ups += s2.sweep()
         s2.get_state(out)
         el = time.perf_counter() - t0
-        nst = args.warmup + args.steps
+        nst = args.e2e_sweeps
         e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": Qh.nbytes / nst,
                "d2h_bytes_per_step": (out.nbytes + 8 * nst) / nst,
                "note": "aw_load_state(host Q) + sweeps via aw_lts_sweep + aw_get_state(host Q); mesh pre-processing "
@@ -375,6 +380,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--e2e-sweeps", type=int, default=200)
     ap.add_argument("--workload", default="explosion", choices=["explosion", "batched"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--min-tris", type=int, default=2000)

@@ -346,3 +346,20 @@ def test_vortex_order_of_accuracy(M, ns, order):
     e1 = _vortex_error(ns[0], M)
     e2 = _vortex_error(ns[1], M)
     assert math.log(e1 / e2) / math.log(ns[1] / ns[0]) > order, (e1, e2)
+
+
+def test_positivity_safeguard_on_strong_jump():
+    """R11: on a tube with density ratio 9.5 and pressure ratio 15 the P2
+    predictor starts from nodally positive data and keeps every space-time node
+    physical, and the sweeps run without a non-physical update."""
+    mesh = W.shock_tube_mesh(300, 10, 1.0, 10.0 / 300, seed=W.SEED_BASE + 1047)
+    q = W.cell_average(mesh, lambda x, y: W.riemann_state(x, y, (1.0, 0, 0, 1.0), (1 / 9.5, 0, 0, 1 / 15.0),
+                                                          0.575, 1.4), W._subtriangle_rule(8))
+    o = Oracle(order_M=2, t_end=0.2)
+    o.load_mesh(mesh)
+    o.load_state(q)
+    for _ in range(60):
+        o.sweep()
+        qh = o.get_elem()["qhat"]
+        p = 0.4 * (qh[..., 3] - 0.5 * (qh[..., 1] ** 2 + qh[..., 2] ** 2) / qh[..., 0])
+        assert qh[..., 0].min() > 0 and p.min() > 0
