@@ -95,6 +95,13 @@ int aw_load_batch(aw_ctx* ctx, int n_inst, const int64_t* node_offsets, const in
  * all node and element times set to 0.  NONPHYSICAL if rho or p <= 0. */
 int aw_load_state(aw_ctx* ctx, const double* Q);
 
+/* aw_load_state on node positions xy [n_nodes][2] (host or device pointer)
+ * instead of the mesh's own: element corners become xy[tri] plus their
+ * periodic offsets.  The mesh pre-processing of aw_load_mesh (stencils,
+ * total stencils, wall normals) is kept, so a small move of the nodes changes
+ * the result smoothly.  BAD_MESH if an element turns clockwise. */
+int aw_load_state_xy(aw_ctx* ctx, const double* Q, const double* xy);
+
 /* One cycle of the LTS algorithm (Sec. 2.6): every element satisfying the
  * update criterion on S^W (eq. WENOupdate) moves its nodes (Sec. 2.4),
  * computes the space-time edge and vertex fluxes (eqs. spacetimenodes,
@@ -168,6 +175,53 @@ const char* aw_kernel_name(int k);
  * than 1,048,576 triangles are rejected with AW_ERR_INVALID_ARG; STATE without
  * a loaded state. */
 int aw_ready_set_noalloc(aw_ctx* ctx, int32_t* ready_out, int64_t* n_ready_out);
+
+/* Frozen schedule.  The local time steps are integers of ticks taken from
+ * the CFL bound (eq. timestep) through floor(), so the solution is a
+ * piecewise-smooth function of the data with jumps wherever a step changes
+ * by one tick.  mode 1 (record) logs the step every element takes at each of
+ * its first k updates (update 0 is the step of aw_load_state) into a log
+ * owned by the context; mode 2 (replay) takes the logged steps instead of
+ * the CFL steps, so runs from perturbed data follow the recorded schedule
+ * and differ smoothly; mode 0 returns to CFL steps.  The log survives
+ * aw_load_state and is dropped with the mesh.  Local time stepping only
+ * (INVALID_ARG with gts = 1).  An update beyond k stops the run with STATE.
+ * aw_get_schedule copies the log, [n_tris][k] int64 ticks, to out (host or
+ * device).  Changing the mode re-captures the sweep graph. */
+int aw_schedule(aw_ctx* ctx, int mode, int64_t k);
+int aw_get_schedule(aw_ctx* ctx, int64_t* out);
+
+/* Adjoint of n LTS sweeps for the schedule they take (the sweep map with the
+ * ready sets and tick steps held fixed, and the mesh pre-processing of
+ * aw_load_mesh held fixed).
+ * aw_adjoint_forward runs n_sweeps sweeps from a state just loaded by
+ * aw_load_state / aw_load_state_xy and keeps a device checkpoint of the
+ * state every ckpt_every sweeps (plus the final state); STATE if a sweep ran
+ * since the load.  aw_adjoint then takes dJ/d(final state) of a scalar J --
+ * dJdQ [n_tris][4] conserved averages, dJdX [n_tris][6] element corners,
+ * dJdxy [n_nodes][2] node positions, each NULL for zero, host or device
+ * pointers -- and writes dJ/dQ0 [n_tris][4] and dJ/dxy0 [n_nodes][2] with
+ * respect to the loaded averages and node positions (either may be NULL).
+ * It recomputes each segment of ckpt_every sweeps from its checkpoint and
+ * reverses the sweeps of the segment one by one: phase B of the ready
+ * elements (predictor iterations, characteristic WENO weights and
+ * least-squares solves, virtual projection), then the node commit, the FV
+ * update and memory variables, the edge fluxes and the node solver.  Device
+ * memory: (n_sweeps / ckpt_every + ckpt_every + 3) copies of the state.  The
+ * context is left in the final state; aw_adjoint may be called again for
+ * another J.  STATE if a positivity safeguard (scaling of w_h, predictor
+ * fallback) acted in one of the sweeps: the map has a kink there.  No
+ * counterpart in the paper. */
+int aw_adjoint_forward(aw_ctx* ctx, int64_t n_sweeps, int64_t ckpt_every);
+int aw_adjoint(aw_ctx* ctx, const double* dJdQ, const double* dJdX, const double* dJdxy,
+               double* dJdQ0, double* dJdxy0);
+
+/* Host-only check of the adjoint's element-level pieces (no GPU needed): for
+ * order M and a seed, each reverse (reconstruction, predictor, edge flux,
+ * node solver) is compared with central differences of its forward on
+ * random smooth data; report[0..3] receive the largest relative mismatches.
+ * No counterpart in the paper. */
+int aw_adjoint_selftest(int order_M, uint64_t seed, double* report);
 
 /* Measured FP64 FMA throughput of the current GPU (GFLOP/s), a roofline
  * denominator: a fixed dependent-chain DFMA kernel over all SMs. */

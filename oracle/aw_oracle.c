@@ -120,6 +120,10 @@ struct oc_ctx {
   double* xy0;
   double gcl_max;
   double gcl_checked;
+  /* --- frozen schedule (record / replay of the dt ticks, reading R12) --- */
+  int sched_mode;      /* 0 free, 1 record, 2 replay */
+  int64_t sched_k;     /* entries per element: updates 0..sched_k-1 */
+  int64_t* sched_log;  /* [ne][sched_k] dt ticks chosen at each update count */
 };
 
 static int fail(oc_ctx* c, int code, const char* fmt, ...) {
@@ -1312,6 +1316,16 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
       ticks = r > (double)(c->T - c->t[i]) ? c->T - c->t[i] : (int64_t)r;
       if (ticks < 1) ticks = 1;
     }
+    if (c->sched_mode != 0) {
+      if (c->count[i] >= c->sched_k) {
+        rc = fail(c, OC_STATE, "element %lld: update %lld is beyond the schedule log", (long long)i,
+                  (long long)c->count[i]);
+        break;
+      }
+      int64_t* slot = c->sched_log + i * c->sched_k + c->count[i];
+      if (c->sched_mode == 1) *slot = ticks;
+      else ticks = *slot;
+    }
     c->dt[i] = ticks;
     if (ticks > 0 && ticks < gmin) gmin = ticks;
   }
@@ -1362,6 +1376,10 @@ static void free_mesh(oc_ctx* c) {
   c->sten = NULL; c->sten_shift = NULL; c->sten_ok = NULL; c->sw_ptr = NULL; c->sw = NULL;
   c->Q = NULL; c->QM = NULL; c->HM = NULL; c->X = NULL; c->qhat = NULL; c->t = NULL;
   c->dt = NULL; c->count = NULL; c->nX = NULL; c->nt = NULL; c->xy0 = NULL;
+  free(c->sched_log);
+  c->sched_log = NULL;
+  c->sched_mode = 0;
+  c->sched_k = 0;
   c->have_state = 0;
 }
 
@@ -1415,11 +1433,11 @@ int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
 
 /* pre-processing phase (Sec. 2.6): cell averages at t=0, first WENO without
    virtual data, local time steps, predictor; node times 0 */
-int oc_load_state(oc_ctx* c, const double* Q) {
+static int load_state(oc_ctx* c, const double* Q, const double* xy) {
   if (!c || !c->tri || !Q) return OC_INVALID;
   int64_t ne = c->ne_;
   memcpy(c->Q, Q, sizeof(double) * 4 * ne);
-  memcpy(c->nX, c->xy0, sizeof(double) * 2 * c->nn);
+  memcpy(c->nX, xy ? xy : c->xy0, sizeof(double) * 2 * c->nn);
   for (int64_t i = 0; i < ne; ++i) {
     if (!(Q[4 * i] > 0.0) || !(pressure(c, Q + 4 * i) > 0.0))
       return fail(c, OC_NONPHYSICAL, "initial state of element %lld is not physical", (long long)i);
@@ -1438,6 +1456,36 @@ int oc_load_state(oc_ctx* c, const double* Q) {
   c->gcl_checked = 0.0;
   c->have_state = rc == OC_OK;
   return rc;
+}
+
+int oc_load_state(oc_ctx* c, const double* Q) { return load_state(c, Q, NULL); }
+
+/* initial state on moved node positions; the mesh pre-processing (stencils,
+   total stencils, wall normals) stays that of oc_load_mesh */
+int oc_load_state_xy(oc_ctx* c, const double* Q, const double* xy) {
+  if (!xy) return OC_INVALID;
+  return load_state(c, Q, xy);
+}
+
+int oc_schedule(oc_ctx* c, int mode, int64_t k) {
+  if (!c || !c->tri || mode < 0 || mode > 2) return OC_INVALID;
+  if (mode != 0 && c->cfg.gts) return fail(c, OC_INVALID, "the schedule log is for local time stepping");
+  if (mode == 1) {
+    if (k < 1) return OC_INVALID;
+    free(c->sched_log);
+    c->sched_log = (int64_t*)calloc((size_t)c->ne_ * k, sizeof(int64_t));
+    c->sched_k = k;
+  } else if (mode == 2 && !c->sched_log) {
+    return fail(c, OC_STATE, "no recorded schedule to replay");
+  }
+  c->sched_mode = mode;
+  return OC_OK;
+}
+
+int oc_get_schedule(const oc_ctx* c, int64_t* out) {
+  if (!c || !c->sched_log || !out) return OC_INVALID;
+  memcpy(out, c->sched_log, sizeof(int64_t) * c->ne_ * c->sched_k);
+  return OC_OK;
 }
 
 /* one cycle of the LTS algorithm under the Jacobi reading R2 (Sec. 2.6) */

@@ -44,6 +44,15 @@ int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris,
                  const int32_t* tri, const int8_t* bc, const int8_t* shift,
                  const double* period);
 int oc_load_state(oc_ctx* c, const double* Q);
+/* oc_load_state on node positions xy [n_nodes][2]; stencils, total stencils
+   and wall normals stay those chosen by oc_load_mesh */
+int oc_load_state_xy(oc_ctx* c, const double* Q, const double* xy);
+/* frozen schedule (reading R12): mode 1 records the dt ticks every element
+   takes at each of its first k updates (count 0 = the initial step), mode 2
+   replays them instead of the CFL steps, mode 0 returns to free steps; the
+   log survives oc_load_state so that perturbed runs replay a base run */
+int oc_schedule(oc_ctx* c, int mode, int64_t k);
+int oc_get_schedule(const oc_ctx* c, int64_t* out); /* [n_tris][k] */
 int oc_sweep(oc_ctx* c, int64_t* n_updated);
 int oc_get_elem(const oc_ctx* c, double* Q, double* QM, double* HM, int64_t* t,
                 int64_t* dt, double* X, int64_t* count, double* qhat);

@@ -54,6 +54,9 @@ def _load():
             lib.oc_last_error.restype = C.c_char_p
             lib.oc_load_mesh.argtypes = [P, C.c_int64, P, C.c_int64, P, P, P, P]
             lib.oc_load_state.argtypes = [P, P]
+            lib.oc_load_state_xy.argtypes = [P, P, P]
+            lib.oc_schedule.argtypes = [P, C.c_int, C.c_int64]
+            lib.oc_get_schedule.argtypes = [P, P]
             lib.oc_sweep.argtypes = [P, C.POINTER(C.c_int64)]
             lib.oc_get_elem.argtypes = [P] + [P] * 8
             lib.oc_set_elem.argtypes = [P] + [P] * 8
@@ -134,6 +137,26 @@ class Oracle:
     def load_state(self, Q):
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         self._check(self.lib.oc_load_state(self.h, _ptr(Q)))
+
+    def load_state_xy(self, Q, xy):
+        """Initial state on moved node positions; the mesh pre-processing
+        (stencils, total stencils, wall normals) stays that of load_mesh."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self._check(self.lib.oc_load_state_xy(self.h, _ptr(Q), _ptr(xy)))
+
+    def schedule(self, mode, k=0):
+        """Frozen schedule: mode "record" logs the dt ticks of each element's
+        first k updates, "replay" reuses them, "free" returns to CFL steps."""
+        m = {"free": 0, "record": 1, "replay": 2}[mode]
+        self._check(self.lib.oc_schedule(self.h, m, k))
+        if m == 1:
+            self._sched_k = k
+
+    def get_schedule(self):
+        out = np.empty((self.n_tris, self._sched_k), np.int64)
+        self._check(self.lib.oc_get_schedule(self.h, _ptr(out)))
+        return out
 
     def sweep(self):
         n = C.c_int64(0)

@@ -25,7 +25,8 @@ EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load
             "aw_gts_step", "aw_advance_to", "aw_enqueue_sweeps", "aw_sync", "aw_get_state", "aw_get_nodes",
             "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
             "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_profile_enable", "aw_profile_read",
-            "aw_kernel_name", "aw_ready_set_noalloc", "aw_measure_fp64_peak"]
+            "aw_kernel_name", "aw_ready_set_noalloc", "aw_measure_fp64_peak", "aw_load_state_xy", "aw_schedule",
+            "aw_get_schedule", "aw_adjoint_forward", "aw_adjoint", "aw_adjoint_selftest"]
 
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +83,12 @@ def load(path: str | None = None):
             lib.aw_kernel_name.restype = C.c_char_p
             lib.aw_ready_set_noalloc.argtypes = [P, P, P]
             lib.aw_measure_fp64_peak.argtypes = [C.POINTER(C.c_double)]
+            lib.aw_load_state_xy.argtypes = [P, P, P]
+            lib.aw_schedule.argtypes = [P, C.c_int, i64]
+            lib.aw_get_schedule.argtypes = [P, P]
+            lib.aw_adjoint_forward.argtypes = [P, i64, i64]
+            lib.aw_adjoint.argtypes = [P, P, P, P, P, P]
+            lib.aw_adjoint_selftest.argtypes = [C.c_int, C.c_uint64, P]
             _lib = lib
     return _lib
 
@@ -100,6 +107,23 @@ def fp64_peak_gflops() -> float:
     if rc:
         raise AwError(rc, "aw_measure_fp64_peak")
     return v.value
+
+
+def adjoint_selftest(order_M: int, seed: int = 1):
+    """Largest relative mismatch of each element-level reverse (reconstruction,
+    predictor, edge flux, node solver) against central differences of its
+    forward, computed on the host (no GPU needed)."""
+    r = np.zeros(4)
+    rc = load().aw_adjoint_selftest(order_M, seed, _ptr(r))
+    if rc:
+        raise AwError(rc, "aw_adjoint_selftest")
+    return dict(recon=r[0], predictor=r[1], edge=r[2], node=r[3])
+
+
+def _f64(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
 
 
 class Solver:
@@ -173,6 +197,36 @@ class Solver:
         if not hasattr(Q, "data_ptr"):
             Q = np.ascontiguousarray(Q, dtype=np.float64)
         self._check(self.lib.aw_load_state(self.h, _ptr(Q)))
+
+    def load_state_xy(self, Q, xy):
+        """Initial state on node positions xy; the mesh pre-processing stays."""
+        Q, xy = _f64(Q), _f64(xy)
+        self._check(self.lib.aw_load_state_xy(self.h, _ptr(Q), _ptr(xy)))
+
+    def schedule(self, mode, k=0):
+        """Frozen schedule: "record" the dt ticks of each element's first k
+        updates, "replay" them, or "free" (CFL steps)."""
+        self._check(self.lib.aw_schedule(self.h, {"free": 0, "record": 1, "replay": 2}[mode], k))
+        if mode == "record":
+            self._sched_k = k
+
+    def get_schedule(self):
+        out = np.empty((self.n_tris, self._sched_k), np.int64)
+        self._check(self.lib.aw_get_schedule(self.h, _ptr(out)))
+        return out
+
+    def adjoint_forward(self, n_sweeps, ckpt_every=10):
+        """n_sweeps sweeps from the state just loaded, keeping checkpoints."""
+        self._check(self.lib.aw_adjoint_forward(self.h, n_sweeps, ckpt_every))
+
+    def adjoint(self, dJdQ=None, dJdX=None, dJdxy=None, out_Q=None, out_xy=None):
+        """dJ/dQ0 [n_tris,4] and dJ/dxy0 [n_nodes,2] of the recorded run from
+        dJ/d(final Q [n_tris,4], element corners [n_tris,6], nodes [n_nodes,2])."""
+        gQ = np.empty((self.n_tris, 4)) if out_Q is None else out_Q
+        gxy = np.empty((self.n_nodes, 2)) if out_xy is None else out_xy
+        self._check(self.lib.aw_adjoint(self.h, _ptr(_f64(dJdQ)), _ptr(_f64(dJdX)), _ptr(_f64(dJdxy)), _ptr(gQ),
+                                        _ptr(gxy)))
+        return gQ, gxy
 
     def sweep(self):
         n = C.c_int64(0)

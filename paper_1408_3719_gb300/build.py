@@ -1,6 +1,6 @@
 """Build the sm_103a shared library ``_build/libaleweno.so`` in-tree with nvcc.
 
-The two translation units compile in parallel; host code is compiled with
+The translation units compile in parallel; host code is compiled with
 ``-ffp-contract=off`` so that mesh pre-processing (stencil selection compares
 floating-point distances) rounds the same on x86 and Arm hosts.
 """
@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaleweno.so")
-SOURCES = ["aw_host.cu", "aw_kernels.cu", "aw_noalloc.cu"]
+SOURCES = ["aw_host.cu", "aw_kernels.cu", "aw_noalloc.cu", "aw_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 

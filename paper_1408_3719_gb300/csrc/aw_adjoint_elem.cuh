@@ -1,0 +1,1196 @@
+// Element-local pieces of one LTS sweep written serially, each with its
+// hand-written reverse (the discrete adjoint of the same arithmetic):
+//   recon_fwd / recon_rev   virtual data -> WENO nodal values w_h (eqs.
+//                           intConsRec, weno; characteristic weights R10)
+//   pred_fwd / pred_rev     w_h, vertices, dt -> space-time predictor and its
+//                           derived tables (eqs. PDECG, pdef, CGfinal, Jac,
+//                           newVertPos)
+//   edge_fwd / edge_rev     one swept edge surface: Gauss quadrature of the
+//                           Rusanov ALE flux (eqs. spacetimenodes, rusanov, STint)
+//   node_fwd / node_rev     node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
+// The integer schedule (ready sets, time steps in ticks) and the mesh
+// pre-processing (stencils, wall normals) are held fixed: the reverse
+// functions differentiate the sweep map for that schedule.  Every function is
+// __host__ __device__ so that the library can check each reverse against
+// central differences of its forward on the host.
+#pragma once
+#include <cmath>
+
+#include "aw_internal.h"
+
+#ifdef __CUDACC__
+#define AW_HD __host__ __device__
+#else
+#define AW_HD
+#endif
+
+namespace aw {
+namespace adj {
+
+template <int M>
+struct Sz {
+  static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, Nst = Mc * Nt, NU = Mc - 1, NE = 2 * Mc;
+  static constexpr int MaxU = kNSten * (NE - 1);
+  static constexpr int NL = NU * (NU + 1) / 2;
+};
+
+AW_HD inline double tri_area(const double* X) {
+  return 0.5 * ((X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0]));
+}
+// adds s * d|T|/dX to Xb
+AW_HD inline void tri_area_rev(const double* X, double s, double* Xb) {
+  Xb[0] += 0.5 * s * (X[3] - X[5]);
+  Xb[1] += 0.5 * s * (X[4] - X[2]);
+  Xb[2] += 0.5 * s * (X[5] - X[1]);
+  Xb[3] += 0.5 * s * (X[0] - X[4]);
+  Xb[4] += 0.5 * s * (X[1] - X[3]);
+  Xb[5] += 0.5 * s * (X[2] - X[0]);
+}
+
+// graded monomials of degree 1..M and their x, y derivatives
+template <int M>
+AW_HD inline void mono(double x, double y, double* m, double* mx, double* my) {
+  m[0] = x; mx[0] = 1; my[0] = 0;
+  m[1] = y; mx[1] = 0; my[1] = 1;
+  if (M >= 2) {
+    m[2] = x * x; mx[2] = 2 * x; my[2] = 0;
+    m[3] = x * y; mx[3] = y; my[3] = x;
+    m[4] = y * y; mx[4] = 0; my[4] = 2 * y;
+  }
+  if (M >= 3) {
+    m[5] = m[2] * x; mx[5] = 3 * x * x; my[5] = 0;
+    m[6] = m[2] * y; mx[6] = 2 * x * y; my[6] = x * x;
+    m[7] = m[4] * x; mx[7] = y * y; my[7] = 2 * x * y;
+    m[8] = m[4] * y; mx[8] = 0; my[8] = 3 * y * y;
+  }
+}
+
+// Euler fluxes f, g of one state and the reverse (adds to qb)
+AW_HD inline void euler_fg(double gm1, const double* q, double* f, double* g) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  f[0] = q[1]; f[1] = q[1] * u + p; f[2] = q[1] * v; f[3] = u * (q[3] + p);
+  g[0] = q[2]; g[1] = q[2] * u; g[2] = q[2] * v + p; g[3] = v * (q[3] + p);
+}
+AW_HD inline void euler_fg_rev(double gm1, const double* q, const double* fb, const double* gb, double* qb) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  double ub = fb[1] * q[1] + fb[3] * (q[3] + p) + gb[1] * q[2];
+  double vb = fb[2] * q[1] + gb[2] * q[2] + gb[3] * (q[3] + p);
+  const double pb = fb[1] + fb[3] * u + gb[2] + gb[3] * v;
+  double q1b = fb[0] + fb[1] * u + fb[2] * v;
+  double q2b = gb[0] + gb[1] * u + gb[2] * v;
+  double q3b = fb[3] * u + gb[3] * v;
+  q3b += gm1 * pb;
+  q1b -= 0.5 * gm1 * pb * u;
+  q2b -= 0.5 * gm1 * pb * v;
+  ub -= 0.5 * gm1 * pb * q[1];
+  vb -= 0.5 * gm1 * pb * q[2];
+  q1b += ub * ir;
+  q2b += vb * ir;
+  const double irb = ub * q[1] + vb * q[2];
+  qb[0] -= irb * ir * ir;
+  qb[1] += q1b;
+  qb[2] += q2b;
+  qb[3] += q3b;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction of one element
+// ---------------------------------------------------------------------------
+template <int M>
+struct ReconIn {
+  using S = Sz<M>;
+  double X[6], Q[4];                 // own vertices and average (after the update)
+  int nU;                            // distinct stencil members
+  double Xv[S::MaxU][6];             // members' virtual vertices, periodic shift applied
+  double Qv[S::MaxU][4];             // members' virtual averages
+  unsigned char st[kNSten][S::NE];   // stencil rows: 0 = the element, u + 1 = member u
+  signed char ok[kNSten];
+};
+
+template <int M>
+struct ReconTape {
+  using S = Sz<M>;
+  double ja, jb, jc, jd, idet, J[4];
+  double rows[S::MaxU + 1][S::NU + 4];
+  double Lf[kNSten][S::NL];      // Cholesky factors, diagonal stored as 1 / L_aa
+  double c[kNSten][S::NU][4];
+  double gx, gy, gn, nx, ny;
+  double R[16], Lm[16];
+  double ch[kNSten][S::NU][4];
+  double y[kNSten][4][S::NU];    // SigU ch
+  double e1[kNSten][4], om[kNSten][4], tot[4];
+  double wc[S::NU][4], cv[S::NU][4];
+  double w[S::Mc][4];            // nodal w_h
+  int limited;                   // the positivity scaling would change w_h
+};
+
+template <int M>
+AW_HD inline void chol_solve(const double* Lf, double* y) {
+  constexpr int NU = Sz<M>::NU;
+  for (int a = 0; a < NU; ++a) {
+    double acc = y[a];
+    for (int k = 0; k < a; ++k) acc -= Lf[a * (a + 1) / 2 + k] * y[k];
+    y[a] = acc * Lf[a * (a + 1) / 2 + a];
+  }
+  for (int a = NU - 1; a >= 0; --a) {
+    double acc = y[a];
+    for (int k = a + 1; k < NU; ++k) acc -= Lf[k * (k + 1) / 2 + a] * y[k];
+    y[a] = acc * Lf[a * (a + 1) / 2 + a];
+  }
+}
+
+AW_HD inline double pressure_of(double gm1, const double* q) {
+  return gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+}
+
+template <int M>
+AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE;
+  const double* X = in.X;
+  tp.ja = X[2] - X[0]; tp.jb = X[4] - X[0]; tp.jc = X[3] - X[1]; tp.jd = X[5] - X[1];
+  tp.idet = 1.0 / (tp.ja * tp.jd - tp.jb * tp.jc);
+  tp.J[0] = tp.jd * tp.idet; tp.J[1] = -tp.jb * tp.idet; tp.J[2] = -tp.jc * tp.idet; tp.J[3] = tp.ja * tp.idet;
+  const double* J = tp.J;
+  for (int u = 0; u < in.nU; ++u) {
+    double xr[3], yr[3];
+    for (int k = 0; k < 3; ++k) {
+      const double px = in.Xv[u][2 * k] - X[0], py = in.Xv[u][2 * k + 1] - X[1];
+      xr[k] = J[0] * px + J[1] * py - (1.0 / 3.0);
+      yr[k] = J[2] * px + J[3] * py - (1.0 / 3.0);
+    }
+    double row[NU];
+    for (int a = 0; a < NU; ++a) row[a] = 0.0;
+    for (int qq = 0; qq < T.nq; ++qq) {
+      const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
+      const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
+      double m[kMaxNU], mx[kMaxNU], my[kMaxNU];
+      mono<M>(x, y, m, mx, my);
+      for (int a = 0; a < NU; ++a) row[a] += T.qw[qq] * m[a];
+    }
+    double* dst = tp.rows[u + 1];
+    for (int a = 0; a < NU; ++a) dst[a] = row[a] - T.mbar[a];
+    for (int v = 0; v < 4; ++v) dst[NU + v] = in.Qv[u][v] - in.Q[v];
+  }
+  for (int s = 0; s < kNSten; ++s) {
+    if (!in.ok[s]) continue;
+    double Lw[NU][NU], b[NU][4];
+    for (int a = 0; a < NU; ++a) {
+      for (int bb = 0; bb <= a; ++bb) {
+        double acc = 0.0;
+        for (int m = 1; m < NE; ++m) {
+          const double* r = tp.rows[in.st[s][m]];
+          acc += r[a] * r[bb];
+        }
+        Lw[a][bb] = acc;
+      }
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int m = 1; m < NE; ++m) {
+          const double* r = tp.rows[in.st[s][m]];
+          acc += r[a] * r[NU + v];
+        }
+        b[a][v] = acc;
+      }
+    }
+    for (int a = 0; a < NU; ++a) {
+      double dd = Lw[a][a];
+      for (int k = 0; k < a; ++k) dd -= Lw[a][k] * Lw[a][k];
+      const double il = 1.0 / sqrt(dd);
+      Lw[a][a] = il;
+      for (int bb = a + 1; bb < NU; ++bb) {
+        double v = Lw[bb][a];
+        for (int k = 0; k < a; ++k) v -= Lw[bb][k] * Lw[a][k];
+        Lw[bb][a] = v * il;
+      }
+    }
+    for (int a = 0; a < NU; ++a)
+      for (int bb = 0; bb <= a; ++bb) tp.Lf[s][a * (a + 1) / 2 + bb] = Lw[a][bb];
+    for (int v = 0; v < 4; ++v) {
+      double y[NU];
+      for (int a = 0; a < NU; ++a) y[a] = b[a][v];
+      chol_solve<M>(tp.Lf[s], y);
+      for (int a = 0; a < NU; ++a) tp.c[s][a][v] = y[a];
+    }
+  }
+  // characteristic fields along the density gradient of the central stencil
+  tp.gx = tp.c[0][0][0] * J[0] + tp.c[0][1][0] * J[2];
+  tp.gy = tp.c[0][0][0] * J[1] + tp.c[0][1][0] * J[3];
+  tp.gn = sqrt(tp.gx * tp.gx + tp.gy * tp.gy);
+  tp.nx = 1.0; tp.ny = 0.0;
+  if (tp.gn > 0.0) { tp.nx = tp.gx / tp.gn; tp.ny = tp.gy / tp.gn; }
+  {
+    const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
+    const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
+    const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
+    const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
+    double* R = tp.R;
+    double* Lm = tp.Lm;
+    R[0] = 1; R[1] = 1; R[2] = 0; R[3] = 1;
+    R[4] = u - a * nx; R[5] = u; R[6] = -ny; R[7] = u + a * nx;
+    R[8] = v - a * ny; R[9] = v; R[10] = nx; R[11] = v + a * ny;
+    R[12] = H - a * un; R[13] = q2; R[14] = ut; R[15] = H + a * un;
+    Lm[0] = 0.5 * (b2 + un * ia); Lm[1] = -0.5 * (b1 * u + nx * ia); Lm[2] = -0.5 * (b1 * v + ny * ia); Lm[3] = 0.5 * b1;
+    Lm[4] = 1.0 - b2; Lm[5] = b1 * u; Lm[6] = b1 * v; Lm[7] = -b1;
+    Lm[8] = -ut; Lm[9] = -ny; Lm[10] = nx; Lm[11] = 0.0;
+    Lm[12] = 0.5 * (b2 - un * ia); Lm[13] = -0.5 * (b1 * u - nx * ia); Lm[14] = -0.5 * (b1 * v - ny * ia); Lm[15] = 0.5 * b1;
+  }
+  for (int s = 0; s < kNSten; ++s) {
+    if (!in.ok[s]) continue;
+    for (int r = 0; r < 4; ++r) {
+      const double* Lr = tp.Lm + 4 * r;
+      for (int l = 0; l < NU; ++l)
+        tp.ch[s][l][r] = Lr[0] * tp.c[s][l][0] + Lr[1] * tp.c[s][l][1] + Lr[2] * tp.c[s][l][2] + Lr[3] * tp.c[s][l][3];
+      double sg = 0.0;
+      for (int a = 0; a < NU; ++a) {
+        double acc = 0.0;
+        for (int bb = a; bb < NU; ++bb) acc += T.SigU[a][bb] * tp.ch[s][bb][r];
+        tp.y[s][r][a] = acc;
+        sg += acc * acc;
+      }
+      tp.e1[s][r] = sg + 1e-14;
+    }
+  }
+  for (int r = 0; r < 4; ++r) {
+    double tot = 0.0;
+    for (int s = 0; s < kNSten; ++s) {
+      tp.om[s][r] = 0.0;
+      if (!in.ok[s]) continue;
+      const double e1 = tp.e1[s][r], e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
+      tp.om[s][r] = (s == 0 ? 1e5 : 1.0) / e8;
+      tot += tp.om[s][r];
+    }
+    tp.tot[r] = tot;
+    const double itot = 1.0 / tot;
+    for (int l = 0; l < NU; ++l) {
+      double acc = 0.0;
+      for (int s = 0; s < kNSten; ++s)
+        if (in.ok[s]) acc += (tp.om[s][r] * itot) * tp.ch[s][l][r];
+      tp.wc[l][r] = acc;
+    }
+  }
+  for (int l = 0; l < NU; ++l)
+    for (int v = 0; v < 4; ++v) {
+      const double* Rv = tp.R + 4 * v;
+      tp.cv[l][v] = Rv[0] * tp.wc[l][0] + Rv[1] * tp.wc[l][1] + Rv[2] * tp.wc[l][2] + Rv[3] * tp.wc[l][3];
+    }
+  for (int s = 0; s < Mc; ++s)
+    for (int v = 0; v < 4; ++v) {
+      double acc = in.Q[v];
+      for (int l = 0; l < NU; ++l) acc += T.Bnod[s][l] * tp.cv[l][v];
+      tp.w[s][v] = acc;
+    }
+  // the positivity scaling (R11) is a kink: the reverse reports where it acts
+  const double gm1 = T.gamma - 1.0, rho_min = 1e-8 * in.Q[0], p_min = 1e-8 * pressure_of(gm1, in.Q);
+  tp.limited = 0;
+  for (int s = 0; s < Mc; ++s)
+    if (tp.w[s][0] < rho_min || pressure_of(gm1, tp.w[s]) < p_min) tp.limited = 1;
+}
+
+// Reverse of recon_fwd: wb = dJ/dw (Mc x 4); adds to Xb (6), Qb (4) of the
+// element and to Xvb, Qvb of the members (arrays zeroed by the caller).
+template <int M>
+AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp, const double (*wb)[4], double* Xb,
+                     double* Qb, double (*Xvb)[6], double (*Qvb)[4]) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE;
+  // w = Q + Bnod cv
+  double cvb[NU][4];
+  for (int v = 0; v < 4; ++v) {
+    double acc = 0.0;
+    for (int s = 0; s < Mc; ++s) acc += wb[s][v];
+    Qb[v] += acc;
+  }
+  for (int l = 0; l < NU; ++l)
+    for (int v = 0; v < 4; ++v) {
+      double acc = 0.0;
+      for (int s = 0; s < Mc; ++s) acc += T.Bnod[s][l] * wb[s][v];
+      cvb[l][v] = acc;
+    }
+  // cv = R wc
+  double wcb[NU][4], Rb[16], Lb[16];
+  for (int k = 0; k < 16; ++k) { Rb[k] = 0.0; Lb[k] = 0.0; }
+  for (int l = 0; l < NU; ++l)
+    for (int r = 0; r < 4; ++r) {
+      double acc = 0.0;
+      for (int v = 0; v < 4; ++v) acc += tp.R[4 * v + r] * cvb[l][v];
+      wcb[l][r] = acc;
+    }
+  for (int v = 0; v < 4; ++v)
+    for (int r = 0; r < 4; ++r) {
+      double acc = 0.0;
+      for (int l = 0; l < NU; ++l) acc += cvb[l][v] * tp.wc[l][r];
+      Rb[4 * v + r] = acc;
+    }
+  // weights and characteristic coefficients
+  double chb[kNSten][NU][4];
+  for (int s = 0; s < kNSten; ++s)
+    for (int l = 0; l < NU; ++l)
+      for (int r = 0; r < 4; ++r) chb[s][l][r] = 0.0;
+  for (int r = 0; r < 4; ++r) {
+    const double itot = 1.0 / tp.tot[r];
+    double omtb[kNSten], dot = 0.0;
+    for (int s = 0; s < kNSten; ++s) {
+      omtb[s] = 0.0;
+      if (!in.ok[s]) continue;
+      const double omt = tp.om[s][r] * itot;
+      double acc = 0.0;
+      for (int l = 0; l < NU; ++l) {
+        acc += wcb[l][r] * tp.ch[s][l][r];
+        chb[s][l][r] += omt * wcb[l][r];
+      }
+      omtb[s] = acc;
+      dot += acc * omt;
+    }
+    for (int s = 0; s < kNSten; ++s) {
+      if (!in.ok[s]) continue;
+      const double omb = (omtb[s] - dot) * itot;
+      const double sigb = omb * (-8.0 * tp.om[s][r] / tp.e1[s][r]);
+      // sigma = sum_a y_a^2, y = SigU ch
+      for (int a = 0; a < NU; ++a) {
+        const double yb = 2.0 * tp.y[s][r][a] * sigb;
+        for (int bb = a; bb < NU; ++bb) chb[s][bb][r] += T.SigU[a][bb] * yb;
+      }
+    }
+  }
+  // ch = Lm c
+  double cb[kNSten][NU][4];
+  for (int s = 0; s < kNSten; ++s) {
+    if (!in.ok[s]) continue;
+    for (int l = 0; l < NU; ++l)
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int r = 0; r < 4; ++r) {
+          acc += tp.Lm[4 * r + v] * chb[s][l][r];
+          Lb[4 * r + v] += chb[s][l][r] * tp.c[s][l][v];
+        }
+        cb[s][l][v] = acc;
+      }
+  }
+  // eigenvectors of the direction n and the state Q
+  double nxb = 0.0, nyb = 0.0;
+  {
+    const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
+    const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
+    const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny;
+    const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), ia = 1.0 / a;
+    double ub = 0, vb = 0, ab = 0, Hb = 0, unb = 0, utb = 0, q2b = 0, b1b = 0, b2b = 0, iab = 0;
+    const double* R_ = Rb;
+    ub += R_[4]; ab -= R_[4] * nx; nxb -= R_[4] * a;
+    ub += R_[5];
+    nyb -= R_[6];
+    ub += R_[7]; ab += R_[7] * nx; nxb += R_[7] * a;
+    vb += R_[8]; ab -= R_[8] * ny; nyb -= R_[8] * a;
+    vb += R_[9];
+    nxb += R_[10];
+    vb += R_[11]; ab += R_[11] * ny; nyb += R_[11] * a;
+    Hb += R_[12]; ab -= R_[12] * un; unb -= R_[12] * a;
+    q2b += R_[13];
+    utb += R_[14];
+    Hb += R_[15]; ab += R_[15] * un; unb += R_[15] * a;
+    const double* L_ = Lb;
+    b2b += 0.5 * L_[0]; unb += 0.5 * L_[0] * ia; iab += 0.5 * L_[0] * un;
+    b1b -= 0.5 * L_[1] * u; ub -= 0.5 * L_[1] * b1; nxb -= 0.5 * L_[1] * ia; iab -= 0.5 * L_[1] * nx;
+    b1b -= 0.5 * L_[2] * v; vb -= 0.5 * L_[2] * b1; nyb -= 0.5 * L_[2] * ia; iab -= 0.5 * L_[2] * ny;
+    b1b += 0.5 * L_[3];
+    b2b -= L_[4];
+    b1b += L_[5] * u; ub += L_[5] * b1;
+    b1b += L_[6] * v; vb += L_[6] * b1;
+    b1b -= L_[7];
+    utb -= L_[8];
+    nyb -= L_[9];
+    nxb += L_[10];
+    b2b += 0.5 * L_[12]; unb -= 0.5 * L_[12] * ia; iab -= 0.5 * L_[12] * un;
+    b1b -= 0.5 * L_[13] * u; ub -= 0.5 * L_[13] * b1; nxb += 0.5 * L_[13] * ia; iab += 0.5 * L_[13] * nx;
+    b1b -= 0.5 * L_[14] * v; vb -= 0.5 * L_[14] * b1; nyb += 0.5 * L_[14] * ia; iab += 0.5 * L_[14] * ny;
+    b1b += 0.5 * L_[15];
+    // b2 = b1 q2, b1 = (g-1)/a^2, ia = 1/a
+    b1b += b2b * q2; q2b += b2b * b1;
+    ab += b1b * (-2.0 * b1 / a);
+    ab -= iab * ia * ia;
+    // q2, un, ut
+    ub += q2b * u; vb += q2b * v;
+    ub += unb * nx; vb += unb * ny; nxb += unb * u; nyb += unb * v;
+    ub -= utb * ny; vb += utb * nx; nyb -= utb * u; nxb += utb * v;
+    // H = (E + p)/rho, a = sqrt(g p / rho)
+    double rhob = 0.0, pb = 0.0, Eb = 0.0;
+    Eb += Hb / rho; pb += Hb / rho; rhob -= Hb * H / rho;
+    pb += ab * g / (2.0 * a * rho); rhob -= ab * a / (2.0 * rho);
+    // p = (g-1)(E - rho (u^2+v^2)/2)
+    Eb += pb * (g - 1.0); rhob -= pb * (g - 1.0) * 0.5 * (u * u + v * v);
+    ub -= pb * (g - 1.0) * rho * u; vb -= pb * (g - 1.0) * rho * v;
+    // u = Q1 / rho, v = Q2 / rho
+    Qb[1] += ub / rho; rhob -= ub * u / rho;
+    Qb[2] += vb / rho; rhob -= vb * v / rho;
+    Qb[0] += rhob;
+    Qb[3] += Eb;
+  }
+  // n = g / |g|; g from the central stencil's linear coefficients and J
+  double Jb[4] = {0, 0, 0, 0};
+  if (tp.gn > 0.0) {
+    const double dn = tp.nx * nxb + tp.ny * nyb;
+    const double gxb = (nxb - tp.nx * dn) / tp.gn, gyb = (nyb - tp.ny * dn) / tp.gn;
+    cb[0][0][0] += gxb * tp.J[0] + gyb * tp.J[1];
+    cb[0][1][0] += gxb * tp.J[2] + gyb * tp.J[3];
+    Jb[0] += gxb * tp.c[0][0][0];
+    Jb[2] += gxb * tp.c[0][1][0];
+    Jb[1] += gyb * tp.c[0][0][0];
+    Jb[3] += gyb * tp.c[0][1][0];
+  }
+  // least-squares solves: c = N^-1 b, N = sum r r^T, b = sum r rhs^T
+  double rowb[S::MaxU + 1][NU + 4];
+  for (int u = 0; u <= in.nU; ++u)
+    for (int k = 0; k < NU + 4; ++k) rowb[u][k] = 0.0;
+  for (int s = 0; s < kNSten; ++s) {
+    if (!in.ok[s]) continue;
+    double lam[NU][4], Nb[NU][NU];
+    for (int v = 0; v < 4; ++v) {
+      double y[NU];
+      for (int a = 0; a < NU; ++a) y[a] = cb[s][a][v];
+      chol_solve<M>(tp.Lf[s], y);
+      for (int a = 0; a < NU; ++a) lam[a][v] = y[a];
+    }
+    for (int a = 0; a < NU; ++a)
+      for (int bb = 0; bb < NU; ++bb) {
+        double acc = 0.0;
+        for (int v = 0; v < 4; ++v) acc -= lam[a][v] * tp.c[s][bb][v];
+        Nb[a][bb] = acc;
+      }
+    for (int m = 1; m < NE; ++m) {
+      const int ri = in.st[s][m];
+      const double* r = tp.rows[ri];
+      double* rb = rowb[ri];
+      for (int k = 0; k < NU; ++k) {
+        double acc = 0.0;
+        for (int bb = 0; bb < NU; ++bb) acc += (Nb[k][bb] + Nb[bb][k]) * r[bb];
+        for (int v = 0; v < 4; ++v) acc += lam[k][v] * r[NU + v];
+        rb[k] += acc;
+      }
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int a = 0; a < NU; ++a) acc += lam[a][v] * r[a];
+        rb[NU + v] += acc;
+      }
+    }
+  }
+  // rows: basis averages over the virtual members, rhs Qv - Q
+  const double* X = in.X;
+  const double* J = tp.J;
+  for (int u = 0; u < in.nU; ++u) {
+    const double* rb = rowb[u + 1];
+    for (int v = 0; v < 4; ++v) {
+      Qvb[u][v] += rb[NU + v];
+      Qb[v] -= rb[NU + v];
+    }
+    double px[3], py[3], xr[3], yr[3];
+    for (int k = 0; k < 3; ++k) {
+      px[k] = in.Xv[u][2 * k] - X[0];
+      py[k] = in.Xv[u][2 * k + 1] - X[1];
+      xr[k] = J[0] * px[k] + J[1] * py[k] - (1.0 / 3.0);
+      yr[k] = J[2] * px[k] + J[3] * py[k] - (1.0 / 3.0);
+    }
+    double xrb[3] = {0, 0, 0}, yrb[3] = {0, 0, 0};
+    for (int qq = 0; qq < T.nq; ++qq) {
+      const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
+      const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
+      double m[kMaxNU], mx[kMaxNU], my[kMaxNU];
+      mono<M>(x, y, m, mx, my);
+      double xb = 0.0, yb = 0.0;
+      for (int a = 0; a < NU; ++a) {
+        xb += rb[a] * T.qw[qq] * mx[a];
+        yb += rb[a] * T.qw[qq] * my[a];
+      }
+      for (int k = 0; k < 3; ++k) {
+        xrb[k] += T.qb[qq][k] * xb;
+        yrb[k] += T.qb[qq][k] * yb;
+      }
+    }
+    for (int k = 0; k < 3; ++k) {
+      const double pxb = J[0] * xrb[k] + J[2] * yrb[k], pyb = J[1] * xrb[k] + J[3] * yrb[k];
+      Jb[0] += xrb[k] * px[k];
+      Jb[1] += xrb[k] * py[k];
+      Jb[2] += yrb[k] * px[k];
+      Jb[3] += yrb[k] * py[k];
+      Xvb[u][2 * k] += pxb;
+      Xvb[u][2 * k + 1] += pyb;
+      Xb[0] -= pxb;
+      Xb[1] -= pyb;
+    }
+  }
+  // J = inverse of the element's affine map
+  {
+    double jab = Jb[3] * tp.idet, jbb = -Jb[1] * tp.idet, jcb = -Jb[2] * tp.idet, jdb = Jb[0] * tp.idet;
+    const double idb = Jb[0] * tp.jd - Jb[1] * tp.jb - Jb[2] * tp.jc + Jb[3] * tp.ja;
+    const double detb = -idb * tp.idet * tp.idet;
+    jab += detb * tp.jd; jdb += detb * tp.ja; jbb -= detb * tp.jc; jcb -= detb * tp.jb;
+    Xb[2] += jab; Xb[0] -= jab;
+    Xb[4] += jbb; Xb[0] -= jbb;
+    Xb[3] += jcb; Xb[1] -= jcb;
+    Xb[5] += jdb; Xb[1] -= jdb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Predictor of one element and its derived tables
+// ---------------------------------------------------------------------------
+constexpr int kMaxIt = 8;  // Picard iterations the reverse can store
+
+template <int M>
+struct PredTape {
+  using S = Sz<M>;
+  double q[kMaxIt][S::Nst][4];   // iterate entering iteration it
+  double x[kMaxIt][S::Nst][2];
+  double qf[S::Nst][4];          // final predictor
+  int bad;                       // a non-physical node: the forward fell back to w_h
+};
+
+template <int M>
+struct PredTables {
+  using S = Sz<M>;
+  double tr[3][S::Nt][S::Nt][4];  // edge, Gauss point, tau power, variable
+  double av[S::Nt][4];
+  double vd[6][S::Nt];            // vertex k, component c -> [2k + c], powers 1..Nt
+};
+
+// nodal P and V of slice t of iterate (q, x); static = iteration 0 (no mesh
+// motion yet, so xi_t = eta_t = 0)
+template <int M>
+AW_HD inline void pred_node(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
+                            bool stat, double* P, double* V) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, Nt = S::Nt;
+  const double gm1 = T.gamma - 1.0;
+  double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
+  double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
+  double xx = 0, xe = 0, yx = 0, ye = 0;
+  for (int r = 0; r < Mc; ++r) {
+    const double a = T.Dxi[s][r], b = T.Deta[s][r];
+    const int lr = t * Mc + r;
+    double f[4], g[4];
+    euler_fg(gm1, q[lr], f, g);
+    for (int v = 0; v < 4; ++v) {
+      Qx[v] += a * q[lr][v]; Qe[v] += b * q[lr][v];
+      fx[v] += a * f[v]; fe[v] += b * f[v];
+      gx[v] += a * g[v]; ge[v] += b * g[v];
+    }
+    xx += a * x[lr][0]; xe += b * x[lr][0];
+    yx += a * x[lr][1]; ye += b * x[lr][1];
+  }
+  double xt = 0.0, yt = 0.0;
+  if (!stat) {
+    for (int u = 0; u < Nt; ++u) {
+      xt += T.Dtau[t][u] * x[u * Mc + s][0];
+      yt += T.Dtau[t][u] * x[u * Mc + s][1];
+    }
+    xt *= idt;
+    yt *= idt;
+  }
+  const double idet = 1.0 / (xx * ye - xe * yx);
+  const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+  const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
+  for (int v = 0; v < 4; ++v) {
+    const double fs = -(fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
+    P[v] = fs - (Qx[v] * xit + Qe[v] * ett);
+  }
+  const double* qs = q[t * Mc + s];
+  V[0] = T.eulerian ? 0.0 : qs[1] / qs[0];
+  V[1] = T.eulerian ? 0.0 : qs[2] / qs[0];
+}
+
+// reverse of pred_node: adds to qb, xb (whole iterate)
+template <int M>
+AW_HD inline void pred_node_rev(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
+                                bool stat, const double* Pb, const double* Vb, double (*qb)[4], double (*xb)[2]) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, Nt = S::Nt;
+  const double gm1 = T.gamma - 1.0;
+  double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
+  double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
+  double xx = 0, xe = 0, yx = 0, ye = 0;
+  for (int r = 0; r < Mc; ++r) {
+    const double a = T.Dxi[s][r], b = T.Deta[s][r];
+    const int lr = t * Mc + r;
+    double f[4], g[4];
+    euler_fg(gm1, q[lr], f, g);
+    for (int v = 0; v < 4; ++v) {
+      Qx[v] += a * q[lr][v]; Qe[v] += b * q[lr][v];
+      fx[v] += a * f[v]; fe[v] += b * f[v];
+      gx[v] += a * g[v]; ge[v] += b * g[v];
+    }
+    xx += a * x[lr][0]; xe += b * x[lr][0];
+    yx += a * x[lr][1]; ye += b * x[lr][1];
+  }
+  double xt = 0.0, yt = 0.0;
+  if (!stat) {
+    for (int u = 0; u < Nt; ++u) {
+      xt += T.Dtau[t][u] * x[u * Mc + s][0];
+      yt += T.Dtau[t][u] * x[u * Mc + s][1];
+    }
+    xt *= idt;
+    yt *= idt;
+  }
+  const double idet = 1.0 / (xx * ye - xe * yx);
+  const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+  const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
+  double Qxb[4], Qeb[4], fxb[4], feb[4], gxb[4], geb[4];
+  double xixb = 0, xiyb = 0, etxb = 0, etyb = 0, xitb = 0, ettb = 0;
+  for (int v = 0; v < 4; ++v) {
+    Qxb[v] = -Pb[v] * xit; Qeb[v] = -Pb[v] * ett;
+    xitb -= Pb[v] * Qx[v]; ettb -= Pb[v] * Qe[v];
+    fxb[v] = -Pb[v] * xix; feb[v] = -Pb[v] * etx; gxb[v] = -Pb[v] * xiy; geb[v] = -Pb[v] * ety;
+    xixb -= Pb[v] * fx[v]; etxb -= Pb[v] * fe[v]; xiyb -= Pb[v] * gx[v]; etyb -= Pb[v] * ge[v];
+  }
+  double xtb = 0, ytb = 0;
+  xixb -= xitb * xt; xiyb -= xitb * yt; xtb -= xitb * xix; ytb -= xitb * xiy;
+  etxb -= ettb * xt; etyb -= ettb * yt; xtb -= ettb * etx; ytb -= ettb * ety;
+  double xxb = 0, xeb = 0, yxb = 0, yeb = 0, idb = 0;
+  yeb += xixb * idet; idb += xixb * ye;
+  xeb -= xiyb * idet; idb -= xiyb * xe;
+  yxb -= etxb * idet; idb -= etxb * yx;
+  xxb += etyb * idet; idb += etyb * xx;
+  const double detb = -idb * idet * idet;
+  xxb += detb * ye; yeb += detb * xx; xeb -= detb * yx; yxb -= detb * xe;
+  if (!stat) {
+    for (int u = 0; u < Nt; ++u) {
+      xb[u * Mc + s][0] += idt * T.Dtau[t][u] * xtb;
+      xb[u * Mc + s][1] += idt * T.Dtau[t][u] * ytb;
+    }
+  }
+  for (int r = 0; r < Mc; ++r) {
+    const double a = T.Dxi[s][r], b = T.Deta[s][r];
+    const int lr = t * Mc + r;
+    xb[lr][0] += a * xxb + b * xeb;
+    xb[lr][1] += a * yxb + b * yeb;
+    double fb[4], gb[4];
+    for (int v = 0; v < 4; ++v) {
+      qb[lr][v] += a * Qxb[v] + b * Qeb[v];
+      fb[v] = a * fxb[v] + b * feb[v];
+      gb[v] = a * gxb[v] + b * geb[v];
+    }
+    euler_fg_rev(gm1, q[lr], fb, gb, qb[lr]);
+  }
+  if (!T.eulerian) {
+    const int l = t * Mc + s;
+    const double ir = 1.0 / q[l][0];
+    qb[l][1] += Vb[0] * ir;
+    qb[l][2] += Vb[1] * ir;
+    qb[l][0] -= (Vb[0] * q[l][1] + Vb[1] * q[l][2]) * ir * ir;
+  }
+}
+
+template <int M>
+AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X, double dts, PredTape<M>& tp,
+                    PredTables<M>& out) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
+  double q[Nst][4], x[Nst][2];
+  for (int t = 0; t < Nt; ++t)
+    for (int s = 0; s < Mc; ++s) {
+      const int l = t * Mc + s;
+      for (int v = 0; v < 4; ++v) q[l][v] = w[s][v];
+      x[l][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
+      x[l][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
+    }
+  const double idt = nit > 0 ? 1.0 / dts : 0.0;
+  for (int it = 0; it < nit; ++it) {
+    for (int l = 0; l < Nst; ++l) {
+      for (int v = 0; v < 4; ++v) tp.q[it][l][v] = q[l][v];
+      tp.x[it][l][0] = x[l][0];
+      tp.x[it][l][1] = x[l][1];
+    }
+    double P[Nst][4], V[Nst][2];
+    const int nsl = it == 0 ? 1 : Nt;
+    for (int t = 0; t < nsl; ++t)
+      for (int s = 0; s < Mc; ++s) pred_node<M>(T, tp.q[it], tp.x[it], t, s, idt, it == 0, P[t * Mc + s], V[t * Mc + s]);
+    for (int t = 1; t < Nt; ++t)
+      for (int s = 0; s < Mc; ++s) {
+        const int l = t * Mc + s;
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+          for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * P[(it == 0 ? 0 : u) * Mc + s][v];
+          q[l][v] = tp.q[it][s][v] + dts * acc;
+        }
+        for (int c = 0; c < 2; ++c) {
+          double acc = 0.0;
+          for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * V[(it == 0 ? 0 : u) * Mc + s][c];
+          x[l][c] = tp.x[it][s][c] + dts * acc;
+        }
+      }
+  }
+  const double gm1 = T.gamma - 1.0;
+  tp.bad = 0;
+  for (int l = 0; l < Nst; ++l)
+    if (!(q[l][0] > 0.0) || !(pressure_of(gm1, q[l]) > 0.0)) tp.bad = 1;
+  for (int l = 0; l < Nst; ++l)
+    for (int v = 0; v < 4; ++v) tp.qf[l][v] = q[l][v];
+  // derived tables
+  for (int e = 0; e < 3; ++e)
+    for (int g = 0; g < Nt; ++g)
+      for (int v = 0; v < 4; ++v) {
+        double val[Nt];
+        for (int tt = 0; tt < Nt; ++tt) {
+          double acc = 0.0;
+          for (int r = 0; r < Mc; ++r) acc += T.Tr[e][g][r] * q[tt * Mc + r][v];
+          val[tt] = acc;
+        }
+        for (int p = 0; p < Nt; ++p) {
+          double acc = 0.0;
+          for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
+          out.tr[e][g][p][v] = acc;
+        }
+      }
+  for (int v = 0; v < 4; ++v) {
+    double val[Nt];
+    for (int tt = 0; tt < Nt; ++tt) {
+      double acc = 0.0;
+      for (int r = 0; r < Mc; ++r) acc += T.wavg[r] * q[tt * Mc + r][v];
+      val[tt] = acc;
+    }
+    for (int p = 0; p < Nt; ++p) {
+      double acc = 0.0;
+      for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
+      out.av[p][v] = acc;
+    }
+  }
+  for (int kc = 0; kc < 6; ++kc) {
+    const int k = kc / 2, c = kc % 2, sn = T.vnode[k];
+    double vel[Nt];
+    for (int tt = 0; tt < Nt; ++tt) {
+      const double* qq = q[tt * Mc + sn];
+      vel[tt] = T.eulerian ? 0.0 : qq[1 + c] / qq[0];
+    }
+    for (int p = 0; p < Nt; ++p) {
+      double acc = 0.0;
+      for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * vel[tt];
+      out.vd[kc][p] = acc / (p + 1);
+    }
+  }
+}
+
+// Reverse of pred_fwd: tb = dJ/d(tables); adds to wb (Mc x 4) and Xb (6).
+template <int M>
+AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, const PredTables<M>& tb,
+                    double (*wb)[4], double* Xb) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
+  double qb[Nst][4], xb[Nst][2];
+  for (int l = 0; l < Nst; ++l) {
+    for (int v = 0; v < 4; ++v) qb[l][v] = 0.0;
+    xb[l][0] = xb[l][1] = 0.0;
+  }
+  // tables
+  for (int e = 0; e < 3; ++e)
+    for (int g = 0; g < Nt; ++g)
+      for (int v = 0; v < 4; ++v)
+        for (int tt = 0; tt < Nt; ++tt) {
+          double valb = 0.0;
+          for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.tr[e][g][p][v];
+          for (int r = 0; r < Mc; ++r) qb[tt * Mc + r][v] += T.Tr[e][g][r] * valb;
+        }
+  for (int v = 0; v < 4; ++v)
+    for (int tt = 0; tt < Nt; ++tt) {
+      double valb = 0.0;
+      for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.av[p][v];
+      for (int r = 0; r < Mc; ++r) qb[tt * Mc + r][v] += T.wavg[r] * valb;
+    }
+  if (!T.eulerian)
+    for (int kc = 0; kc < 6; ++kc) {
+      const int k = kc / 2, c = kc % 2, sn = T.vnode[k];
+      for (int tt = 0; tt < Nt; ++tt) {
+        double velb = 0.0;
+        for (int p = 0; p < Nt; ++p) velb += T.VtInv[p][tt] * tb.vd[kc][p] / (p + 1);
+        const double* qq = tp.qf[tt * Mc + sn];
+        qb[tt * Mc + sn][1 + c] += velb / qq[0];
+        qb[tt * Mc + sn][0] -= velb * qq[1 + c] / (qq[0] * qq[0]);
+      }
+    }
+  // Picard iterations in reverse
+  const double idt = nit > 0 ? 1.0 / dts : 0.0;
+  for (int it = nit - 1; it >= 0; --it) {
+    double Pb[Nst][4], Vb[Nst][2];
+    for (int l = 0; l < Nst; ++l) {
+      for (int v = 0; v < 4; ++v) Pb[l][v] = 0.0;
+      Vb[l][0] = Vb[l][1] = 0.0;
+    }
+    double qo[Nst][4], xo[Nst][2];  // adjoint of the iterate entering it
+    for (int s = 0; s < Mc; ++s) {
+      for (int v = 0; v < 4; ++v) qo[s][v] = qb[s][v];
+      xo[s][0] = xb[s][0];
+      xo[s][1] = xb[s][1];
+    }
+    for (int l = Mc; l < Nst; ++l) {
+      for (int v = 0; v < 4; ++v) qo[l][v] = 0.0;
+      xo[l][0] = xo[l][1] = 0.0;
+    }
+    for (int t = 1; t < Nt; ++t)
+      for (int s = 0; s < Mc; ++s) {
+        const int l = t * Mc + s;
+        for (int v = 0; v < 4; ++v) {
+          qo[s][v] += qb[l][v];
+          for (int u = 0; u < Nt; ++u) Pb[(it == 0 ? 0 : u) * Mc + s][v] += dts * T.B[t - 1][u] * qb[l][v];
+        }
+        for (int c = 0; c < 2; ++c) {
+          xo[s][c] += xb[l][c];
+          for (int u = 0; u < Nt; ++u) Vb[(it == 0 ? 0 : u) * Mc + s][c] += dts * T.B[t - 1][u] * xb[l][c];
+        }
+      }
+    const int nsl = it == 0 ? 1 : Nt;
+    for (int t = 0; t < nsl; ++t)
+      for (int s = 0; s < Mc; ++s)
+        pred_node_rev<M>(T, tp.q[it], tp.x[it], t, s, idt, it == 0, Pb[t * Mc + s], Vb[t * Mc + s], qo, xo);
+    for (int l = 0; l < Nst; ++l) {
+      for (int v = 0; v < 4; ++v) qb[l][v] = qo[l][v];
+      xb[l][0] = xo[l][0];
+      xb[l][1] = xo[l][1];
+    }
+  }
+  // initial iterate: q = w on every slice, x = lattice positions
+  for (int s = 0; s < Mc; ++s) {
+    double x0b = 0.0, x1b = 0.0;
+    for (int t = 0; t < Nt; ++t) {
+      for (int v = 0; v < 4; ++v) wb[s][v] += qb[t * Mc + s][v];
+      x0b += xb[t * Mc + s][0];
+      x1b += xb[t * Mc + s][1];
+    }
+    const double l0 = T.lat[s][0], l1 = T.lat[s][1];
+    Xb[0] += x0b * (1.0 - l0 - l1); Xb[2] += x0b * l0; Xb[4] += x0b * l1;
+    Xb[1] += x1b * (1.0 - l0 - l1); Xb[3] += x1b * l0; Xb[5] += x1b * l1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One swept edge surface
+// ---------------------------------------------------------------------------
+template <int M>
+struct EdgeIn {
+  using S = Sz<M>;
+  double P[4][2];                 // old a, old b, new b, new a (periodic shift applied)
+  double tk[4];                   // their ticks
+  double tsec;                    // seconds per tick
+  double trL[S::Nt][S::Nt][4];    // left trace: Gauss point, tau power, variable
+  double trR[S::Nt][S::Nt][4];    // right trace, its own Gauss point order
+  double tL, dtL, tR, dtR;        // ticks of the two sides
+  int has_R, bc;                  // bc 0 wall, 1 transmissive (no right side)
+};
+
+AW_HD inline void rusanov_fwd(double g, const double* qm, const double* qp, const double* n, double* F) {
+  const double rim = 1.0 / qm[0], rip = 1.0 / qp[0];
+  const double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
+  const double pm = (g - 1.0) * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
+  const double pp = (g - 1.0) * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
+  const double nn2 = n[0] * n[0] + n[1] * n[1];
+  const double cmn = sqrt(g * pm * rim * nn2), cpn = sqrt(g * pp * rip * nn2);
+  const double wm = um * n[0] + vm * n[1] + n[2], wp = up * n[0] + vp * n[1] + n[2];
+  const double sm = fabs(wm) + cmn, sp = fabs(wp) + cpn;
+  const double smax = fmax(sm, sp);
+  const double vnm = um * n[0] + vm * n[1], vnp = up * n[0] + vp * n[1];
+  const double Fm[4] = {qm[0] * wm, qm[1] * wm + pm * n[0], qm[2] * wm + pm * n[1], qm[3] * wm + pm * vnm};
+  const double Fp[4] = {qp[0] * wp, qp[1] * wp + pp * n[0], qp[2] * wp + pp * n[1], qp[3] * wp + pp * vnp};
+  for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
+}
+
+// one side's contribution F_side(q) = q w + p (0, n0, n1, vn), w = v.n + n2;
+// adds its reverse to qb, nb
+AW_HD inline void side_flux_rev(double g, const double* q, const double* n, const double* Fb, double* qb, double* nb) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  const double w = u * n[0] + v * n[1] + n[2], vn = u * n[0] + v * n[1];
+  double wb = 0.0, pb = 0.0, vnb = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    qb[k] += Fb[k] * w;
+    wb += Fb[k] * q[k];
+  }
+  pb += Fb[1] * n[0] + Fb[2] * n[1] + Fb[3] * vn;
+  nb[0] += Fb[1] * p;
+  nb[1] += Fb[2] * p;
+  vnb += Fb[3] * p;
+  double ub = wb * n[0] + vnb * n[0], vb = wb * n[1] + vnb * n[1];
+  nb[0] += (wb + vnb) * u;
+  nb[1] += (wb + vnb) * v;
+  nb[2] += wb;
+  // p = (g-1)(E - (q1 u + q2 v)/2)
+  qb[3] += pb * (g - 1.0);
+  qb[1] -= 0.5 * (g - 1.0) * pb * u;
+  qb[2] -= 0.5 * (g - 1.0) * pb * v;
+  ub -= 0.5 * (g - 1.0) * pb * q[1];
+  vb -= 0.5 * (g - 1.0) * pb * q[2];
+  qb[1] += ub * ir;
+  qb[2] += vb * ir;
+  qb[0] -= (ub * q[1] + vb * q[2]) * ir * ir;
+}
+
+// wave-speed bound s = |v.n + n2| + sqrt(g p / rho * |n_xy|^2); reverse adds sb ds
+AW_HD inline double speed_of(double g, const double* q, const double* n) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  const double nn2 = n[0] * n[0] + n[1] * n[1];
+  return fabs(u * n[0] + v * n[1] + n[2]) + sqrt(g * p * ir * nn2);
+}
+AW_HD inline void speed_rev(double g, const double* q, const double* n, double sb, double* qb, double* nb) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  const double nn2 = n[0] * n[0] + n[1] * n[1];
+  const double w = u * n[0] + v * n[1] + n[2];
+  const double cn = sqrt(g * p * ir * nn2);
+  const double wb = w >= 0.0 ? sb : -sb;
+  double ub = wb * n[0], vb = wb * n[1];
+  nb[0] += wb * u;
+  nb[1] += wb * v;
+  nb[2] += wb;
+  if (cn > 0.0) {
+    const double zb = sb / (2.0 * cn);  // z = g p ir nn2
+    const double pb = zb * g * ir * nn2;
+    const double irb = zb * g * p * nn2;
+    const double nn2b = zb * g * p * ir;
+    nb[0] += 2.0 * n[0] * nn2b;
+    nb[1] += 2.0 * n[1] * nn2b;
+    qb[3] += pb * (g - 1.0);
+    qb[1] -= 0.5 * (g - 1.0) * pb * u;
+    qb[2] -= 0.5 * (g - 1.0) * pb * v;
+    ub -= 0.5 * (g - 1.0) * pb * q[1];
+    vb -= 0.5 * (g - 1.0) * pb * q[2];
+    qb[0] -= irb * ir * ir;
+  }
+  qb[1] += ub * ir;
+  qb[2] += vb * ir;
+  qb[0] -= (ub * q[1] + vb * q[2]) * ir * ir;
+}
+
+template <int M>
+AW_HD inline void edge_point(const Tab& T, const EdgeIn<M>& in, int gx, int gt, double* qm, double* qp, double* n,
+                             double* dchi, double* dtau, double* tl, double* tr) {
+  constexpr int Nt = Sz<M>::Nt;
+  const double chi = T.glx[gx], tau = T.glx[gt];
+  double P[4][3];
+  for (int k = 0; k < 4; ++k) {
+    P[k][0] = in.P[k][0];
+    P[k][1] = in.P[k][1];
+    P[k][2] = in.tk[k] * in.tsec;
+  }
+  for (int c = 0; c < 3; ++c) {
+    dchi[c] = (1.0 - tau) * (P[1][c] - P[0][c]) + tau * (P[2][c] - P[3][c]);
+    dtau[c] = (1.0 - chi) * (P[3][c] - P[0][c]) + chi * (P[2][c] - P[1][c]);
+  }
+  n[0] = dchi[1] * dtau[2] - dchi[2] * dtau[1];
+  n[1] = dchi[2] * dtau[0] - dchi[0] * dtau[2];
+  n[2] = dchi[0] * dtau[1] - dchi[1] * dtau[0];
+  const double tt = (1 - chi) * (1 - tau) * in.tk[0] + chi * (1 - tau) * in.tk[1] + chi * tau * in.tk[2] +
+                    (1 - chi) * tau * in.tk[3];
+  *tl = in.dtL > 0 ? (tt - in.tL) / in.dtL : 0.0;
+  for (int v = 0; v < 4; ++v) {
+    double acc = in.trL[gx][Nt - 1][v];
+    for (int p = Nt - 2; p >= 0; --p) acc = acc * *tl + in.trL[gx][p][v];
+    qm[v] = acc;
+  }
+  *tr = 0.0;
+  if (in.has_R) {
+    *tr = in.dtR > 0 ? (tt - in.tR) / in.dtR : 0.0;
+    for (int v = 0; v < 4; ++v) {
+      double acc = in.trR[Nt - 1 - gx][Nt - 1][v];
+      for (int p = Nt - 2; p >= 0; --p) acc = acc * *tr + in.trR[Nt - 1 - gx][p][v];
+      qp[v] = acc;
+    }
+  } else {
+    for (int v = 0; v < 4; ++v) qp[v] = qm[v];
+    if (in.bc == 0) {
+      const double nn = n[0] * n[0] + n[1] * n[1];
+      if (nn > 0.0) {
+        const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+        qp[1] = qm[1] - 2.0 * mn * n[0];
+        qp[2] = qm[2] - 2.0 * mn * n[1];
+      }
+    }
+  }
+}
+
+template <int M>
+AW_HD void edge_fwd(const Tab& T, const EdgeIn<M>& in, double* G) {
+  constexpr int Nt = Sz<M>::Nt;
+  for (int v = 0; v < 4; ++v) G[v] = 0.0;
+  for (int gx = 0; gx < Nt; ++gx)
+    for (int gt = 0; gt < Nt; ++gt) {
+      double qm[4], qp[4], n[3], dchi[3], dtau[3], tl, tr, F[4];
+      edge_point<M>(T, in, gx, gt, qm, qp, n, dchi, dtau, &tl, &tr);
+      rusanov_fwd(T.gamma, qm, qp, n, F);
+      const double wq = T.glw[gx] * T.glw[gt];
+      for (int v = 0; v < 4; ++v) G[v] += wq * F[v];
+    }
+}
+
+// reverse of edge_fwd: adds to Pb[4][2] and the two traces' adjoints
+template <int M>
+AW_HD void edge_rev(const Tab& T, const EdgeIn<M>& in, const double* Gb, double (*Pb)[2], double (*trLb)[Sz<M>::Nt][4],
+                    double (*trRb)[Sz<M>::Nt][4]) {
+  constexpr int Nt = Sz<M>::Nt;
+  const double g = T.gamma;
+  for (int gx = 0; gx < Nt; ++gx)
+    for (int gt = 0; gt < Nt; ++gt) {
+      double qm[4], qp[4], n[3], dchi[3], dtau[3], tl, tr;
+      edge_point<M>(T, in, gx, gt, qm, qp, n, dchi, dtau, &tl, &tr);
+      const double wq = T.glw[gx] * T.glw[gt];
+      double Fb[4];
+      for (int v = 0; v < 4; ++v) Fb[v] = wq * Gb[v];
+      double qmb[4] = {0, 0, 0, 0}, qpb[4] = {0, 0, 0, 0}, nb[3] = {0, 0, 0};
+      // F = (Fm + Fp)/2 - smax (qp - qm)/2
+      const double sm = speed_of(g, qm, n), sp = speed_of(g, qp, n), smax = fmax(sm, sp);
+      double half[4], smaxb = 0.0;
+      for (int v = 0; v < 4; ++v) {
+        half[v] = 0.5 * Fb[v];
+        smaxb -= 0.5 * Fb[v] * (qp[v] - qm[v]);
+        qpb[v] -= 0.5 * smax * Fb[v];
+        qmb[v] += 0.5 * smax * Fb[v];
+      }
+      side_flux_rev(g, qm, n, half, qmb, nb);
+      side_flux_rev(g, qp, n, half, qpb, nb);
+      if (sm >= sp) speed_rev(g, qm, n, smaxb, qmb, nb);
+      else speed_rev(g, qp, n, smaxb, qpb, nb);
+      // right state
+      if (in.has_R) {
+        double tp_ = 1.0;
+        for (int p = 0; p < Nt; ++p) {
+          for (int v = 0; v < 4; ++v) trRb[Nt - 1 - gx][p][v] += qpb[v] * tp_;
+          tp_ *= tr;
+        }
+      } else {
+        for (int v = 0; v < 4; ++v) qmb[v] += (v == 1 || v == 2) ? 0.0 : qpb[v];
+        const double nn = n[0] * n[0] + n[1] * n[1];
+        if (in.bc == 0 && nn > 0.0) {
+          const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+          qmb[1] += qpb[1];
+          qmb[2] += qpb[2];
+          const double mnb = -2.0 * (qpb[1] * n[0] + qpb[2] * n[1]);
+          nb[0] -= 2.0 * mn * qpb[1];
+          nb[1] -= 2.0 * mn * qpb[2];
+          qmb[1] += mnb * n[0] / nn;
+          qmb[2] += mnb * n[1] / nn;
+          nb[0] += mnb * qm[1] / nn;
+          nb[1] += mnb * qm[2] / nn;
+          const double nnb = -mnb * mn / nn;
+          nb[0] += 2.0 * n[0] * nnb;
+          nb[1] += 2.0 * n[1] * nnb;
+        } else {
+          qmb[1] += qpb[1];
+          qmb[2] += qpb[2];
+        }
+      }
+      {
+        double tp_ = 1.0;
+        for (int p = 0; p < Nt; ++p) {
+          for (int v = 0; v < 4; ++v) trLb[gx][p][v] += qmb[v] * tp_;
+          tp_ *= tl;
+        }
+      }
+      // n = dchi x dtau (spatial components of the corners only)
+      double dchib[3], dtaub[3];
+      dchib[0] = dtau[1] * nb[2] - dtau[2] * nb[1];
+      dchib[1] = dtau[2] * nb[0] - dtau[0] * nb[2];
+      dchib[2] = dtau[0] * nb[1] - dtau[1] * nb[0];
+      dtaub[0] = nb[1] * dchi[2] - nb[2] * dchi[1];
+      dtaub[1] = nb[2] * dchi[0] - nb[0] * dchi[2];
+      dtaub[2] = nb[0] * dchi[1] - nb[1] * dchi[0];
+      const double chi = T.glx[gx], tau = T.glx[gt];
+      for (int c = 0; c < 2; ++c) {
+        Pb[1][c] += (1.0 - tau) * dchib[c]; Pb[0][c] -= (1.0 - tau) * dchib[c];
+        Pb[2][c] += tau * dchib[c]; Pb[3][c] -= tau * dchib[c];
+        Pb[3][c] += (1.0 - chi) * dtaub[c]; Pb[0][c] -= (1.0 - chi) * dtaub[c];
+        Pb[2][c] += chi * dtaub[c]; Pb[1][c] -= chi * dtaub[c];
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Node solver for one node: mass-weighted mean of the Voronoi elements'
+// time-integrated vertex velocities over [tau0, tau1] of each element
+// ---------------------------------------------------------------------------
+template <int M>
+struct NodeElem {
+  double rho, X[6];       // element average density and vertices (sweep start)
+  double vd[2][Sz<M>::Nt];// vertex displacement coefficients of this node, x and y
+  double tau0, tau1, dts; // dts = 0: the element has finished (no motion)
+};
+
+template <int M>
+AW_HD inline void node_elem_disp(const NodeElem<M>& e, double* D) {
+  constexpr int Nt = Sz<M>::Nt;
+  D[0] = D[1] = 0.0;
+  if (!(e.dts > 0.0)) return;
+  for (int c = 0; c < 2; ++c) {
+    double a0 = e.vd[c][Nt - 1], a1 = e.vd[c][Nt - 1];
+    for (int p = Nt - 2; p >= 0; --p) {
+      a0 = a0 * e.tau0 + e.vd[c][p];
+      a1 = a1 * e.tau1 + e.vd[c][p];
+    }
+    D[c] = e.dts * (a1 * e.tau1 - a0 * e.tau0);
+  }
+}
+
+template <int M>
+AW_HD void node_fwd(int nv, const NodeElem<M>* el, int type, const double* nrm, double* D) {
+  double num0 = 0.0, num1 = 0.0, den = 0.0;
+  for (int k = 0; k < nv; ++k) {
+    const double mu = el[k].rho * tri_area(el[k].X);
+    double Dk[2];
+    node_elem_disp<M>(el[k], Dk);
+    num0 += mu * Dk[0];
+    num1 += mu * Dk[1];
+    den += mu;
+  }
+  D[0] = num0 / den;
+  D[1] = num1 / den;
+  if (type == 1) {
+    const double dn = D[0] * nrm[0] + D[1] * nrm[1];
+    D[0] -= dn * nrm[0];
+    D[1] -= dn * nrm[1];
+  } else if (type == 2) {
+    D[0] = D[1] = 0.0;
+  }
+}
+
+// reverse: Db = dJ/dD; adds to rhob[k], Xb[k][6], vdb[k][2][Nt]
+template <int M>
+AW_HD void node_rev(int nv, const NodeElem<M>* el, int type, const double* nrm, const double* Db_in, double* rhob,
+                    double (*Xb)[6], double (*vdb)[2][Sz<M>::Nt]) {
+  constexpr int Nt = Sz<M>::Nt;
+  double Db[2] = {Db_in[0], Db_in[1]};
+  if (type == 1) {
+    const double dn = Db[0] * nrm[0] + Db[1] * nrm[1];
+    Db[0] -= dn * nrm[0];
+    Db[1] -= dn * nrm[1];
+  } else if (type == 2) {
+    return;
+  }
+  double num0 = 0.0, num1 = 0.0, den = 0.0;
+  for (int k = 0; k < nv; ++k) {
+    const double mu = el[k].rho * tri_area(el[k].X);
+    double Dk[2];
+    node_elem_disp<M>(el[k], Dk);
+    num0 += mu * Dk[0];
+    num1 += mu * Dk[1];
+    den += mu;
+  }
+  const double D0 = num0 / den, D1 = num1 / den;
+  const double n0b = Db[0] / den, n1b = Db[1] / den, denb = -(Db[0] * D0 + Db[1] * D1) / den;
+  for (int k = 0; k < nv; ++k) {
+    const double area = tri_area(el[k].X), mu = el[k].rho * area;
+    double Dk[2];
+    node_elem_disp<M>(el[k], Dk);
+    const double mub = n0b * Dk[0] + n1b * Dk[1] + denb;
+    rhob[k] += mub * area;
+    tri_area_rev(el[k].X, mub * el[k].rho, Xb[k]);
+    if (el[k].dts > 0.0) {
+      const double Dkb[2] = {n0b * mu, n1b * mu};
+      double p1 = el[k].tau1, p0 = el[k].tau0;
+      for (int p = 0; p < Nt; ++p) {
+        // D = dts (sum_p vd[p] tau1^(p+1) - sum_p vd[p] tau0^(p+1))
+        for (int c = 0; c < 2; ++c) vdb[k][c][p] += Dkb[c] * el[k].dts * (p1 - p0);
+        p1 *= el[k].tau1;
+        p0 *= el[k].tau0;
+      }
+    }
+  }
+}
+
+}  // namespace adj
+}  // namespace aw

@@ -35,6 +35,25 @@ struct aw_ctx {
   double* d_corner0 = nullptr;  // element corners at t = 0
   std::vector<double> etick_h, ntick_h;  // seconds per tick of each element / node
   cudaGraphExec_t graph_exec = nullptr;  // one captured sweep
+  std::vector<int> tri_h;                // host copies for aw_load_state_xy
+  std::vector<double> cshift_h;
+  bool fresh = false;                    // a state was loaded and no sweep has run since
+  // frozen schedule (record / replay of the dt ticks)
+  long long* d_sched = nullptr;
+  // checkpointed forward run and its adjoint
+  struct Snap {
+    double *Q, *QM, *HM, *X, *qhat, *trace, *avgc, *vdisp, *nX;
+    long long *t, *dt, *count, *nt;
+    Counters* cnt;
+  };
+  std::vector<void*> adj_allocs;
+  std::vector<Snap> ckpt;  // state before sweep m * adj_k
+  Snap fin{};              // state after the run
+  std::vector<Snap> slots; // sweep-start states of one segment
+  Adj adjv{};
+  double* d_gxy = nullptr;
+  long long adj_n = 0, adj_k = 0;
+  bool adj_ready = false;
 };
 
 namespace {
@@ -607,7 +626,16 @@ void free_all(aw_ctx* c) {
   }
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  for (void* p : c->adj_allocs) cudaFree(p);
+  c->adj_allocs.clear();
+  c->ckpt.clear();
+  c->slots.clear();
+  c->adjv = Adj{};
+  c->d_gxy = nullptr;
+  c->adj_ready = false;
+  c->d_sched = nullptr;
   c->have_mesh = c->have_state = false;
+  c->fresh = false;
 }
 
 // Counters and epoch stamps restart together (a stale stamp equal to a new
@@ -650,6 +678,10 @@ int sync_counters(aw_ctx* c) {
 int check_device_error(aw_ctx* c) {
   if (c->hcnt->err_code != 0) {
     c->failed = true;
+    if (c->hcnt->err_code == AW_ERR_STATE)
+      return set_err(c, AW_ERR_STATE,
+                     "element %d: update beyond the recorded schedule, or a positivity safeguard acted in a "
+                     "differentiated sweep", c->hcnt->err_elem);
     return set_err(c, c->hcnt->err_code, "element %d is non-physical after its update (rho, p or area <= 0)", c->hcnt->err_elem);
   }
   return AW_OK;
@@ -670,6 +702,74 @@ void ctx_error(aw_ctx* c, const char* msg) {
   if (c) c->err = msg;
 }
 }  // namespace aw
+
+// ---------------------------------------------------------------------------
+// snapshots of the sweep state for the checkpointed adjoint
+// ---------------------------------------------------------------------------
+namespace {
+
+int adj_alloc(aw_ctx* c, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess)
+    return set_err(c, AW_ERR_CUDA, "cudaMalloc of %zu bytes for the adjoint failed", bytes);
+  c->adj_allocs.push_back(*p);
+  return AW_OK;
+}
+
+int snap_alloc(aw_ctx* c, aw_ctx::Snap* s) {
+  const size_t ne = c->ne, nn = c->nn, Nt = c->tab.Nt;
+  const size_t nd[9] = {4 * ne, 4 * ne, 4 * ne, 6 * ne, ne * c->tab.Nst * 4, ne * 3 * Nt * Nt * 4, ne * Nt * 4,
+                        ne * 6 * Nt, 2 * nn};
+  const size_t nl[4] = {ne, ne, ne, nn};
+  size_t bytes = 0;
+  auto pad = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  for (size_t k : nd) bytes += pad(k * sizeof(double));
+  for (size_t k : nl) bytes += pad(k * sizeof(long long));
+  bytes += pad(sizeof(Counters));
+  void* base = nullptr;
+  int rc = adj_alloc(c, &base, bytes);
+  if (rc) return rc;
+  char* p = (char*)base;
+  double** dp[9] = {&s->Q, &s->QM, &s->HM, &s->X, &s->qhat, &s->trace, &s->avgc, &s->vdisp, &s->nX};
+  for (int k = 0; k < 9; ++k) { *dp[k] = (double*)p; p += pad(nd[k] * sizeof(double)); }
+  long long** lp[4] = {&s->t, &s->dt, &s->count, &s->nt};
+  for (int k = 0; k < 4; ++k) { *lp[k] = (long long*)p; p += pad(nl[k] * sizeof(long long)); }
+  s->cnt = (Counters*)p;
+  return AW_OK;
+}
+
+// save = true: live -> snapshot; false: snapshot -> live (the per-sweep
+// counters are then reset with the epoch still growing)
+int snap_copy(aw_ctx* c, const aw_ctx::Snap& s, bool save) {
+  const Dev& d = c->d;
+  const size_t ne = c->ne, nn = c->nn, Nt = c->tab.Nt;
+  struct { void* live; void* snap; size_t bytes; } arr[] = {
+      {d.Q, s.Q, 4 * ne * sizeof(double)}, {d.QM, s.QM, 4 * ne * sizeof(double)},
+      {d.HM, s.HM, 4 * ne * sizeof(double)}, {d.X, s.X, 6 * ne * sizeof(double)},
+      {d.qhat, s.qhat, ne * c->tab.Nst * 4 * sizeof(double)}, {d.trace, s.trace, ne * 3 * Nt * Nt * 4 * sizeof(double)},
+      {d.avgc, s.avgc, ne * Nt * 4 * sizeof(double)}, {d.vdisp, s.vdisp, ne * 6 * Nt * sizeof(double)},
+      {d.nX, s.nX, 2 * nn * sizeof(double)}, {d.t, s.t, ne * sizeof(long long)}, {d.dt, s.dt, ne * sizeof(long long)},
+      {d.count, s.count, ne * sizeof(long long)}, {d.nt, s.nt, nn * sizeof(long long)}};
+  for (auto& a : arr) {
+    if (save) CK(cudaMemcpyAsync(a.snap, a.live, a.bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else CK(cudaMemcpyAsync(a.live, a.snap, a.bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (save) {
+    CK(cudaMemcpyAsync(s.cnt, d.cnt, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    launch_adj_reset(d, s.cnt, c->stream);
+    CK(cudaGetLastError());
+  }
+  return AW_OK;
+}
+
+Dev snap_view(const aw_ctx* c, const aw_ctx::Snap& s) {
+  Dev v = c->d;
+  v.Q = s.Q; v.QM = s.QM; v.HM = s.HM; v.X = s.X; v.qhat = s.qhat; v.trace = s.trace; v.avgc = s.avgc;
+  v.vdisp = s.vdisp; v.nX = s.nX; v.t = s.t; v.dt = s.dt; v.count = s.count; v.nt = s.nt;
+  return v;
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -791,6 +891,8 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
   CK(cudaMemcpyAsync(d.nX, hxy.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->xy0 = hxy;
+  c->tri_h = m.tri;
+  c->cshift_h = m.cshift;
   c->ne = m.ne; c->nn = m.nn; c->ned = m.ned; c->sw_total = (long long)m.sw.size();
   c->u_total = (long long)m.u_elem.size();
   c->have_mesh = true;
@@ -836,7 +938,7 @@ int aw_load_batch(aw_ctx* c, int n_inst, const int64_t* node_offsets, const int6
   return load_common(c, nn, xy, ne, gtri.data(), bc, nullptr, nullptr, et.data());
 }
 
-int aw_load_state(aw_ctx* c, const double* Q) {
+static int load_state_impl(aw_ctx* c, const double* Q, const double* xy) {
   if (!c || !Q) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   const size_t ne = c->ne, nn = c->nn;
@@ -848,15 +950,36 @@ int aw_load_state(aw_ctx* c, const double* Q) {
     double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
     if (!(q[0] > 0) || !(p > 0)) return set_err(c, AW_ERR_NONPHYSICAL, "initial state of element %zu is not physical", i);
   }
+  std::vector<double> hxy, corners;
+  if (xy) {
+    hxy.resize(2 * nn);
+    CK(cudaMemcpy(hxy.data(), xy, hxy.size() * sizeof(double), cudaMemcpyDefault));
+    corners.resize(6 * ne);
+    for (size_t i = 0; i < ne; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const int n = c->tri_h[3 * i + k];
+        corners[6 * i + 2 * k] = hxy[2 * n] + c->cshift_h[6 * i + 2 * k];
+        corners[6 * i + 2 * k + 1] = hxy[2 * n + 1] + c->cshift_h[6 * i + 2 * k + 1];
+      }
+    for (size_t i = 0; i < ne; ++i) {
+      const double* X = &corners[6 * i];
+      if (!(0.5 * ((X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0])) > 0))
+        return set_err(c, AW_ERR_BAD_MESH, "element %zu is not counter-clockwise at the given node positions", i);
+    }
+  }
   Dev& d = c->d;
-  double* corners = c->d_corner0;
   CK(cudaMemcpyAsync(d.Q, hQ.data(), 4 * ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(d.QM, 0, 4 * ne * sizeof(double), c->stream));
   CK(cudaMemsetAsync(d.HM, 0, 4 * ne * sizeof(double), c->stream));
   CK(cudaMemsetAsync(d.t, 0, ne * sizeof(long long), c->stream));
   CK(cudaMemsetAsync(d.count, 0, ne * sizeof(long long), c->stream));
-  CK(cudaMemcpyAsync(d.X, corners, 6 * ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(d.nX, c->xy0.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (xy) {
+    CK(cudaMemcpyAsync(d.X, corners.data(), 6 * ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.nX, hxy.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(d.X, c->d_corner0, 6 * ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.nX, c->xy0.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
   CK(cudaMemsetAsync(d.nt, 0, nn * sizeof(long long), c->stream));
   int rc0 = reset_sweep_state(c);
   if (rc0) return rc0;
@@ -873,11 +996,21 @@ int aw_load_state(aw_ctx* c, const double* Q) {
   if ((rc = check_device_error(c))) return rc;
   c->have_state = true;
   c->failed = false;
+  c->fresh = true;
+  c->adj_ready = false;
   return AW_OK;
+}
+
+int aw_load_state(aw_ctx* c, const double* Q) { return load_state_impl(c, Q, nullptr); }
+
+int aw_load_state_xy(aw_ctx* c, const double* Q, const double* xy) {
+  if (!c || !xy) return AW_ERR_INVALID_ARG;
+  return load_state_impl(c, Q, xy);
 }
 
 static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  if (n > 0) c->fresh = false;
   // Without profiling a sweep is one CUDA-graph launch (captured once per
   // loaded mesh); with profiling the kernels are launched one by one with
   // events between them.
@@ -1051,6 +1184,8 @@ int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const doubl
   CK(cudaStreamSynchronize(c->stream));
   c->have_state = true;
   c->failed = false;
+  c->fresh = false;
+  c->adj_ready = false;
   return AW_OK;
 }
 
@@ -1122,4 +1257,154 @@ int aw_measure_fp64_peak(double* gflops) {
   return AW_OK;
 }
 
+int aw_schedule(aw_ctx* c, int mode, int64_t k) {
+  if (!c || mode < 0 || mode > 2) return AW_ERR_INVALID_ARG;
+  if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
+  if (mode != 0 && c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the schedule log is for local time stepping");
+  CK(cudaStreamSynchronize(c->stream));
+  if (mode == 1) {
+    if (k < 1 || k > (1LL << 20)) return set_err(c, AW_ERR_INVALID_ARG, "schedule length must be in [1, 2^20]");
+    long long* p = nullptr;
+    int rc = dalloc(c, &p, (size_t)c->ne * k);
+    if (rc) return rc;
+    CK(cudaMemset(p, 0, (size_t)c->ne * k * sizeof(long long)));
+    c->d_sched = p;
+    c->d.sched_log = c->d_sched;
+    c->d.sched_k = k;
+  } else if (mode == 2 && !c->d_sched) {
+    return set_err(c, AW_ERR_STATE, "no recorded schedule to replay");
+  }
+  c->d.sched_mode = mode;
+  if (c->graph_exec) {  // the captured sweep holds the old mode
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  return AW_OK;
+}
+
+int aw_get_schedule(aw_ctx* c, int64_t* out) {
+  if (!c || !out) return AW_ERR_INVALID_ARG;
+  if (!c->d_sched) return set_err(c, AW_ERR_STATE, "no recorded schedule");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(out, c->d_sched, (size_t)c->ne * c->d.sched_k * sizeof(long long), cudaMemcpyDefault));
+  return AW_OK;
+}
+
+int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
+  if (!c || n_sweeps < 0 || ckpt_every < 1) return AW_ERR_INVALID_ARG;
+  if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  if (!c->fresh) return set_err(c, AW_ERR_STATE, "aw_adjoint_forward starts from a state just loaded");
+  if (c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint is for local time stepping");
+  CK(cudaStreamSynchronize(c->stream));
+  for (void* p : c->adj_allocs) cudaFree(p);
+  c->adj_allocs.clear();
+  c->ckpt.clear();
+  c->slots.clear();
+  c->adjv = Adj{};
+  c->d_gxy = nullptr;
+  c->adj_ready = false;
+  int rc;
+  const int64_t nck = n_sweeps / ckpt_every + 1;
+  c->ckpt.resize(nck);
+  for (auto& s : c->ckpt)
+    if ((rc = snap_alloc(c, &s))) return rc;
+  if ((rc = snap_alloc(c, &c->fin))) return rc;
+  if ((rc = snap_copy(c, c->ckpt[0], true))) return rc;
+  for (int64_t m = 1; m <= n_sweeps; ++m) {
+    if ((rc = do_sweeps(c, 1, nullptr, false))) return rc;
+    if (m % ckpt_every == 0 && (rc = snap_copy(c, c->ckpt[m / ckpt_every], true))) return rc;
+  }
+  if ((rc = snap_copy(c, c->fin, true))) return rc;
+  if ((rc = sync_counters(c))) return rc;
+  if ((rc = check_device_error(c))) return rc;
+  c->adj_n = n_sweeps;
+  c->adj_k = ckpt_every;
+  c->adj_ready = true;
+  c->fresh = false;
+  return AW_OK;
+}
+
+int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* dJdxy, double* gQ0, double* gxy0) {
+  if (!c) return AW_ERR_INVALID_ARG;
+  if (!c->adj_ready || c->failed) return set_err(c, AW_ERR_STATE, "no recorded forward run (call aw_adjoint_forward)");
+  const size_t ne = c->ne, nn = c->nn, Nt = c->tab.Nt;
+  int rc;
+  Adj& a = c->adjv;
+  if (!c->d_gxy) {
+    void* p = nullptr;
+    size_t nd[9] = {4 * ne, 4 * ne, 6 * ne, ne * 3 * Nt * Nt * 4, ne * Nt * 4, ne * 6 * Nt, 2 * nn, 2 * nn, 4 * ne};
+    double** dst[9] = {&a.Qb, &a.QMb, &a.Xb, &a.trb, &a.avb, &a.vdb, &a.nXb, &a.nXnb, &a.gb};
+    for (int k = 0; k < 9; ++k) {
+      if ((rc = adj_alloc(c, &p, nd[k] * sizeof(double)))) return rc;
+      *dst[k] = (double*)p;
+    }
+    if ((rc = adj_alloc(c, &p, 2 * nn * sizeof(double)))) return rc;
+    c->d_gxy = (double*)p;
+  }
+  if ((int64_t)c->slots.size() < c->adj_k + 1) {
+    c->slots.resize(c->adj_k + 1);
+    for (auto& s : c->slots)
+      if ((rc = snap_alloc(c, &s))) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  // seed with dJ / d(final state)
+  if (dJdQ) CK(cudaMemcpyAsync(a.Qb, dJdQ, 4 * ne * sizeof(double), cudaMemcpyDefault, c->stream));
+  else CK(cudaMemsetAsync(a.Qb, 0, 4 * ne * sizeof(double), c->stream));
+  if (dJdX) CK(cudaMemcpyAsync(a.Xb, dJdX, 6 * ne * sizeof(double), cudaMemcpyDefault, c->stream));
+  else CK(cudaMemsetAsync(a.Xb, 0, 6 * ne * sizeof(double), c->stream));
+  if (dJdxy) CK(cudaMemcpyAsync(a.nXb, dJdxy, 2 * nn * sizeof(double), cudaMemcpyDefault, c->stream));
+  else CK(cudaMemsetAsync(a.nXb, 0, 2 * nn * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.QMb, 0, 4 * ne * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.trb, 0, ne * 3 * Nt * Nt * 4 * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.avb, 0, ne * Nt * 4 * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.vdb, 0, ne * 6 * Nt * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.nXnb, 0, 2 * nn * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(a.gb, 0, 4 * ne * sizeof(double), c->stream));
+  const int64_t n = c->adj_n, k = c->adj_k;
+  const int64_t nseg = (n + k - 1) / k;
+  for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+    const int64_t s0 = seg * k, s1 = std::min(s0 + k, n), len = s1 - s0;
+    // recompute the segment from its checkpoint, keeping every sweep-start state
+    if ((rc = snap_copy(c, c->ckpt[seg], false))) return rc;
+    for (int64_t j = 1; j <= len; ++j) {
+      if ((rc = do_sweeps(c, 1, nullptr, false))) return rc;
+      if ((rc = snap_copy(c, c->slots[j], true))) return rc;
+    }
+    for (int64_t j = len - 1; j >= 0; --j) {
+      const aw_ctx::Snap& pre = j == 0 ? c->ckpt[seg] : c->slots[j];
+      if ((rc = snap_copy(c, pre, false))) return rc;
+      launch_phase_a_lists(c->tab, c->d, c->nsm, c->stream);
+      const Dev post = snap_view(c, c->slots[j + 1]);
+      launch_adj_elem(c->tab, post, c->d, a, c->nsm, c->stream, 0);
+      launch_adj_phase_a(c->tab, c->d, post, a, c->nsm, c->stream);
+      CK(cudaGetLastError());
+    }
+  }
+  // the pre-processing phase: reconstruction and predictor of every element
+  launch_adj_elem(c->tab, snap_view(c, c->ckpt[0]), c->d, a, c->nsm, c->stream, 1);
+  CK(cudaMemcpyAsync(c->d_gxy, a.nXb, 2 * nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  launch_adj_grad(c->d, a, c->d_gxy, c->nsm, c->stream);
+  CK(cudaGetLastError());
+  if ((rc = snap_copy(c, c->fin, false))) return rc;
+  if ((rc = sync_counters(c))) return rc;
+  if ((rc = check_device_error(c))) return rc;
+  if (gQ0) CK(cudaMemcpy(gQ0, a.Qb, 4 * ne * sizeof(double), cudaMemcpyDefault));
+  if (gxy0) CK(cudaMemcpy(gxy0, c->d_gxy, 2 * nn * sizeof(double), cudaMemcpyDefault));
+  return AW_OK;
+}
+
+int aw_adjoint_selftest(int order_M, uint64_t seed, double* report) {
+  if (order_M < 1 || order_M > kMaxM || !report) return AW_ERR_INVALID_ARG;
+  aw_ctx tmp;
+  tmp.cfg.order_M = order_M;
+  tmp.cfg.gamma = 1.4;
+  tmp.cfg.cfl = 0.5;
+  tmp.cfg.time_quantum_log2 = 20;
+  tmp.cfg.t_end = 1.0;
+  int rc = build_tab(&tmp);
+  if (rc) return rc;
+  return adjoint_selftest(tmp.tab, (unsigned long long)seed, report);
+}
+
 }  // extern "C"
+

@@ -101,6 +101,24 @@ struct Dev {
   double* N;         // [ned*4]
   double* w0;        // [ne*Mc*4] nodal WENO values, by position in the ready list
   struct Counters* cnt;
+  // frozen schedule: 0 free, 1 record, 2 replay the dt ticks of each
+  // element's update count c at sched_log[i * sched_k + c]
+  long long* sched_log;
+  long long sched_k;
+  int sched_mode;
+};
+
+// Adjoint arrays (same layouts as the state they belong to).
+struct Adj {
+  double* Qb;    // [ne*4]
+  double* QMb;   // [ne*4]
+  double* Xb;    // [ne*6]
+  double* trb;   // [ne*3*Nt*Nt*4]
+  double* avb;   // [ne*Nt*4]
+  double* vdb;   // [ne*6*Nt]
+  double* nXb;   // [nn*2]
+  double* nXnb;  // [nn*2] new node positions of the running sweep
+  double* gb;    // [ne*4] adjoint multiplying -sign * G of each own edge
 };
 
 struct Counters {
@@ -131,6 +149,21 @@ void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEve
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 double measure_fp64_peak();
+// k_ready, k_nodes, k_edges of one sweep: ready/moved/active/touched lists
+// and the new node positions, without changing the state
+void launch_phase_a_lists(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+
+// adjoint kernels (aw_adjoint.cu)
+void launch_adj_elem(const Tab& tab, const Dev& post, const Dev& live, const Adj& a, int nsm, cudaStream_t s,
+                     int initial);
+void launch_adj_phase_a(const Tab& tab, const Dev& live, const Dev& post, const Adj& a, int nsm, cudaStream_t s);
+// per-sweep counters to zero, candidates invalid, epoch + 1; with saved (a
+// device copy of the counters) != 0 the other fields are copied from it
+void launch_adj_reset(const Dev& d, const Counters* saved, cudaStream_t s);
+void launch_adj_grad(const Dev& d, const Adj& a, double* gxy, int nsm, cudaStream_t s);
+// host-side check of every element-level reverse against central
+// differences of its forward; report[0..3]: recon, predictor, edge, node
+int adjoint_selftest(const Tab& tab, unsigned long long seed, double* report);
 
 }  // namespace aw
 

@@ -1131,6 +1131,16 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
           if (tks < 1) tks = 1;
           atomicMin(&d.cnt->gts_min, tks);
         }
+        if (d.sched_mode) {  // frozen schedule: record or replay this update's step
+          const long long ci = d.count[i];
+          if (ci >= d.sched_k) {
+            set_error(d.cnt, -7, i);
+          } else {
+            long long* slot = d.sched_log + (size_t)i * d.sched_k + ci;
+            if (d.sched_mode == 1) *slot = tks;
+            else tks = *slot;
+          }
+        }
         d.dt[i] = tks;
       }
     }
@@ -1223,6 +1233,15 @@ void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
   launch_predict<M>(T, d, nsm, s, 1);
 }
 
+template <int M>
+void lists_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
+  const int grid_w = nsm * 8;
+  k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
+  k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
+  k_edges<<<grid_w, kBlock, 0, s>>>(d);
+}
+
 __global__ void k_dfma_chain(double* out, int iters, double a, double b) {
   double x[8];
 #pragma unroll
@@ -1258,6 +1277,14 @@ void launch_initial(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
     case 1: initial_impl<1>(T, d, nsm, s); break;
     case 2: initial_impl<2>(T, d, nsm, s); break;
     default: initial_impl<3>(T, d, nsm, s); break;
+  }
+}
+
+void launch_phase_a_lists(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+  switch (T.M) {
+    case 1: lists_impl<1>(T, d, nsm, s); break;
+    case 2: lists_impl<2>(T, d, nsm, s); break;
+    default: lists_impl<3>(T, d, nsm, s); break;
   }
 }
 

@@ -1,0 +1,69 @@
+"""Objective and finite-difference helpers of the adjoint tests.  No torch
+import: the oracle's difference quotients run in spawned worker processes that
+import only this module, numpy and the oracle."""
+import numpy as np
+
+H = 1e-6          # central-difference step
+TOL = 1e-6        # relative agreement of <dJ/dx, v> with the difference quotient
+
+
+def _areas(X):
+    return 0.5 * ((X[:, 2] - X[:, 0]) * (X[:, 5] - X[:, 1]) - (X[:, 3] - X[:, 1]) * (X[:, 4] - X[:, 0]))
+
+
+def _mask(mesh):
+    """elements whose initial centroid is within 1 of the vortex centre (5, 5)"""
+    c = mesh["xy"][mesh["tri"]].mean(1) - 5.0
+    return (np.hypot(c[:, 0], c[:, 1]) < 1.0).astype(np.float64)
+
+
+def _J(Q, X, mask):
+    return float(np.sum(mask * _areas(X) * 0.5 * (Q[:, 1] ** 2 + Q[:, 2] ** 2) / Q[:, 0]))
+
+
+def _dJ(Q, X, mask):
+    A = _areas(X)
+    ke = 0.5 * (Q[:, 1] ** 2 + Q[:, 2] ** 2) / Q[:, 0]
+    gQ = np.zeros_like(Q)
+    gQ[:, 0] = -mask * A * ke / Q[:, 0]
+    gQ[:, 1] = mask * A * Q[:, 1] / Q[:, 0]
+    gQ[:, 2] = mask * A * Q[:, 2] / Q[:, 0]
+    s = mask * ke
+    gX = np.zeros_like(X)
+    gX[:, 0] = 0.5 * s * (X[:, 3] - X[:, 5])
+    gX[:, 1] = 0.5 * s * (X[:, 4] - X[:, 2])
+    gX[:, 2] = 0.5 * s * (X[:, 5] - X[:, 1])
+    gX[:, 3] = 0.5 * s * (X[:, 0] - X[:, 4])
+    gX[:, 4] = 0.5 * s * (X[:, 1] - X[:, 3])
+    gX[:, 5] = 0.5 * s * (X[:, 2] - X[:, 0])
+    return gQ, gX
+
+
+def _direction(rng, Q, xy, kind):
+    vQ = rng.standard_normal(Q.shape) * np.array([0.1, 0.1, 0.1, 0.3]) if kind in ("Q", "both") else np.zeros_like(Q)
+    vxy = rng.standard_normal(xy.shape) * 0.01 if kind in ("xy", "both") else np.zeros_like(xy)
+    return vQ, vxy
+
+
+def _oracle_fd(args):
+    """Central difference of the oracle along one direction, in a process of
+    its own (spawned: no CUDA state): record the base schedule, replay it."""
+    mesh, Q0, order, n_sweeps, vQ, vxy = args
+    from oracle.pyoracle import Oracle
+    o = Oracle(order_M=order, t_end=1.0)
+    o.load_mesh(mesh)
+    o.schedule("record", n_sweeps + 2)
+    o.load_state_xy(Q0, mesh["xy"])
+    for _ in range(n_sweeps):
+        o.sweep()
+    log = o.get_schedule()
+    o.schedule("replay")
+    mask = _mask(mesh)
+    out = []
+    for sgn in (1.0, -1.0):
+        o.load_state_xy(Q0 + sgn * H * vQ, mesh["xy"] + sgn * H * vxy)
+        for _ in range(n_sweeps):
+            o.sweep()
+        e = o.get_elem()
+        out.append(_J(e["Q"], e["X"], mask))
+    return (out[0] - out[1]) / (2 * H), log
