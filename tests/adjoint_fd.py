@@ -3,8 +3,17 @@ import: the oracle's difference quotients run in spawned worker processes that
 import only this module, numpy and the oracle."""
 import numpy as np
 
+from paper_1408_3719_gb300 import workloads as W
+
 H = 1e-6          # central-difference step
 TOL = 1e-6        # relative agreement of <dJ/dx, v> with the difference quotient
+ROUND = 1e-15     # relative rounding noise of one evaluation of J
+
+
+def agree(ad, fd, J0):
+    """|ad - fd| within TOL of fd, plus the rounding error of the quotient
+    itself (ROUND |J| / H, a few 1e-10 here)"""
+    return abs(ad - fd) <= TOL * abs(fd) + ROUND * abs(J0) / H
 
 
 def _areas(X):
@@ -13,8 +22,28 @@ def _areas(X):
 
 def _mask(mesh):
     """elements whose initial centroid is within 1 of the vortex centre (5, 5)"""
-    c = mesh["xy"][mesh["tri"]].mean(1) - 5.0
+    c = W._corner_coords(mesh).mean(1) - 5.0
     return (np.hypot(c[:, 0], c[:, 1]) < 1.0).astype(np.float64)
+
+
+def wavy_vortex(nv, gamma=1.4):
+    """The isentropic vortex with a smooth periodic entropy wave on the density
+    (velocity and pressure kept), so that no characteristic field is flat.
+    On the plain isentropic vortex the entropy field is flat to the
+    discretisation error: its nonlinear weights then work at sigma ~ epsilon =
+    1e-14, where they curve so strongly that a central difference of step 1e-6
+    along a random perturbation of the averages leaves the linear regime."""
+    mesh, _ = W.vortex(nv)
+
+    def fun(x, y):
+        q = W.vortex_state(x, y, gamma, mesh["period"])
+        rho = q[..., 0]
+        u, v = q[..., 1] / rho, q[..., 2] / rho
+        p = (gamma - 1.0) * (q[..., 3] - 0.5 * rho * (u * u + v * v))
+        f = 1.0 + 0.1 * np.sin(0.2 * np.pi * x) * np.cos(0.2 * np.pi * y)
+        return W.prim_to_cons(f * rho, u, v, p, gamma)
+
+    return mesh, W.cell_average(mesh, fun, W._duffy_rule(8))
 
 
 def _J(Q, X, mask):
