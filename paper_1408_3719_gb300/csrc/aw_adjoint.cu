@@ -33,53 +33,78 @@ __device__ __forceinline__ void set_error(Counters* cnt, int code, int elem) {
   if (atomicCAS(&cnt->err_code, 0, code) == 0) cnt->err_elem = elem;
 }
 
-// Phase B of one element, reversed.  Thread per element; the element's
-// recomputed forward data and adjoints live in local memory.
+// Work space of one element's phase-B reverse (shared memory of its warp).
 template <int M>
-__global__ void __launch_bounds__(64) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
+struct ElemWork {
+  using S = Sz<M>;
+  adj::ReconIn<M> in;
+  adj::ReconTape<M> rt;
+  adj::PredTape<M> pt;
+  adj::PredTables<M> tab, tb;
+  double wb[S::Mc][4];
+  double Xb[6], Qb[4];
+  double Xvb[S::MaxU][6], Qvb[S::MaxU][4];
+  double mem_tau[S::MaxU], mem_dts[S::MaxU];
+  int mem_j[S::MaxU];
+  union Scratch {
+    adj::PredWork<M> pw;
+    adj::PredRev<M> pr;
+    adj::ReconRev<M> rr;
+  } sc;
+};
+
+// Phase B of one element, reversed: one warp per element, its recomputed
+// forward data and adjoints in shared memory.
+template <int M>
+__global__ void __launch_bounds__(32) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, NE = S::NE, MaxU = S::MaxU;
+  extern __shared__ double smem_elem[];
+  ElemWork<M>& W = *reinterpret_cast<ElemWork<M>*>(smem_elem);
+  const adj::TeamWarp tm{(int)threadIdx.x, 32};
+  const int lane = threadIdx.x;
   const int n = initial ? post.ne : live.cnt->n_ready;
-  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < n; pos += gridDim.x * blockDim.x) {
+  for (int pos = blockIdx.x; pos < n; pos += gridDim.x) {
     const int i = initial ? pos : live.ready_list[pos];
-    adj::ReconIn<M> in;
-    int mem_j[MaxU];
-    double mem_tau[MaxU], mem_dts[MaxU];
-    for (int k = 0; k < 6; ++k) in.X[k] = post.X[6 * (size_t)i + k];
-    for (int v = 0; v < 4; ++v) in.Q[v] = post.Q[4 * (size_t)i + v];
     const long long ti = post.t[i];
-    const int u0 = post.u_ptr[i];
-    in.nU = post.u_ptr[i + 1] - u0;
-    if (in.nU > MaxU) {
-      set_error(live.cnt, -7, i);
+    const int u0 = post.u_ptr[i], nU = post.u_ptr[i + 1] - u0;
+    const double dts = (double)post.dt[i] * post.etick[i];
+    const int nit = dts > 0.0 ? T.nit : 0;
+    if (nU > MaxU || nit > adj::kMaxIt) {
+      if (lane == 0) set_error(live.cnt, -7, i);
       continue;
     }
-    for (int u = 0; u < in.nU; ++u) {
+    if (lane < 6) W.in.X[lane] = post.X[6 * (size_t)i + lane];
+    if (lane < 4) W.in.Q[lane] = post.Q[4 * (size_t)i + lane];
+    if (lane == 0) W.in.nU = nU;
+    for (int k = lane; k < kNSten * NE; k += 32) W.in.st[k / NE][k % NE] = post.sten[(size_t)i * kNSten * NE + k];
+    for (int s = lane; s < kNSten; s += 32) W.in.ok[s] = post.sten_ok[(size_t)i * kNSten + s];
+    for (int u = lane; u < nU; u += 32) {
       const int j = post.u_elem[u0 + u];
-      mem_j[u] = j;
+      W.mem_j[u] = j;
       const long long tj = post.t[j], dtj = post.dt[j];
-      double* Xv = in.Xv[u];
+      double* Xv = W.in.Xv[u];
       for (int k = 0; k < 6; ++k) Xv[k] = post.X[6 * (size_t)j + k];
       if (tj == ti || dtj == 0) {
-        mem_tau[u] = -1.0;  // real data of the member
-        mem_dts[u] = 0.0;
-        for (int v = 0; v < 4; ++v) in.Qv[u][v] = post.Q[4 * (size_t)j + v];
+        W.mem_tau[u] = -1.0;  // real data of the member
+        W.mem_dts[u] = 0.0;
+        for (int v = 0; v < 4; ++v) W.in.Qv[u][v] = post.Q[4 * (size_t)j + v];
       } else {
         const double tau = (double)(ti - tj) / (double)dtj;
-        const double dts = (double)dtj * post.etick[j];
-        mem_tau[u] = tau;
-        mem_dts[u] = dts;
+        const double dtsj = (double)dtj * post.etick[j];
+        W.mem_tau[u] = tau;
+        W.mem_dts[u] = dtsj;
         const double* vd = post.vdisp + (size_t)j * 6 * Nt;
         for (int kc = 0; kc < 6; ++kc) {
           double acc = vd[kc * Nt + Nt - 1];
           for (int p = Nt - 2; p >= 0; --p) acc = acc * tau + vd[kc * Nt + p];
-          Xv[kc] += dts * (acc * tau);
+          Xv[kc] += dtsj * (acc * tau);
         }
         const double* av = post.avgc + (size_t)j * Nt * 4;
         for (int v = 0; v < 4; ++v) {
           double acc = av[(Nt - 1) * 4 + v];
           for (int p = Nt - 2; p >= 0; --p) acc = acc * tau + av[p * 4 + v];
-          in.Qv[u][v] = acc;
+          W.in.Qv[u][v] = acc;
         }
       }
       const double sx = post.u_shift[2 * (size_t)(u0 + u)], sy = post.u_shift[2 * (size_t)(u0 + u) + 1];
@@ -87,73 +112,64 @@ __global__ void __launch_bounds__(64) k_adj_elem(Tab T, Dev post, Dev live, Adj 
         Xv[2 * k] += sx;
         Xv[2 * k + 1] += sy;
       }
+      for (int k = 0; k < 6; ++k) W.Xvb[u][k] = 0.0;
+      for (int v = 0; v < 4; ++v) W.Qvb[u][v] = 0.0;
     }
-    for (int s = 0; s < kNSten; ++s) {
-      in.ok[s] = post.sten_ok[(size_t)i * kNSten + s];
-      for (int m = 0; m < NE; ++m) in.st[s][m] = post.sten[((size_t)i * kNSten + s) * NE + m];
-    }
-    adj::ReconTape<M> rt;
-    adj::recon_fwd<M>(T, in, rt);
-    if (rt.limited) {  // the positivity scaling is a kink of the map
-      set_error(live.cnt, -7, i);
+    for (int k = lane; k < Mc * 4; k += 32) (&W.wb[0][0])[k] = 0.0;
+    if (lane < 6) W.Xb[lane] = 0.0;
+    if (lane < 4) W.Qb[lane] = 0.0;
+    tm.sync();
+    adj::recon_fwd<M>(T, W.in, W.rt, tm);
+    if (W.rt.limited) {  // the positivity scaling is a kink of the map
+      if (lane == 0) set_error(live.cnt, -7, i);
+      tm.sync();
       continue;
     }
-    const double dts = (double)post.dt[i] * post.etick[i];
-    const int nit = dts > 0.0 ? T.nit : 0;
-    adj::PredTape<M> pt;
-    adj::PredTables<M> tab;
-    adj::pred_fwd<M>(T, nit, rt.w, in.X, dts, pt, tab);
-    if (pt.bad) {
-      set_error(live.cnt, -7, i);
+    adj::pred_fwd<M>(T, nit, W.rt.w, W.in.X, dts, W.pt, W.tab, W.sc.pw, tm);
+    if (W.pt.bad) {
+      if (lane == 0) set_error(live.cnt, -7, i);
+      tm.sync();
       continue;
     }
-    // adjoints of the element's new tables (they are overwritten by this
-    // sweep, so their adjoint restarts from zero before phase A)
-    adj::PredTables<M> tb;
+    // adjoints of the element's new tables (overwritten by this sweep, so
+    // their adjoint restarts from zero before phase A)
     {
       double* tr = a.trb + (size_t)i * 3 * Nt * Nt * 4;
       double* av = a.avb + (size_t)i * Nt * 4;
       double* vd = a.vdb + (size_t)i * 6 * Nt;
-      double* ftr = &tb.tr[0][0][0][0];
-      for (int k = 0; k < 3 * Nt * Nt * 4; ++k) { ftr[k] = tr[k]; tr[k] = 0.0; }
-      for (int k = 0; k < Nt * 4; ++k) { (&tb.av[0][0])[k] = av[k]; av[k] = 0.0; }
-      for (int k = 0; k < 6 * Nt; ++k) { (&tb.vd[0][0])[k] = vd[k]; vd[k] = 0.0; }
+      for (int k = lane; k < 3 * Nt * Nt * 4; k += 32) { (&W.tb.tr[0][0][0][0])[k] = tr[k]; tr[k] = 0.0; }
+      for (int k = lane; k < Nt * 4; k += 32) { (&W.tb.av[0][0])[k] = av[k]; av[k] = 0.0; }
+      for (int k = lane; k < 6 * Nt; k += 32) { (&W.tb.vd[0][0])[k] = vd[k]; vd[k] = 0.0; }
     }
-    double wb[Mc][4], Xb[6] = {0, 0, 0, 0, 0, 0}, Qb[4] = {0, 0, 0, 0};
-    for (int s = 0; s < Mc; ++s)
-      for (int v = 0; v < 4; ++v) wb[s][v] = 0.0;
-    adj::pred_rev<M>(T, nit, dts, pt, tb, wb, Xb);
-    double Xvb[MaxU][6], Qvb[MaxU][4];
-    for (int u = 0; u < in.nU; ++u) {
-      for (int k = 0; k < 6; ++k) Xvb[u][k] = 0.0;
-      for (int v = 0; v < 4; ++v) Qvb[u][v] = 0.0;
-    }
-    adj::recon_rev<M>(T, in, rt, wb, Xb, Qb, Xvb, Qvb);
-    for (int u = 0; u < in.nU; ++u) {
-      const int j = mem_j[u];
-      for (int k = 0; k < 6; ++k) atomicAdd(&a.Xb[6 * (size_t)j + k], Xvb[u][k]);
-      if (mem_tau[u] < 0.0) {
-        for (int v = 0; v < 4; ++v) atomicAdd(&a.Qb[4 * (size_t)j + v], Qvb[u][v]);
+    tm.sync();
+    adj::pred_rev<M>(T, nit, dts, W.pt, W.tb, W.wb, W.Xb, W.sc.pr, tm);
+    adj::recon_rev<M>(T, W.in, W.rt, W.wb, W.Xb, W.Qb, W.Xvb, W.Qvb, W.sc.rr, tm);
+    for (int u = lane; u < nU; u += 32) {
+      const int j = W.mem_j[u];
+      for (int k = 0; k < 6; ++k) atomicAdd(&a.Xb[6 * (size_t)j + k], W.Xvb[u][k]);
+      if (W.mem_tau[u] < 0.0) {
+        for (int v = 0; v < 4; ++v) atomicAdd(&a.Qb[4 * (size_t)j + v], W.Qvb[u][v]);
       } else {
-        const double tau = mem_tau[u], dtsj = mem_dts[u];
+        const double tau = W.mem_tau[u], dtsj = W.mem_dts[u];
         double* vd = a.vdb + (size_t)j * 6 * Nt;
         for (int kc = 0; kc < 6; ++kc) {
           double tp = tau;
           for (int p = 0; p < Nt; ++p) {
-            atomicAdd(&vd[kc * Nt + p], Xvb[u][kc] * dtsj * tp);
+            atomicAdd(&vd[kc * Nt + p], W.Xvb[u][kc] * dtsj * tp);
             tp *= tau;
           }
         }
         double* av = a.avb + (size_t)j * Nt * 4;
         double tp = 1.0;
         for (int p = 0; p < Nt; ++p) {
-          for (int v = 0; v < 4; ++v) atomicAdd(&av[p * 4 + v], Qvb[u][v] * tp);
+          for (int v = 0; v < 4; ++v) atomicAdd(&av[p * 4 + v], W.Qvb[u][v] * tp);
           tp *= tau;
         }
       }
     }
-    for (int k = 0; k < 6; ++k) atomicAdd(&a.Xb[6 * (size_t)i + k], Xb[k]);
-    for (int v = 0; v < 4; ++v) atomicAdd(&a.Qb[4 * (size_t)i + v], Qb[v]);
+    if (lane < 6) atomicAdd(&a.Xb[6 * (size_t)i + lane], W.Xb[lane]);
+    if (lane < 4) atomicAdd(&a.Qb[4 * (size_t)i + lane], W.Qb[lane]);
+    tm.sync();
   }
 }
 
@@ -348,8 +364,16 @@ __global__ void k_adj_grad(Dev d, Adj a, double* gxy) {
 
 template <int M>
 void elem_impl(const Tab& T, const Dev& post, const Dev& live, const Adj& a, int nsm, cudaStream_t s, int initial) {
-  const int grid = initial ? (post.ne + 63) / 64 : nsm * 4;
-  k_adj_elem<M><<<grid, 64, 0, s>>>(T, post, live, a, initial);
+  constexpr size_t bytes = sizeof(ElemWork<M>);
+  static_assert(bytes <= 227 * 1024, "element work space exceeds shared memory");
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_adj_elem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    attr = true;
+  }
+  const int per_sm = (int)((227 * 1024) / bytes);
+  const int grid = initial ? post.ne : nsm * (per_sm > 0 ? per_sm : 1);
+  k_adj_elem<M><<<grid, 32, bytes, s>>>(T, post, live, a, initial);
 }
 
 template <int M>
@@ -432,11 +456,14 @@ double selftest_recon(const Tab& T, Rng& g) {
     for (int k = 0; k < 6; ++k) dXv[u][k] = h * g.sym();
     for (int v = 0; v < 4; ++v) dQv[u][v] = g.sym();
   }
-  adj::recon_fwd<M>(T, *in, *tp);
+  const adj::TeamSerial tm;
+  adj::recon_fwd<M>(T, *in, *tp, tm);
   double Xb[6] = {0}, Qb[4] = {0};
   auto* Xvb = new double[in->nU][6]();
   auto* Qvb = new double[in->nU][4]();
-  adj::recon_rev<M>(T, *in, *tp, wb, Xb, Qb, Xvb, Qvb);
+  auto* rr = new adj::ReconRev<M>();
+  adj::recon_rev<M>(T, *in, *tp, wb, Xb, Qb, Xvb, Qvb, *rr, tm);
+  delete rr;
   double ad = 0.0;
   for (int k = 0; k < 6; ++k) ad += Xb[k] * dX[k];
   for (int v = 0; v < 4; ++v) ad += Qb[v] * dQ[v];
@@ -453,7 +480,7 @@ double selftest_recon(const Tab& T, Rng& g) {
       for (int v = 0; v < 4; ++v) p->Qv[u][v] += eps * dQv[u][v];
     }
     auto* t2 = new adj::ReconTape<M>();
-    adj::recon_fwd<M>(T, *p, *t2);
+    adj::recon_fwd<M>(T, *p, *t2, tm);
     double acc = 0.0;
     for (int s = 0; s < Mc; ++s)
       for (int v = 0; v < 4; ++v) acc += wb[s][v] * t2->w[s][v];
@@ -487,11 +514,14 @@ double selftest_pred(const Tab& T, Rng& g) {
   for (int k = 0; k < 6; ++k) dX[k] = h * g.sym();
   for (int s = 0; s < Mc; ++s)
     for (int v = 0; v < 4; ++v) dw[s][v] = g.sym();
+  const adj::TeamSerial tm;
   auto* tp = new adj::PredTape<M>();
   auto* out = new adj::PredTables<M>();
-  adj::pred_fwd<M>(T, T.nit, w, X, dts, *tp, *out);
+  auto* pw = new adj::PredWork<M>();
+  auto* pr = new adj::PredRev<M>();
+  adj::pred_fwd<M>(T, T.nit, w, X, dts, *tp, *out, *pw, tm);
   double wb[Mc][4] = {}, Xb[6] = {0};
-  adj::pred_rev<M>(T, T.nit, dts, *tp, *tb, wb, Xb);
+  adj::pred_rev<M>(T, T.nit, dts, *tp, *tb, wb, Xb, *pr, tm);
   double ad = 0.0;
   for (int k = 0; k < 6; ++k) ad += Xb[k] * dX[k];
   for (int s = 0; s < Mc; ++s)
@@ -503,7 +533,7 @@ double selftest_pred(const Tab& T, Rng& g) {
       for (int v = 0; v < 4; ++v) w2[s][v] = w[s][v] + eps * dw[s][v];
     auto* t2 = new adj::PredTape<M>();
     auto* o2 = new adj::PredTables<M>();
-    adj::pred_fwd<M>(T, T.nit, w2, X2, dts, *t2, *o2);
+    adj::pred_fwd<M>(T, T.nit, w2, X2, dts, *t2, *o2, *pw, tm);
     double acc = 0.0;
     for (size_t k = 0; k < sizeof(adj::PredTables<M>) / sizeof(double); ++k)
       acc += (&tb->tr[0][0][0][0])[k] * (&o2->tr[0][0][0][0])[k];
@@ -513,7 +543,7 @@ double selftest_pred(const Tab& T, Rng& g) {
   };
   const double e = 1e-5;
   const double fd = fd4(J, e);
-  delete tb; delete tp; delete out;
+  delete tb; delete tp; delete out; delete pw; delete pr;
   return fabs(fd - ad) / fmax(fabs(fd), 1e-300);
 }
 

@@ -1,5 +1,5 @@
-// Element-local pieces of one LTS sweep written serially, each with its
-// hand-written reverse (the discrete adjoint of the same arithmetic):
+// Element-local pieces of one LTS sweep, each with its hand-written reverse
+// (the discrete adjoint of the same arithmetic):
 //   recon_fwd / recon_rev   virtual data -> WENO nodal values w_h (eqs.
 //                           intConsRec, weno; characteristic weights R10)
 //   pred_fwd / pred_rev     w_h, vertices, dt -> space-time predictor and its
@@ -10,9 +10,13 @@
 //   node_fwd / node_rev     node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
 // The integer schedule (ready sets, time steps in ticks) and the mesh
 // pre-processing (stencils, wall normals) are held fixed: the reverse
-// functions differentiate the sweep map for that schedule.  Every function is
-// __host__ __device__ so that the library can check each reverse against
-// central differences of its forward on the host.
+// functions differentiate the sweep map for that schedule.
+//
+// The reconstruction and predictor pieces run on a team: the 32 lanes of a
+// warp on the GPU (work arrays in shared memory, loops strided over the
+// lanes, scatters by shared-memory atomics), or one serial rank on the host,
+// where the library checks every reverse against central differences of its
+// forward.  All functions are __host__ __device__.
 #pragma once
 #include <cmath>
 
@@ -32,6 +36,46 @@ struct Sz {
   static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, Nst = Mc * Nt, NU = Mc - 1, NE = 2 * Mc;
   static constexpr int MaxU = kNSten * (NE - 1);
   static constexpr int NL = NU * (NU + 1) / 2;
+  static constexpr int NN = NL + 4 * NU;  // normal matrix (lower triangle) and right-hand sides
+};
+
+// one serial rank
+struct TeamSerial {
+  int rank = 0, size = 1;
+  AW_HD void sync() const {}
+  AW_HD double sum(double v) const { return v; }
+  AW_HD void add(double* p, double v) const { *p += v; }
+  AW_HD int any(int f) const { return f; }
+};
+
+// the 32 lanes of a warp; every lane calls sync, sum and any
+struct TeamWarp {
+  int rank, size;
+  AW_HD void sync() const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+#endif
+  }
+  AW_HD double sum(double v) const {
+#ifdef __CUDA_ARCH__
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#endif
+    return v;
+  }
+  AW_HD void add(double* p, double v) const {
+#ifdef __CUDA_ARCH__
+    atomicAdd(p, v);
+#else
+    *p += v;
+#endif
+  }
+  AW_HD int any(int f) const {
+#ifdef __CUDA_ARCH__
+    return __any_sync(0xffffffffu, f);
+#else
+    return f;
+#endif
+  }
 };
 
 AW_HD inline double tri_area(const double* X) {
@@ -95,6 +139,10 @@ AW_HD inline void euler_fg_rev(double gm1, const double* q, const double* fb, co
   qb[3] += q3b;
 }
 
+AW_HD inline double pressure_of(double gm1, const double* q) {
+  return gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+}
+
 // ---------------------------------------------------------------------------
 // Reconstruction of one element
 // ---------------------------------------------------------------------------
@@ -102,9 +150,9 @@ template <int M>
 struct ReconIn {
   using S = Sz<M>;
   double X[6], Q[4];                 // own vertices and average (after the update)
-  int nU;                            // distinct stencil members
   double Xv[S::MaxU][6];             // members' virtual vertices, periodic shift applied
   double Qv[S::MaxU][4];             // members' virtual averages
+  int nU;                            // distinct stencil members
   unsigned char st[kNSten][S::NE];   // stencil rows: 0 = the element, u + 1 = member u
   signed char ok[kNSten];
 };
@@ -114,6 +162,7 @@ struct ReconTape {
   using S = Sz<M>;
   double ja, jb, jc, jd, idet, J[4];
   double rows[S::MaxU + 1][S::NU + 4];
+  double Nrm[kNSten][S::NN];     // normal equations: lower triangle, then right-hand sides
   double Lf[kNSten][S::NL];      // Cholesky factors, diagonal stored as 1 / L_aa
   double c[kNSten][S::NU][4];
   double gx, gy, gn, nx, ny;
@@ -124,6 +173,16 @@ struct ReconTape {
   double wc[S::NU][4], cv[S::NU][4];
   double w[S::Mc][4];            // nodal w_h
   int limited;                   // the positivity scaling would change w_h
+};
+
+// reverse scratch of the reconstruction
+template <int M>
+struct ReconRev {
+  using S = Sz<M>;
+  double cvb[S::NU][4], wcb[S::NU][4], Rb[16], Lb[16];
+  double omtb[kNSten][4], dot[4];
+  double chb[kNSten][S::NU][4], cb[kNSten][S::NU][4];
+  double lam[kNSten][S::NU][4];
 };
 
 template <int M>
@@ -141,20 +200,19 @@ AW_HD inline void chol_solve(const double* Lf, double* y) {
   }
 }
 
-AW_HD inline double pressure_of(double gm1, const double* q) {
-  return gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
-}
-
-template <int M>
-AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
+template <int M, class Tm>
+AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp, const Tm& tm) {
   using S = Sz<M>;
-  constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE;
+  constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE, NL = S::NL, NN = S::NN;
   const double* X = in.X;
-  tp.ja = X[2] - X[0]; tp.jb = X[4] - X[0]; tp.jc = X[3] - X[1]; tp.jd = X[5] - X[1];
-  tp.idet = 1.0 / (tp.ja * tp.jd - tp.jb * tp.jc);
-  tp.J[0] = tp.jd * tp.idet; tp.J[1] = -tp.jb * tp.idet; tp.J[2] = -tp.jc * tp.idet; tp.J[3] = tp.ja * tp.idet;
-  const double* J = tp.J;
-  for (int u = 0; u < in.nU; ++u) {
+  const double ja = X[2] - X[0], jb = X[4] - X[0], jc = X[3] - X[1], jd = X[5] - X[1];
+  const double idet = 1.0 / (ja * jd - jb * jc);
+  const double J[4] = {jd * idet, -jb * idet, -jc * idet, ja * idet};
+  if (tm.rank == 0) {
+    tp.ja = ja; tp.jb = jb; tp.jc = jc; tp.jd = jd; tp.idet = idet;
+    for (int k = 0; k < 4; ++k) tp.J[k] = J[k];
+  }
+  for (int u = tm.rank; u < in.nU; u += tm.size) {
     double xr[3], yr[3];
     for (int k = 0; k < 3; ++k) {
       const double px = in.Xv[u][2 * k] - X[0], py = in.Xv[u][2 * k + 1] - X[1];
@@ -174,27 +232,33 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
     for (int a = 0; a < NU; ++a) dst[a] = row[a] - T.mbar[a];
     for (int v = 0; v < 4; ++v) dst[NU + v] = in.Qv[u][v] - in.Q[v];
   }
-  for (int s = 0; s < kNSten; ++s) {
+  tm.sync();
+  // normal equations of every stencil
+  for (int it = tm.rank; it < kNSten * NN; it += tm.size) {
+    const int s = it / NN, q = it % NN;
     if (!in.ok[s]) continue;
-    double Lw[NU][NU], b[NU][4];
-    for (int a = 0; a < NU; ++a) {
-      for (int bb = 0; bb <= a; ++bb) {
-        double acc = 0.0;
-        for (int m = 1; m < NE; ++m) {
-          const double* r = tp.rows[in.st[s][m]];
-          acc += r[a] * r[bb];
-        }
-        Lw[a][bb] = acc;
-      }
-      for (int v = 0; v < 4; ++v) {
-        double acc = 0.0;
-        for (int m = 1; m < NE; ++m) {
-          const double* r = tp.rows[in.st[s][m]];
-          acc += r[a] * r[NU + v];
-        }
-        b[a][v] = acc;
-      }
+    int a, b;
+    if (q < NL) {
+      a = 0;
+      while ((a + 1) * (a + 2) / 2 <= q) ++a;
+      b = q - a * (a + 1) / 2;
+    } else {
+      a = (q - NL) / 4;
+      b = NU + (q - NL) % 4;
     }
+    double acc = 0.0;
+    for (int m = 1; m < NE; ++m) {
+      const double* r = tp.rows[in.st[s][m]];
+      acc += r[a] * r[b];
+    }
+    tp.Nrm[s][q] = acc;
+  }
+  tm.sync();
+  for (int s = tm.rank; s < kNSten; s += tm.size) {
+    if (!in.ok[s]) continue;
+    double Lw[NU][NU];
+    for (int a = 0; a < NU; ++a)
+      for (int bb = 0; bb <= a; ++bb) Lw[a][bb] = tp.Nrm[s][a * (a + 1) / 2 + bb];
     for (int a = 0; a < NU; ++a) {
       double dd = Lw[a][a];
       for (int k = 0; k < a; ++k) dd -= Lw[a][k] * Lw[a][k];
@@ -208,20 +272,24 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
     }
     for (int a = 0; a < NU; ++a)
       for (int bb = 0; bb <= a; ++bb) tp.Lf[s][a * (a + 1) / 2 + bb] = Lw[a][bb];
-    for (int v = 0; v < 4; ++v) {
-      double y[NU];
-      for (int a = 0; a < NU; ++a) y[a] = b[a][v];
-      chol_solve<M>(tp.Lf[s], y);
-      for (int a = 0; a < NU; ++a) tp.c[s][a][v] = y[a];
-    }
   }
+  tm.sync();
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, v = it % 4;
+    if (!in.ok[s]) continue;
+    double y[NU];
+    for (int a = 0; a < NU; ++a) y[a] = tp.Nrm[s][NL + a * 4 + v];
+    chol_solve<M>(tp.Lf[s], y);
+    for (int a = 0; a < NU; ++a) tp.c[s][a][v] = y[a];
+  }
+  tm.sync();
   // characteristic fields along the density gradient of the central stencil
-  tp.gx = tp.c[0][0][0] * J[0] + tp.c[0][1][0] * J[2];
-  tp.gy = tp.c[0][0][0] * J[1] + tp.c[0][1][0] * J[3];
-  tp.gn = sqrt(tp.gx * tp.gx + tp.gy * tp.gy);
-  tp.nx = 1.0; tp.ny = 0.0;
-  if (tp.gn > 0.0) { tp.nx = tp.gx / tp.gn; tp.ny = tp.gy / tp.gn; }
-  {
+  if (tm.rank == 0) {
+    tp.gx = tp.c[0][0][0] * J[0] + tp.c[0][1][0] * J[2];
+    tp.gy = tp.c[0][0][0] * J[1] + tp.c[0][1][0] * J[3];
+    tp.gn = sqrt(tp.gx * tp.gx + tp.gy * tp.gy);
+    tp.nx = 1.0; tp.ny = 0.0;
+    if (tp.gn > 0.0) { tp.nx = tp.gx / tp.gn; tp.ny = tp.gy / tp.gn; }
     const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
     const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
     const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
@@ -237,23 +305,24 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
     Lm[8] = -ut; Lm[9] = -ny; Lm[10] = nx; Lm[11] = 0.0;
     Lm[12] = 0.5 * (b2 - un * ia); Lm[13] = -0.5 * (b1 * u - nx * ia); Lm[14] = -0.5 * (b1 * v - ny * ia); Lm[15] = 0.5 * b1;
   }
-  for (int s = 0; s < kNSten; ++s) {
+  tm.sync();
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, r = it % 4;
     if (!in.ok[s]) continue;
-    for (int r = 0; r < 4; ++r) {
-      const double* Lr = tp.Lm + 4 * r;
-      for (int l = 0; l < NU; ++l)
-        tp.ch[s][l][r] = Lr[0] * tp.c[s][l][0] + Lr[1] * tp.c[s][l][1] + Lr[2] * tp.c[s][l][2] + Lr[3] * tp.c[s][l][3];
-      double sg = 0.0;
-      for (int a = 0; a < NU; ++a) {
-        double acc = 0.0;
-        for (int bb = a; bb < NU; ++bb) acc += T.SigU[a][bb] * tp.ch[s][bb][r];
-        tp.y[s][r][a] = acc;
-        sg += acc * acc;
-      }
-      tp.e1[s][r] = sg + 1e-14;
+    const double* Lr = tp.Lm + 4 * r;
+    for (int l = 0; l < NU; ++l)
+      tp.ch[s][l][r] = Lr[0] * tp.c[s][l][0] + Lr[1] * tp.c[s][l][1] + Lr[2] * tp.c[s][l][2] + Lr[3] * tp.c[s][l][3];
+    double sg = 0.0;
+    for (int a = 0; a < NU; ++a) {
+      double acc = 0.0;
+      for (int bb = a; bb < NU; ++bb) acc += T.SigU[a][bb] * tp.ch[s][bb][r];
+      tp.y[s][r][a] = acc;
+      sg += acc * acc;
     }
+    tp.e1[s][r] = sg + 1e-14;
   }
-  for (int r = 0; r < 4; ++r) {
+  tm.sync();
+  for (int r = tm.rank; r < 4; r += tm.size) {
     double tot = 0.0;
     for (int s = 0; s < kNSten; ++s) {
       tp.om[s][r] = 0.0;
@@ -263,121 +332,137 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp) {
       tot += tp.om[s][r];
     }
     tp.tot[r] = tot;
-    const double itot = 1.0 / tot;
-    for (int l = 0; l < NU; ++l) {
-      double acc = 0.0;
-      for (int s = 0; s < kNSten; ++s)
-        if (in.ok[s]) acc += (tp.om[s][r] * itot) * tp.ch[s][l][r];
-      tp.wc[l][r] = acc;
-    }
   }
-  for (int l = 0; l < NU; ++l)
-    for (int v = 0; v < 4; ++v) {
-      const double* Rv = tp.R + 4 * v;
-      tp.cv[l][v] = Rv[0] * tp.wc[l][0] + Rv[1] * tp.wc[l][1] + Rv[2] * tp.wc[l][2] + Rv[3] * tp.wc[l][3];
-    }
-  for (int s = 0; s < Mc; ++s)
-    for (int v = 0; v < 4; ++v) {
-      double acc = in.Q[v];
-      for (int l = 0; l < NU; ++l) acc += T.Bnod[s][l] * tp.cv[l][v];
-      tp.w[s][v] = acc;
-    }
+  tm.sync();
+  for (int it = tm.rank; it < NU * 4; it += tm.size) {
+    const int l = it / 4, r = it % 4;
+    const double itot = 1.0 / tp.tot[r];
+    double acc = 0.0;
+    for (int s = 0; s < kNSten; ++s)
+      if (in.ok[s]) acc += (tp.om[s][r] * itot) * tp.ch[s][l][r];
+    tp.wc[l][r] = acc;
+  }
+  tm.sync();
+  for (int it = tm.rank; it < NU * 4; it += tm.size) {
+    const int l = it / 4, v = it % 4;
+    const double* Rv = tp.R + 4 * v;
+    tp.cv[l][v] = Rv[0] * tp.wc[l][0] + Rv[1] * tp.wc[l][1] + Rv[2] * tp.wc[l][2] + Rv[3] * tp.wc[l][3];
+  }
+  tm.sync();
+  for (int it = tm.rank; it < Mc * 4; it += tm.size) {
+    const int s = it / 4, v = it % 4;
+    double acc = in.Q[v];
+    for (int l = 0; l < NU; ++l) acc += T.Bnod[s][l] * tp.cv[l][v];
+    tp.w[s][v] = acc;
+  }
+  tm.sync();
   // the positivity scaling (R11) is a kink: the reverse reports where it acts
   const double gm1 = T.gamma - 1.0, rho_min = 1e-8 * in.Q[0], p_min = 1e-8 * pressure_of(gm1, in.Q);
-  tp.limited = 0;
-  for (int s = 0; s < Mc; ++s)
-    if (tp.w[s][0] < rho_min || pressure_of(gm1, tp.w[s]) < p_min) tp.limited = 1;
+  int lim = 0;
+  for (int s = tm.rank; s < Mc; s += tm.size)
+    if (tp.w[s][0] < rho_min || pressure_of(gm1, tp.w[s]) < p_min) lim = 1;
+  lim = tm.any(lim);
+  if (tm.rank == 0) tp.limited = lim;
+  tm.sync();
 }
 
 // Reverse of recon_fwd: wb = dJ/dw (Mc x 4); adds to Xb (6), Qb (4) of the
-// element and to Xvb, Qvb of the members (arrays zeroed by the caller).
-template <int M>
+// element (rank 0 writes them) and to Xvb, Qvb of the members (zeroed by the
+// caller; each member's row is written by one rank).
+template <int M, class Tm>
 AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp, const double (*wb)[4], double* Xb,
-                     double* Qb, double (*Xvb)[6], double (*Qvb)[4]) {
+                     double* Qb, double (*Xvb)[6], double (*Qvb)[4], ReconRev<M>& sc, const Tm& tm) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE;
+  double pQ[4] = {0, 0, 0, 0}, pX[6] = {0, 0, 0, 0, 0, 0}, pJ[4] = {0, 0, 0, 0};  // this rank's partial sums
   // w = Q + Bnod cv
-  double cvb[NU][4];
-  for (int v = 0; v < 4; ++v) {
+  for (int v = tm.rank; v < 4; v += tm.size) {
     double acc = 0.0;
     for (int s = 0; s < Mc; ++s) acc += wb[s][v];
-    Qb[v] += acc;
+    pQ[v] += acc;
   }
-  for (int l = 0; l < NU; ++l)
-    for (int v = 0; v < 4; ++v) {
-      double acc = 0.0;
-      for (int s = 0; s < Mc; ++s) acc += T.Bnod[s][l] * wb[s][v];
-      cvb[l][v] = acc;
-    }
+  for (int it = tm.rank; it < NU * 4; it += tm.size) {
+    const int l = it / 4, v = it % 4;
+    double acc = 0.0;
+    for (int s = 0; s < Mc; ++s) acc += T.Bnod[s][l] * wb[s][v];
+    sc.cvb[l][v] = acc;
+  }
+  tm.sync();
   // cv = R wc
-  double wcb[NU][4], Rb[16], Lb[16];
-  for (int k = 0; k < 16; ++k) { Rb[k] = 0.0; Lb[k] = 0.0; }
-  for (int l = 0; l < NU; ++l)
-    for (int r = 0; r < 4; ++r) {
-      double acc = 0.0;
-      for (int v = 0; v < 4; ++v) acc += tp.R[4 * v + r] * cvb[l][v];
-      wcb[l][r] = acc;
-    }
-  for (int v = 0; v < 4; ++v)
-    for (int r = 0; r < 4; ++r) {
-      double acc = 0.0;
-      for (int l = 0; l < NU; ++l) acc += cvb[l][v] * tp.wc[l][r];
-      Rb[4 * v + r] = acc;
-    }
-  // weights and characteristic coefficients
-  double chb[kNSten][NU][4];
-  for (int s = 0; s < kNSten; ++s)
-    for (int l = 0; l < NU; ++l)
-      for (int r = 0; r < 4; ++r) chb[s][l][r] = 0.0;
-  for (int r = 0; r < 4; ++r) {
+  for (int it = tm.rank; it < NU * 4; it += tm.size) {
+    const int l = it / 4, r = it % 4;
+    double acc = 0.0;
+    for (int v = 0; v < 4; ++v) acc += tp.R[4 * v + r] * sc.cvb[l][v];
+    sc.wcb[l][r] = acc;
+  }
+  for (int it = tm.rank; it < 16; it += tm.size) {
+    const int v = it / 4, r = it % 4;
+    double acc = 0.0;
+    for (int l = 0; l < NU; ++l) acc += sc.cvb[l][v] * tp.wc[l][r];
+    sc.Rb[4 * v + r] = acc;
+  }
+  tm.sync();
+  // nonlinear weights: wc = sum_s om_s / tot ch_s
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, r = it % 4;
+    double acc = 0.0;
+    if (in.ok[s])
+      for (int l = 0; l < NU; ++l) acc += sc.wcb[l][r] * tp.ch[s][l][r];
+    sc.omtb[s][r] = acc;
+  }
+  tm.sync();
+  for (int r = tm.rank; r < 4; r += tm.size) {
     const double itot = 1.0 / tp.tot[r];
-    double omtb[kNSten], dot = 0.0;
-    for (int s = 0; s < kNSten; ++s) {
-      omtb[s] = 0.0;
-      if (!in.ok[s]) continue;
-      const double omt = tp.om[s][r] * itot;
-      double acc = 0.0;
-      for (int l = 0; l < NU; ++l) {
-        acc += wcb[l][r] * tp.ch[s][l][r];
-        chb[s][l][r] += omt * wcb[l][r];
-      }
-      omtb[s] = acc;
-      dot += acc * omt;
+    double dot = 0.0;
+    for (int s = 0; s < kNSten; ++s)
+      if (in.ok[s]) dot += sc.omtb[s][r] * (tp.om[s][r] * itot);
+    sc.dot[r] = dot;
+  }
+  tm.sync();
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, r = it % 4;
+    if (!in.ok[s]) {
+      for (int l = 0; l < NU; ++l) sc.chb[s][l][r] = 0.0;
+      continue;
     }
-    for (int s = 0; s < kNSten; ++s) {
-      if (!in.ok[s]) continue;
-      const double omb = (omtb[s] - dot) * itot;
-      const double sigb = omb * (-8.0 * tp.om[s][r] / tp.e1[s][r]);
-      // sigma = sum_a y_a^2, y = SigU ch
-      for (int a = 0; a < NU; ++a) {
-        const double yb = 2.0 * tp.y[s][r][a] * sigb;
-        for (int bb = a; bb < NU; ++bb) chb[s][bb][r] += T.SigU[a][bb] * yb;
-      }
+    const double itot = 1.0 / tp.tot[r];
+    const double omt = tp.om[s][r] * itot;
+    for (int l = 0; l < NU; ++l) sc.chb[s][l][r] = omt * sc.wcb[l][r];
+    const double omb = (sc.omtb[s][r] - sc.dot[r]) * itot;
+    const double sigb = omb * (-8.0 * tp.om[s][r] / tp.e1[s][r]);
+    // sigma = sum_a y_a^2, y = SigU ch
+    for (int a = 0; a < NU; ++a) {
+      const double yb = 2.0 * tp.y[s][r][a] * sigb;
+      for (int bb = a; bb < NU; ++bb) sc.chb[s][bb][r] += T.SigU[a][bb] * yb;
     }
   }
+  tm.sync();
   // ch = Lm c
-  double cb[kNSten][NU][4];
-  for (int s = 0; s < kNSten; ++s) {
-    if (!in.ok[s]) continue;
-    for (int l = 0; l < NU; ++l)
-      for (int v = 0; v < 4; ++v) {
-        double acc = 0.0;
-        for (int r = 0; r < 4; ++r) {
-          acc += tp.Lm[4 * r + v] * chb[s][l][r];
-          Lb[4 * r + v] += chb[s][l][r] * tp.c[s][l][v];
-        }
-        cb[s][l][v] = acc;
-      }
+  for (int it = tm.rank; it < kNSten * NU * 4; it += tm.size) {
+    const int s = it / (NU * 4), l = (it / 4) % NU, v = it % 4;
+    double acc = 0.0;
+    if (in.ok[s])
+      for (int r = 0; r < 4; ++r) acc += tp.Lm[4 * r + v] * sc.chb[s][l][r];
+    sc.cb[s][l][v] = acc;
   }
-  // eigenvectors of the direction n and the state Q
-  double nxb = 0.0, nyb = 0.0;
-  {
+  for (int it = tm.rank; it < 16; it += tm.size) {
+    const int r = it / 4, v = it % 4;
+    double acc = 0.0;
+    for (int s = 0; s < kNSten; ++s)
+      if (in.ok[s])
+        for (int l = 0; l < NU; ++l) acc += sc.chb[s][l][r] * tp.c[s][l][v];
+    sc.Lb[4 * r + v] = acc;
+  }
+  tm.sync();
+  // eigenvectors of the direction n and the state Q, then n = g / |g|
+  if (tm.rank == 0) {
+    double nxb = 0.0, nyb = 0.0;
     const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
     const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
     const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny;
     const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), ia = 1.0 / a;
     double ub = 0, vb = 0, ab = 0, Hb = 0, unb = 0, utb = 0, q2b = 0, b1b = 0, b2b = 0, iab = 0;
-    const double* R_ = Rb;
+    const double* R_ = sc.Rb;
     ub += R_[4]; ab -= R_[4] * nx; nxb -= R_[4] * a;
     ub += R_[5];
     nyb -= R_[6];
@@ -390,7 +475,7 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     q2b += R_[13];
     utb += R_[14];
     Hb += R_[15]; ab += R_[15] * un; unb += R_[15] * a;
-    const double* L_ = Lb;
+    const double* L_ = sc.Lb;
     b2b += 0.5 * L_[0]; unb += 0.5 * L_[0] * ia; iab += 0.5 * L_[0] * un;
     b1b -= 0.5 * L_[1] * u; ub -= 0.5 * L_[1] * b1; nxb -= 0.5 * L_[1] * ia; iab -= 0.5 * L_[1] * nx;
     b1b -= 0.5 * L_[2] * v; vb -= 0.5 * L_[2] * b1; nyb -= 0.5 * L_[2] * ia; iab -= 0.5 * L_[2] * ny;
@@ -422,67 +507,67 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     Eb += pb * (g - 1.0); rhob -= pb * (g - 1.0) * 0.5 * (u * u + v * v);
     ub -= pb * (g - 1.0) * rho * u; vb -= pb * (g - 1.0) * rho * v;
     // u = Q1 / rho, v = Q2 / rho
-    Qb[1] += ub / rho; rhob -= ub * u / rho;
-    Qb[2] += vb / rho; rhob -= vb * v / rho;
-    Qb[0] += rhob;
-    Qb[3] += Eb;
+    pQ[1] += ub / rho; rhob -= ub * u / rho;
+    pQ[2] += vb / rho; rhob -= vb * v / rho;
+    pQ[0] += rhob;
+    pQ[3] += Eb;
+    if (tp.gn > 0.0) {
+      const double dn = tp.nx * nxb + tp.ny * nyb;
+      const double gxb = (nxb - tp.nx * dn) / tp.gn, gyb = (nyb - tp.ny * dn) / tp.gn;
+      sc.cb[0][0][0] += gxb * tp.J[0] + gyb * tp.J[1];
+      sc.cb[0][1][0] += gxb * tp.J[2] + gyb * tp.J[3];
+      pJ[0] += gxb * tp.c[0][0][0];
+      pJ[2] += gxb * tp.c[0][1][0];
+      pJ[1] += gyb * tp.c[0][0][0];
+      pJ[3] += gyb * tp.c[0][1][0];
+    }
   }
-  // n = g / |g|; g from the central stencil's linear coefficients and J
-  double Jb[4] = {0, 0, 0, 0};
-  if (tp.gn > 0.0) {
-    const double dn = tp.nx * nxb + tp.ny * nyb;
-    const double gxb = (nxb - tp.nx * dn) / tp.gn, gyb = (nyb - tp.ny * dn) / tp.gn;
-    cb[0][0][0] += gxb * tp.J[0] + gyb * tp.J[1];
-    cb[0][1][0] += gxb * tp.J[2] + gyb * tp.J[3];
-    Jb[0] += gxb * tp.c[0][0][0];
-    Jb[2] += gxb * tp.c[0][1][0];
-    Jb[1] += gyb * tp.c[0][0][0];
-    Jb[3] += gyb * tp.c[0][1][0];
-  }
+  tm.sync();
   // least-squares solves: c = N^-1 b, N = sum r r^T, b = sum r rhs^T
-  double rowb[S::MaxU + 1][NU + 4];
-  for (int u = 0; u <= in.nU; ++u)
-    for (int k = 0; k < NU + 4; ++k) rowb[u][k] = 0.0;
-  for (int s = 0; s < kNSten; ++s) {
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, v = it % 4;
     if (!in.ok[s]) continue;
-    double lam[NU][4], Nb[NU][NU];
-    for (int v = 0; v < 4; ++v) {
-      double y[NU];
-      for (int a = 0; a < NU; ++a) y[a] = cb[s][a][v];
-      chol_solve<M>(tp.Lf[s], y);
-      for (int a = 0; a < NU; ++a) lam[a][v] = y[a];
-    }
-    for (int a = 0; a < NU; ++a)
-      for (int bb = 0; bb < NU; ++bb) {
-        double acc = 0.0;
-        for (int v = 0; v < 4; ++v) acc -= lam[a][v] * tp.c[s][bb][v];
-        Nb[a][bb] = acc;
-      }
-    for (int m = 1; m < NE; ++m) {
-      const int ri = in.st[s][m];
-      const double* r = tp.rows[ri];
-      double* rb = rowb[ri];
-      for (int k = 0; k < NU; ++k) {
-        double acc = 0.0;
-        for (int bb = 0; bb < NU; ++bb) acc += (Nb[k][bb] + Nb[bb][k]) * r[bb];
-        for (int v = 0; v < 4; ++v) acc += lam[k][v] * r[NU + v];
-        rb[k] += acc;
-      }
-      for (int v = 0; v < 4; ++v) {
-        double acc = 0.0;
-        for (int a = 0; a < NU; ++a) acc += lam[a][v] * r[a];
-        rb[NU + v] += acc;
-      }
-    }
+    double y[NU];
+    for (int a = 0; a < NU; ++a) y[a] = sc.cb[s][a][v];
+    chol_solve<M>(tp.Lf[s], y);
+    for (int a = 0; a < NU; ++a) sc.lam[s][a][v] = y[a];
   }
-  // rows: basis averages over the virtual members, rhs Qv - Q
+  tm.sync();
+  // each member row: its adjoint from every stencil that holds it, then the
+  // reverse of the row (basis averages over the virtual member, Qv - Q)
   const double* X = in.X;
   const double* J = tp.J;
-  for (int u = 0; u < in.nU; ++u) {
-    const double* rb = rowb[u + 1];
+  for (int u = tm.rank; u < in.nU; u += tm.size) {
+    const int ri = u + 1;
+    const double* r = tp.rows[ri];
+    double rb[NU + 4];
+    for (int k = 0; k < NU + 4; ++k) rb[k] = 0.0;
+    for (int s = 0; s < kNSten; ++s) {
+      if (!in.ok[s]) continue;
+      for (int m = 1; m < NE; ++m) {
+        if (in.st[s][m] != ri) continue;
+        const double(*lam)[4] = sc.lam[s];
+        const double(*c)[4] = tp.c[s];
+        for (int k = 0; k < NU; ++k) {
+          double acc = 0.0;
+          for (int bb = 0; bb < NU; ++bb) {
+            double nkb = 0.0;  // Nb[k][bb] + Nb[bb][k], Nb = -lam c^T
+            for (int v = 0; v < 4; ++v) nkb -= lam[k][v] * c[bb][v] + lam[bb][v] * c[k][v];
+            acc += nkb * r[bb];
+          }
+          for (int v = 0; v < 4; ++v) acc += lam[k][v] * r[NU + v];
+          rb[k] += acc;
+        }
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+          for (int a = 0; a < NU; ++a) acc += lam[a][v] * r[a];
+          rb[NU + v] += acc;
+        }
+      }
+    }
     for (int v = 0; v < 4; ++v) {
       Qvb[u][v] += rb[NU + v];
-      Qb[v] -= rb[NU + v];
+      pQ[v] -= rb[NU + v];
     }
     double px[3], py[3], xr[3], yr[3];
     for (int k = 0; k < 3; ++k) {
@@ -509,33 +594,39 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     }
     for (int k = 0; k < 3; ++k) {
       const double pxb = J[0] * xrb[k] + J[2] * yrb[k], pyb = J[1] * xrb[k] + J[3] * yrb[k];
-      Jb[0] += xrb[k] * px[k];
-      Jb[1] += xrb[k] * py[k];
-      Jb[2] += yrb[k] * px[k];
-      Jb[3] += yrb[k] * py[k];
+      pJ[0] += xrb[k] * px[k];
+      pJ[1] += xrb[k] * py[k];
+      pJ[2] += yrb[k] * px[k];
+      pJ[3] += yrb[k] * py[k];
       Xvb[u][2 * k] += pxb;
       Xvb[u][2 * k + 1] += pyb;
-      Xb[0] -= pxb;
-      Xb[1] -= pyb;
+      pX[0] -= pxb;
+      pX[1] -= pyb;
     }
   }
-  // J = inverse of the element's affine map
-  {
-    double jab = Jb[3] * tp.idet, jbb = -Jb[1] * tp.idet, jcb = -Jb[2] * tp.idet, jdb = Jb[0] * tp.idet;
-    const double idb = Jb[0] * tp.jd - Jb[1] * tp.jb - Jb[2] * tp.jc + Jb[3] * tp.ja;
+  for (int k = 0; k < 4; ++k) pQ[k] = tm.sum(pQ[k]);
+  for (int k = 0; k < 6; ++k) pX[k] = tm.sum(pX[k]);
+  for (int k = 0; k < 4; ++k) pJ[k] = tm.sum(pJ[k]);
+  if (tm.rank == 0) {
+    // J = inverse of the element's affine map
+    double jab = pJ[3] * tp.idet, jbb = -pJ[1] * tp.idet, jcb = -pJ[2] * tp.idet, jdb = pJ[0] * tp.idet;
+    const double idb = pJ[0] * tp.jd - pJ[1] * tp.jb - pJ[2] * tp.jc + pJ[3] * tp.ja;
     const double detb = -idb * tp.idet * tp.idet;
     jab += detb * tp.jd; jdb += detb * tp.ja; jbb -= detb * tp.jc; jcb -= detb * tp.jb;
-    Xb[2] += jab; Xb[0] -= jab;
-    Xb[4] += jbb; Xb[0] -= jbb;
-    Xb[3] += jcb; Xb[1] -= jcb;
-    Xb[5] += jdb; Xb[1] -= jdb;
+    pX[2] += jab; pX[0] -= jab;
+    pX[4] += jbb; pX[0] -= jbb;
+    pX[3] += jcb; pX[1] -= jcb;
+    pX[5] += jdb; pX[1] -= jdb;
+    for (int k = 0; k < 6; ++k) Xb[k] += pX[k];
+    for (int v = 0; v < 4; ++v) Qb[v] += pQ[v];
   }
+  tm.sync();
 }
 
 // ---------------------------------------------------------------------------
 // Predictor of one element and its derived tables
 // ---------------------------------------------------------------------------
-constexpr int kMaxIt = 8;  // Picard iterations the reverse can store
+constexpr int kMaxIt = 6;  // Picard iterations the reverse can store
 
 template <int M>
 struct PredTape {
@@ -554,7 +645,20 @@ struct PredTables {
   double vd[6][S::Nt];            // vertex k, component c -> [2k + c], powers 1..Nt
 };
 
-// nodal P and V of slice t of iterate (q, x); static = iteration 0 (no mesh
+// work arrays of the predictor (forward iterate, nodal P and V) and of its
+// reverse
+template <int M>
+struct PredWork {
+  using S = Sz<M>;
+  double q[S::Nst][4], x[S::Nst][2], P[S::Nst][4], V[S::Nst][2];
+};
+template <int M>
+struct PredRev {
+  using S = Sz<M>;
+  double qb[S::Nst][4], xb[S::Nst][2], qo[S::Nst][4], xo[S::Nst][2], Pb[S::Nst][4], Vb[S::Nst][2];
+};
+
+// nodal P and V of slice t of iterate (q, x); stat = iteration 0 (no mesh
 // motion yet, so xi_t = eta_t = 0)
 template <int M>
 AW_HD inline void pred_node(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
@@ -599,10 +703,11 @@ AW_HD inline void pred_node(const Tab& T, const double (*q)[4], const double (*x
   V[1] = T.eulerian ? 0.0 : qs[2] / qs[0];
 }
 
-// reverse of pred_node: adds to qb, xb (whole iterate)
-template <int M>
+// reverse of pred_node: adds (through tm.add) to qb, xb of the whole iterate
+template <int M, class Tm>
 AW_HD inline void pred_node_rev(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
-                                bool stat, const double* Pb, const double* Vb, double (*qb)[4], double (*xb)[2]) {
+                                bool stat, const double* Pb, const double* Vb, double (*qb)[4], double (*xb)[2],
+                                const Tm& tm) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt;
   const double gm1 = T.gamma - 1.0;
@@ -654,215 +759,229 @@ AW_HD inline void pred_node_rev(const Tab& T, const double (*q)[4], const double
   xxb += detb * ye; yeb += detb * xx; xeb -= detb * yx; yxb -= detb * xe;
   if (!stat) {
     for (int u = 0; u < Nt; ++u) {
-      xb[u * Mc + s][0] += idt * T.Dtau[t][u] * xtb;
-      xb[u * Mc + s][1] += idt * T.Dtau[t][u] * ytb;
+      tm.add(&xb[u * Mc + s][0], idt * T.Dtau[t][u] * xtb);
+      tm.add(&xb[u * Mc + s][1], idt * T.Dtau[t][u] * ytb);
     }
   }
   for (int r = 0; r < Mc; ++r) {
     const double a = T.Dxi[s][r], b = T.Deta[s][r];
     const int lr = t * Mc + r;
-    xb[lr][0] += a * xxb + b * xeb;
-    xb[lr][1] += a * yxb + b * yeb;
-    double fb[4], gb[4];
+    tm.add(&xb[lr][0], a * xxb + b * xeb);
+    tm.add(&xb[lr][1], a * yxb + b * yeb);
+    double fb[4], gb[4], qr[4];
     for (int v = 0; v < 4; ++v) {
-      qb[lr][v] += a * Qxb[v] + b * Qeb[v];
+      qr[v] = a * Qxb[v] + b * Qeb[v];
       fb[v] = a * fxb[v] + b * feb[v];
       gb[v] = a * gxb[v] + b * geb[v];
     }
-    euler_fg_rev(gm1, q[lr], fb, gb, qb[lr]);
+    euler_fg_rev(gm1, q[lr], fb, gb, qr);
+    for (int v = 0; v < 4; ++v) tm.add(&qb[lr][v], qr[v]);
   }
   if (!T.eulerian) {
     const int l = t * Mc + s;
     const double ir = 1.0 / q[l][0];
-    qb[l][1] += Vb[0] * ir;
-    qb[l][2] += Vb[1] * ir;
-    qb[l][0] -= (Vb[0] * q[l][1] + Vb[1] * q[l][2]) * ir * ir;
+    tm.add(&qb[l][1], Vb[0] * ir);
+    tm.add(&qb[l][2], Vb[1] * ir);
+    tm.add(&qb[l][0], -(Vb[0] * q[l][1] + Vb[1] * q[l][2]) * ir * ir);
   }
 }
 
-template <int M>
+template <int M, class Tm>
 AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X, double dts, PredTape<M>& tp,
-                    PredTables<M>& out) {
+                    PredTables<M>& out, PredWork<M>& wk, const Tm& tm) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
-  double q[Nst][4], x[Nst][2];
-  for (int t = 0; t < Nt; ++t)
-    for (int s = 0; s < Mc; ++s) {
-      const int l = t * Mc + s;
-      for (int v = 0; v < 4; ++v) q[l][v] = w[s][v];
-      x[l][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
-      x[l][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
-    }
+  for (int l = tm.rank; l < Nst; l += tm.size) {
+    const int s = l % Mc;
+    for (int v = 0; v < 4; ++v) wk.q[l][v] = w[s][v];
+    wk.x[l][0] = X[0] + (X[2] - X[0]) * T.lat[s][0] + (X[4] - X[0]) * T.lat[s][1];
+    wk.x[l][1] = X[1] + (X[3] - X[1]) * T.lat[s][0] + (X[5] - X[1]) * T.lat[s][1];
+  }
+  tm.sync();
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
   for (int it = 0; it < nit; ++it) {
-    for (int l = 0; l < Nst; ++l) {
-      for (int v = 0; v < 4; ++v) tp.q[it][l][v] = q[l][v];
-      tp.x[it][l][0] = x[l][0];
-      tp.x[it][l][1] = x[l][1];
+    for (int l = tm.rank; l < Nst; l += tm.size) {
+      for (int v = 0; v < 4; ++v) tp.q[it][l][v] = wk.q[l][v];
+      tp.x[it][l][0] = wk.x[l][0];
+      tp.x[it][l][1] = wk.x[l][1];
     }
-    double P[Nst][4], V[Nst][2];
+    tm.sync();
     const int nsl = it == 0 ? 1 : Nt;
-    for (int t = 0; t < nsl; ++t)
-      for (int s = 0; s < Mc; ++s) pred_node<M>(T, tp.q[it], tp.x[it], t, s, idt, it == 0, P[t * Mc + s], V[t * Mc + s]);
-    for (int t = 1; t < Nt; ++t)
-      for (int s = 0; s < Mc; ++s) {
-        const int l = t * Mc + s;
-        for (int v = 0; v < 4; ++v) {
-          double acc = 0.0;
-          for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * P[(it == 0 ? 0 : u) * Mc + s][v];
-          q[l][v] = tp.q[it][s][v] + dts * acc;
-        }
-        for (int c = 0; c < 2; ++c) {
-          double acc = 0.0;
-          for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * V[(it == 0 ? 0 : u) * Mc + s][c];
-          x[l][c] = tp.x[it][s][c] + dts * acc;
-        }
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size)
+      pred_node<M>(T, tp.q[it], tp.x[it], l / Mc, l % Mc, idt, it == 0, wk.P[l], wk.V[l]);
+    tm.sync();
+    for (int l = Mc + tm.rank; l < Nst; l += tm.size) {
+      const int t = l / Mc, s = l % Mc;
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+        for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * wk.P[(it == 0 ? 0 : u) * Mc + s][v];
+        wk.q[l][v] = tp.q[it][s][v] + dts * acc;
       }
+      for (int c = 0; c < 2; ++c) {
+        double acc = 0.0;
+        for (int u = 0; u < Nt; ++u) acc += T.B[t - 1][u] * wk.V[(it == 0 ? 0 : u) * Mc + s][c];
+        wk.x[l][c] = tp.x[it][s][c] + dts * acc;
+      }
+    }
+    tm.sync();
   }
   const double gm1 = T.gamma - 1.0;
-  tp.bad = 0;
-  for (int l = 0; l < Nst; ++l)
-    if (!(q[l][0] > 0.0) || !(pressure_of(gm1, q[l]) > 0.0)) tp.bad = 1;
-  for (int l = 0; l < Nst; ++l)
-    for (int v = 0; v < 4; ++v) tp.qf[l][v] = q[l][v];
+  int bad = 0;
+  for (int l = tm.rank; l < Nst; l += tm.size) {
+    if (!(wk.q[l][0] > 0.0) || !(pressure_of(gm1, wk.q[l]) > 0.0)) bad = 1;
+    for (int v = 0; v < 4; ++v) tp.qf[l][v] = wk.q[l][v];
+  }
+  bad = tm.any(bad);
+  if (tm.rank == 0) tp.bad = bad;
+  tm.sync();
   // derived tables
-  for (int e = 0; e < 3; ++e)
-    for (int g = 0; g < Nt; ++g)
-      for (int v = 0; v < 4; ++v) {
-        double val[Nt];
-        for (int tt = 0; tt < Nt; ++tt) {
-          double acc = 0.0;
-          for (int r = 0; r < Mc; ++r) acc += T.Tr[e][g][r] * q[tt * Mc + r][v];
-          val[tt] = acc;
-        }
-        for (int p = 0; p < Nt; ++p) {
-          double acc = 0.0;
-          for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
-          out.tr[e][g][p][v] = acc;
-        }
+  constexpr int nTr = 3 * Nt * 4, nItems = nTr + 4 + 6;
+  for (int item = tm.rank; item < nItems; item += tm.size) {
+    if (item < nTr) {
+      const int e = item / (Nt * 4), g = (item / 4) % Nt, v = item % 4;
+      double val[Nt];
+      for (int tt = 0; tt < Nt; ++tt) {
+        double acc = 0.0;
+        for (int r = 0; r < Mc; ++r) acc += T.Tr[e][g][r] * tp.qf[tt * Mc + r][v];
+        val[tt] = acc;
       }
-  for (int v = 0; v < 4; ++v) {
-    double val[Nt];
-    for (int tt = 0; tt < Nt; ++tt) {
-      double acc = 0.0;
-      for (int r = 0; r < Mc; ++r) acc += T.wavg[r] * q[tt * Mc + r][v];
-      val[tt] = acc;
-    }
-    for (int p = 0; p < Nt; ++p) {
-      double acc = 0.0;
-      for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
-      out.av[p][v] = acc;
+      for (int p = 0; p < Nt; ++p) {
+        double acc = 0.0;
+        for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
+        out.tr[e][g][p][v] = acc;
+      }
+    } else if (item < nTr + 4) {
+      const int v = item - nTr;
+      double val[Nt];
+      for (int tt = 0; tt < Nt; ++tt) {
+        double acc = 0.0;
+        for (int r = 0; r < Mc; ++r) acc += T.wavg[r] * tp.qf[tt * Mc + r][v];
+        val[tt] = acc;
+      }
+      for (int p = 0; p < Nt; ++p) {
+        double acc = 0.0;
+        for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * val[tt];
+        out.av[p][v] = acc;
+      }
+    } else {
+      const int kc = item - nTr - 4, k = kc / 2, c = kc % 2, sn = T.vnode[k];
+      double vel[Nt];
+      for (int tt = 0; tt < Nt; ++tt) {
+        const double* qq = tp.qf[tt * Mc + sn];
+        vel[tt] = T.eulerian ? 0.0 : qq[1 + c] / qq[0];
+      }
+      for (int p = 0; p < Nt; ++p) {
+        double acc = 0.0;
+        for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * vel[tt];
+        out.vd[kc][p] = acc / (p + 1);
+      }
     }
   }
-  for (int kc = 0; kc < 6; ++kc) {
-    const int k = kc / 2, c = kc % 2, sn = T.vnode[k];
-    double vel[Nt];
-    for (int tt = 0; tt < Nt; ++tt) {
-      const double* qq = q[tt * Mc + sn];
-      vel[tt] = T.eulerian ? 0.0 : qq[1 + c] / qq[0];
-    }
-    for (int p = 0; p < Nt; ++p) {
-      double acc = 0.0;
-      for (int tt = 0; tt < Nt; ++tt) acc += T.VtInv[p][tt] * vel[tt];
-      out.vd[kc][p] = acc / (p + 1);
-    }
-  }
+  tm.sync();
 }
 
-// Reverse of pred_fwd: tb = dJ/d(tables); adds to wb (Mc x 4) and Xb (6).
-template <int M>
+// Reverse of pred_fwd: tb = dJ/d(tables); adds to wb (Mc x 4, each node by
+// one rank) and Xb (6, rank 0).
+template <int M, class Tm>
 AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, const PredTables<M>& tb,
-                    double (*wb)[4], double* Xb) {
+                    double (*wb)[4], double* Xb, PredRev<M>& wk, const Tm& tm) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
-  double qb[Nst][4], xb[Nst][2];
-  for (int l = 0; l < Nst; ++l) {
-    for (int v = 0; v < 4; ++v) qb[l][v] = 0.0;
-    xb[l][0] = xb[l][1] = 0.0;
-  }
-  // tables
-  for (int e = 0; e < 3; ++e)
-    for (int g = 0; g < Nt; ++g)
-      for (int v = 0; v < 4; ++v)
-        for (int tt = 0; tt < Nt; ++tt) {
+  // tables: the adjoint of every node of the final predictor
+  for (int l = tm.rank; l < Nst; l += tm.size) {
+    const int tt = l / Mc, r = l % Mc;
+    for (int v = 0; v < 4; ++v) {
+      double acc = 0.0;
+      for (int e = 0; e < 3; ++e)
+        for (int g = 0; g < Nt; ++g) {
           double valb = 0.0;
           for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.tr[e][g][p][v];
-          for (int r = 0; r < Mc; ++r) qb[tt * Mc + r][v] += T.Tr[e][g][r] * valb;
+          acc += T.Tr[e][g][r] * valb;
         }
-  for (int v = 0; v < 4; ++v)
-    for (int tt = 0; tt < Nt; ++tt) {
       double valb = 0.0;
       for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.av[p][v];
-      for (int r = 0; r < Mc; ++r) qb[tt * Mc + r][v] += T.wavg[r] * valb;
+      acc += T.wavg[r] * valb;
+      wk.qb[l][v] = acc;
     }
-  if (!T.eulerian)
-    for (int kc = 0; kc < 6; ++kc) {
-      const int k = kc / 2, c = kc % 2, sn = T.vnode[k];
-      for (int tt = 0; tt < Nt; ++tt) {
-        double velb = 0.0;
-        for (int p = 0; p < Nt; ++p) velb += T.VtInv[p][tt] * tb.vd[kc][p] / (p + 1);
-        const double* qq = tp.qf[tt * Mc + sn];
-        qb[tt * Mc + sn][1 + c] += velb / qq[0];
-        qb[tt * Mc + sn][0] -= velb * qq[1 + c] / (qq[0] * qq[0]);
+    if (!T.eulerian)
+      for (int k = 0; k < 3; ++k) {
+        if (T.vnode[k] != r) continue;
+        const double* qq = tp.qf[l];
+        for (int c = 0; c < 2; ++c) {
+          double velb = 0.0;
+          for (int p = 0; p < Nt; ++p) velb += T.VtInv[p][tt] * tb.vd[2 * k + c][p] / (p + 1);
+          wk.qb[l][1 + c] += velb / qq[0];
+          wk.qb[l][0] -= velb * qq[1 + c] / (qq[0] * qq[0]);
+        }
       }
-    }
+    wk.xb[l][0] = wk.xb[l][1] = 0.0;
+  }
+  tm.sync();
   // Picard iterations in reverse
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
   for (int it = nit - 1; it >= 0; --it) {
-    double Pb[Nst][4], Vb[Nst][2];
-    for (int l = 0; l < Nst; ++l) {
-      for (int v = 0; v < 4; ++v) Pb[l][v] = 0.0;
-      Vb[l][0] = Vb[l][1] = 0.0;
-    }
-    double qo[Nst][4], xo[Nst][2];  // adjoint of the iterate entering it
-    for (int s = 0; s < Mc; ++s) {
-      for (int v = 0; v < 4; ++v) qo[s][v] = qb[s][v];
-      xo[s][0] = xb[s][0];
-      xo[s][1] = xb[s][1];
-    }
-    for (int l = Mc; l < Nst; ++l) {
-      for (int v = 0; v < 4; ++v) qo[l][v] = 0.0;
-      xo[l][0] = xo[l][1] = 0.0;
-    }
-    for (int t = 1; t < Nt; ++t)
-      for (int s = 0; s < Mc; ++s) {
-        const int l = t * Mc + s;
+    for (int l = tm.rank; l < Nst; l += tm.size) {
+      const int u = l / Mc, s = l % Mc;
+      double P[4] = {0, 0, 0, 0}, V[2] = {0, 0};
+      if (it > 0 || u == 0)
+        for (int t = 1; t < Nt; ++t) {
+          double bt = 0.0;
+          if (it > 0) bt = T.B[t - 1][u];
+          else
+            for (int uu = 0; uu < Nt; ++uu) bt += T.B[t - 1][uu];
+          for (int v = 0; v < 4; ++v) P[v] += dts * bt * wk.qb[t * Mc + s][v];
+          for (int c = 0; c < 2; ++c) V[c] += dts * bt * wk.xb[t * Mc + s][c];
+        }
+      for (int v = 0; v < 4; ++v) wk.Pb[l][v] = P[v];
+      wk.Vb[l][0] = V[0];
+      wk.Vb[l][1] = V[1];
+      if (u == 0) {
         for (int v = 0; v < 4; ++v) {
-          qo[s][v] += qb[l][v];
-          for (int u = 0; u < Nt; ++u) Pb[(it == 0 ? 0 : u) * Mc + s][v] += dts * T.B[t - 1][u] * qb[l][v];
+          double acc = wk.qb[s][v];
+          for (int t = 1; t < Nt; ++t) acc += wk.qb[t * Mc + s][v];
+          wk.qo[l][v] = acc;
         }
         for (int c = 0; c < 2; ++c) {
-          xo[s][c] += xb[l][c];
-          for (int u = 0; u < Nt; ++u) Vb[(it == 0 ? 0 : u) * Mc + s][c] += dts * T.B[t - 1][u] * xb[l][c];
+          double acc = wk.xb[s][c];
+          for (int t = 1; t < Nt; ++t) acc += wk.xb[t * Mc + s][c];
+          wk.xo[l][c] = acc;
         }
+      } else {
+        for (int v = 0; v < 4; ++v) wk.qo[l][v] = 0.0;
+        wk.xo[l][0] = wk.xo[l][1] = 0.0;
       }
-    const int nsl = it == 0 ? 1 : Nt;
-    for (int t = 0; t < nsl; ++t)
-      for (int s = 0; s < Mc; ++s)
-        pred_node_rev<M>(T, tp.q[it], tp.x[it], t, s, idt, it == 0, Pb[t * Mc + s], Vb[t * Mc + s], qo, xo);
-    for (int l = 0; l < Nst; ++l) {
-      for (int v = 0; v < 4; ++v) qb[l][v] = qo[l][v];
-      xb[l][0] = xo[l][0];
-      xb[l][1] = xo[l][1];
     }
+    tm.sync();
+    const int nsl = it == 0 ? 1 : Nt;
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size)
+      pred_node_rev<M>(T, tp.q[it], tp.x[it], l / Mc, l % Mc, idt, it == 0, wk.Pb[l], wk.Vb[l], wk.qo, wk.xo, tm);
+    tm.sync();
+    for (int l = tm.rank; l < Nst; l += tm.size) {
+      for (int v = 0; v < 4; ++v) wk.qb[l][v] = wk.qo[l][v];
+      wk.xb[l][0] = wk.xo[l][0];
+      wk.xb[l][1] = wk.xo[l][1];
+    }
+    tm.sync();
   }
   // initial iterate: q = w on every slice, x = lattice positions
-  for (int s = 0; s < Mc; ++s) {
+  double pX[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = tm.rank; s < Mc; s += tm.size) {
     double x0b = 0.0, x1b = 0.0;
     for (int t = 0; t < Nt; ++t) {
-      for (int v = 0; v < 4; ++v) wb[s][v] += qb[t * Mc + s][v];
-      x0b += xb[t * Mc + s][0];
-      x1b += xb[t * Mc + s][1];
+      for (int v = 0; v < 4; ++v) wb[s][v] += wk.qb[t * Mc + s][v];
+      x0b += wk.xb[t * Mc + s][0];
+      x1b += wk.xb[t * Mc + s][1];
     }
     const double l0 = T.lat[s][0], l1 = T.lat[s][1];
-    Xb[0] += x0b * (1.0 - l0 - l1); Xb[2] += x0b * l0; Xb[4] += x0b * l1;
-    Xb[1] += x1b * (1.0 - l0 - l1); Xb[3] += x1b * l0; Xb[5] += x1b * l1;
+    pX[0] += x0b * (1.0 - l0 - l1); pX[2] += x0b * l0; pX[4] += x0b * l1;
+    pX[1] += x1b * (1.0 - l0 - l1); pX[3] += x1b * l0; pX[5] += x1b * l1;
   }
+  for (int k = 0; k < 6; ++k) pX[k] = tm.sum(pX[k]);
+  if (tm.rank == 0)
+    for (int k = 0; k < 6; ++k) Xb[k] += pX[k];
+  tm.sync();
 }
 
-// ---------------------------------------------------------------------------
-// One swept edge surface
-// ---------------------------------------------------------------------------
 template <int M>
 struct EdgeIn {
   using S = Sz<M>;
