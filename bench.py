@@ -369,6 +369,86 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Config 5: gradient of the kinetic energy in the disc r < 1 about the
+    vortex centre after 50 LTS sweeps of P2 on the ~50k-triangle isentropic
+    vortex, with respect to the initial averages and node positions
+    (checkpoints every 10 sweeps).  One step = load, checkpointed forward run,
+    reverse pass.  value = element updates of the forward run differentiated
+    per second of the reverse pass."""
+    import torch
+    from paper_1408_3719_gb300 import aleweno
+    from paper_1408_3719_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    aleweno.load()
+    mesh, Q0 = W.vortex(args.vortex_n)
+    n_sw, ck = args.adj_sweeps, args.ckpt
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    s = aleweno.Solver(order_M=args.order, t_end=1.0, stream=stream.cuda_stream)
+    s.load_mesh(mesh)
+    corners = W._corner_coords(mesh).mean(1) - 5.0
+    mask = (np.hypot(corners[:, 0], corners[:, 1]) < 1.0).astype(np.float64)
+
+    def dJ(e):
+        Q, X = e["Q"], e["X"]
+        A = 0.5 * ((X[:, 2] - X[:, 0]) * (X[:, 5] - X[:, 1]) - (X[:, 3] - X[:, 1]) * (X[:, 4] - X[:, 0]))
+        ke = 0.5 * (Q[:, 1] ** 2 + Q[:, 2] ** 2) / Q[:, 0]
+        gQ = np.zeros_like(Q)
+        gQ[:, 0] = -mask * A * ke / Q[:, 0]
+        gQ[:, 1] = mask * A * Q[:, 1] / Q[:, 0]
+        gQ[:, 2] = mask * A * Q[:, 2] / Q[:, 0]
+        sk = 0.5 * mask * ke
+        gX = np.stack([sk * (X[:, 3] - X[:, 5]), sk * (X[:, 4] - X[:, 2]), sk * (X[:, 5] - X[:, 1]),
+                       sk * (X[:, 0] - X[:, 4]), sk * (X[:, 1] - X[:, 3]), sk * (X[:, 2] - X[:, 0])], axis=1)
+        return gQ, gX
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    t_plain, t_fwd, t_adj, updates = [], [], [], 0
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        s.load_state(Q0)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        s.enqueue(n_sw)
+        e1.record(stream)
+        updates = s.sync()
+        e1.synchronize()
+        flush.fill_(float(k))
+        s.load_state(Q0)
+        e2, e3, e4 = ev(), ev(), ev()
+        e2.record(stream)
+        s.adjoint_forward(n_sw, ck)
+        e3.record(stream)
+        gQ, gX = dJ(s.get_elem())
+        flush.fill_(float(k))
+        e4.record(stream)
+        s.adjoint(gQ, gX, None)
+        e5 = ev()
+        e5.record(stream)
+        e5.synchronize()
+        if k >= args.warmup:
+            t_plain.append(e0.elapsed_time(e1))
+            t_fwd.append(e2.elapsed_time(e3))
+            t_adj.append(e4.elapsed_time(e5))
+    mp, mf, ma = (float(np.median(t)) for t in (t_plain, t_fwd, t_adj))
+    line = {"metric": METRIC, "value": updates / (ma * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ma, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"adjoint: isentropic vortex, {Q0.shape[0]} triangles, P{args.order} LTS, "
+                                   f"{n_sw} sweeps, checkpoints every {ck}; value = forward element updates "
+                                   f"differentiated per second of the reverse pass",
+                       "n_tris": int(Q0.shape[0]), "sweeps": n_sw, "ckpt_every": ck, "forward_updates": int(updates),
+                       "l2": "256 MiB write before each timed pass"},
+            "forward_ms": mp, "forward_with_checkpoints_ms": mf, "adjoint_ms": ma,
+            "adjoint_over_forward": ma / mp}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,7 +461,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-sweeps", type=int, default=200)
-    ap.add_argument("--workload", default="explosion", choices=["explosion", "batched"])
+    ap.add_argument("--workload", default="explosion", choices=["explosion", "batched", "adjoint"])
+    ap.add_argument("--vortex-n", type=int, default=158)
+    ap.add_argument("--adj-sweeps", type=int, default=50)
+    ap.add_argument("--ckpt", type=int, default=10)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--min-tris", type=int, default=2000)
     ap.add_argument("--max-tris", type=int, default=60000)
@@ -389,6 +472,12 @@ def main():
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "adjoint":
+        if args.order == 3 and "--order" not in sys.argv:
+            args.order = 2
+        if rank == 0:
+            run_adjoint(args)
+        return
     if args.workload == "batched":
         if args.order == 3 and "--order" not in sys.argv:
             args.order = 2

@@ -53,15 +53,19 @@ struct ElemWork {
   } sc;
 };
 
-// Phase B of one element, reversed: one warp per element, its recomputed
+// Phase B of one element, reversed: one block of kElemThreads threads per
+// element (all four SM sub-partitions share its FP64 work), its recomputed
 // forward data and adjoints in shared memory.
+constexpr int kElemThreads = 128;
+
 template <int M>
-__global__ void __launch_bounds__(32) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
+__global__ void __launch_bounds__(kElemThreads) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
   using S = Sz<M>;
-  constexpr int Mc = S::Mc, Nt = S::Nt, NE = S::NE, MaxU = S::MaxU;
+  constexpr int Mc = S::Mc, Nt = S::Nt, NE = S::NE, MaxU = S::MaxU, NT = kElemThreads;
   extern __shared__ double smem_elem[];
+  __shared__ double red[NT / 32];
   ElemWork<M>& W = *reinterpret_cast<ElemWork<M>*>(smem_elem);
-  const adj::TeamWarp tm{(int)threadIdx.x, 32};
+  const adj::TeamBlock tm{(int)threadIdx.x, NT, red};
   const int lane = threadIdx.x;
   const int n = initial ? post.ne : live.cnt->n_ready;
   for (int pos = blockIdx.x; pos < n; pos += gridDim.x) {
@@ -77,9 +81,9 @@ __global__ void __launch_bounds__(32) k_adj_elem(Tab T, Dev post, Dev live, Adj 
     if (lane < 6) W.in.X[lane] = post.X[6 * (size_t)i + lane];
     if (lane < 4) W.in.Q[lane] = post.Q[4 * (size_t)i + lane];
     if (lane == 0) W.in.nU = nU;
-    for (int k = lane; k < kNSten * NE; k += 32) W.in.st[k / NE][k % NE] = post.sten[(size_t)i * kNSten * NE + k];
-    for (int s = lane; s < kNSten; s += 32) W.in.ok[s] = post.sten_ok[(size_t)i * kNSten + s];
-    for (int u = lane; u < nU; u += 32) {
+    for (int k = lane; k < kNSten * NE; k += NT) W.in.st[k / NE][k % NE] = post.sten[(size_t)i * kNSten * NE + k];
+    for (int s = lane; s < kNSten; s += NT) W.in.ok[s] = post.sten_ok[(size_t)i * kNSten + s];
+    for (int u = lane; u < nU; u += NT) {
       const int j = post.u_elem[u0 + u];
       W.mem_j[u] = j;
       const long long tj = post.t[j], dtj = post.dt[j];
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(32) k_adj_elem(Tab T, Dev post, Dev live, Adj 
       for (int k = 0; k < 6; ++k) W.Xvb[u][k] = 0.0;
       for (int v = 0; v < 4; ++v) W.Qvb[u][v] = 0.0;
     }
-    for (int k = lane; k < Mc * 4; k += 32) (&W.wb[0][0])[k] = 0.0;
+    for (int k = lane; k < Mc * 4; k += NT) (&W.wb[0][0])[k] = 0.0;
     if (lane < 6) W.Xb[lane] = 0.0;
     if (lane < 4) W.Qb[lane] = 0.0;
     tm.sync();
@@ -137,14 +141,14 @@ __global__ void __launch_bounds__(32) k_adj_elem(Tab T, Dev post, Dev live, Adj 
       double* tr = a.trb + (size_t)i * 3 * Nt * Nt * 4;
       double* av = a.avb + (size_t)i * Nt * 4;
       double* vd = a.vdb + (size_t)i * 6 * Nt;
-      for (int k = lane; k < 3 * Nt * Nt * 4; k += 32) { (&W.tb.tr[0][0][0][0])[k] = tr[k]; tr[k] = 0.0; }
-      for (int k = lane; k < Nt * 4; k += 32) { (&W.tb.av[0][0])[k] = av[k]; av[k] = 0.0; }
-      for (int k = lane; k < 6 * Nt; k += 32) { (&W.tb.vd[0][0])[k] = vd[k]; vd[k] = 0.0; }
+      for (int k = lane; k < 3 * Nt * Nt * 4; k += NT) { (&W.tb.tr[0][0][0][0])[k] = tr[k]; tr[k] = 0.0; }
+      for (int k = lane; k < Nt * 4; k += NT) { (&W.tb.av[0][0])[k] = av[k]; av[k] = 0.0; }
+      for (int k = lane; k < 6 * Nt; k += NT) { (&W.tb.vd[0][0])[k] = vd[k]; vd[k] = 0.0; }
     }
     tm.sync();
     adj::pred_rev<M>(T, nit, dts, W.pt, W.tb, W.wb, W.Xb, W.sc.pr, tm);
     adj::recon_rev<M>(T, W.in, W.rt, W.wb, W.Xb, W.Qb, W.Xvb, W.Qvb, W.sc.rr, tm);
-    for (int u = lane; u < nU; u += 32) {
+    for (int u = lane; u < nU; u += NT) {
       const int j = W.mem_j[u];
       for (int k = 0; k < 6; ++k) atomicAdd(&a.Xb[6 * (size_t)j + k], W.Xvb[u][k]);
       if (W.mem_tau[u] < 0.0) {
@@ -223,61 +227,82 @@ __global__ void k_adj_update(Dev live, Dev post, Adj a) {
   }
 }
 
+// One lane per Gauss point: GS lanes (a power of two >= (M+1)^2) per active
+// edge; the corner adjoints are summed over the points by a xor-shuffle tree,
+// the trace adjoints (slots of this edge only) by atomics.
 template <int M>
 __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
-  constexpr int Nt = M + 1;
+  constexpr int Nt = M + 1, NP = Nt * Nt, GS = NP <= 4 ? 4 : 16;
   const int epoch = d.cnt->epoch;
-  const int n = d.cnt->n_active;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const int ed = d.active_list[q];
-    const int na = d.edge_nodes[2 * ed], nb_ = d.edge_nodes[2 * ed + 1];
-    const int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
-    const int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
-    const bool ma = d.node_moved[na] == epoch, mb = d.node_moved[nb_] == epoch;
-    const int le1 = le == 2 ? 0 : le + 1;
-    const double sax = d.cshift[6 * (size_t)L + 2 * le], say = d.cshift[6 * (size_t)L + 2 * le + 1];
-    const double sbx = d.cshift[6 * (size_t)L + 2 * le1], sby = d.cshift[6 * (size_t)L + 2 * le1 + 1];
-    adj::EdgeIn<M> in;
-    in.P[0][0] = d.nX[2 * na] + sax; in.P[0][1] = d.nX[2 * na + 1] + say; in.tk[0] = (double)d.nt[na];
-    in.P[1][0] = d.nX[2 * nb_] + sbx; in.P[1][1] = d.nX[2 * nb_ + 1] + sby; in.tk[1] = (double)d.nt[nb_];
-    if (mb) { in.P[2][0] = d.nXn[2 * nb_] + sbx; in.P[2][1] = d.nXn[2 * nb_ + 1] + sby; in.tk[2] = (double)d.ntn[nb_]; }
-    else { in.P[2][0] = in.P[1][0]; in.P[2][1] = in.P[1][1]; in.tk[2] = in.tk[1]; }
-    if (ma) { in.P[3][0] = d.nXn[2 * na] + sax; in.P[3][1] = d.nXn[2 * na + 1] + say; in.tk[3] = (double)d.ntn[na]; }
-    else { in.P[3][0] = in.P[0][0]; in.P[3][1] = in.P[0][1]; in.tk[3] = in.tk[0]; }
-    in.tsec = d.etick[L];
-    in.tL = (double)d.t[L];
-    in.dtL = (double)d.dt[L];
-    const double* cL = d.trace + (((size_t)L * 3 + le) * Nt) * Nt * 4;
-    for (int k = 0; k < Nt * Nt * 4; ++k) (&in.trL[0][0][0])[k] = cL[k];
-    in.has_R = R >= 0;
-    in.bc = d.edge_bc[ed];
-    if (R >= 0) {
-      in.tR = (double)d.t[R];
-      in.dtR = (double)d.dt[R];
-      const double* cR = d.trace + (((size_t)R * 3 + lr) * Nt) * Nt * 4;
-      for (int k = 0; k < Nt * Nt * 4; ++k) (&in.trR[0][0][0])[k] = cR[k];
-    }
-    double Gb[4];
-    for (int v = 0; v < 4; ++v) Gb[v] = -a.gb[4 * (size_t)L + v] + (R >= 0 ? a.gb[4 * (size_t)R + v] : 0.0);
+  const int n_items = d.cnt->n_active * GS;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
+    const int item = base + threadIdx.x;
+    const int q = item / GS, pt = item % GS;
     double Pb[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
-    for (int k = 0; k < Nt * Nt * 4; ++k) {
-      (&trLb[0][0][0])[k] = 0.0;
-      (&trRb[0][0][0])[k] = 0.0;
+    int na = 0, nb_ = 0;
+    bool ma = false, mb = false;
+    if (item < n_items) {
+      const int ed = d.active_list[q];
+      na = d.edge_nodes[2 * ed];
+      nb_ = d.edge_nodes[2 * ed + 1];
+      ma = d.node_moved[na] == epoch;
+      mb = d.node_moved[nb_] == epoch;
+      if (pt < NP) {
+        const int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
+        const int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
+        const int le1 = le == 2 ? 0 : le + 1;
+        const double sax = d.cshift[6 * (size_t)L + 2 * le], say = d.cshift[6 * (size_t)L + 2 * le + 1];
+        const double sbx = d.cshift[6 * (size_t)L + 2 * le1], sby = d.cshift[6 * (size_t)L + 2 * le1 + 1];
+        adj::EdgeIn<M> in;
+        in.P[0][0] = d.nX[2 * na] + sax; in.P[0][1] = d.nX[2 * na + 1] + say; in.tk[0] = (double)d.nt[na];
+        in.P[1][0] = d.nX[2 * nb_] + sbx; in.P[1][1] = d.nX[2 * nb_ + 1] + sby; in.tk[1] = (double)d.nt[nb_];
+        if (mb) { in.P[2][0] = d.nXn[2 * nb_] + sbx; in.P[2][1] = d.nXn[2 * nb_ + 1] + sby; in.tk[2] = (double)d.ntn[nb_]; }
+        else { in.P[2][0] = in.P[1][0]; in.P[2][1] = in.P[1][1]; in.tk[2] = in.tk[1]; }
+        if (ma) { in.P[3][0] = d.nXn[2 * na] + sax; in.P[3][1] = d.nXn[2 * na + 1] + say; in.tk[3] = (double)d.ntn[na]; }
+        else { in.P[3][0] = in.P[0][0]; in.P[3][1] = in.P[0][1]; in.tk[3] = in.tk[0]; }
+        in.tsec = d.etick[L];
+        in.tL = (double)d.t[L];
+        in.dtL = (double)d.dt[L];
+        const int gx = pt / Nt, gt = pt % Nt;
+        const double* cL = d.trace + (((size_t)L * 3 + le) * Nt) * Nt * 4;
+        for (int k = 0; k < Nt * 4; ++k) (&in.trL[gx][0][0])[k] = cL[gx * Nt * 4 + k];
+        in.has_R = R >= 0;
+        in.bc = d.edge_bc[ed];
+        if (R >= 0) {
+          in.tR = (double)d.t[R];
+          in.dtR = (double)d.dt[R];
+          const double* cR = d.trace + (((size_t)R * 3 + lr) * Nt) * Nt * 4;
+          const int gr = Nt - 1 - gx;
+          for (int k = 0; k < Nt * 4; ++k) (&in.trR[gr][0][0])[k] = cR[gr * Nt * 4 + k];
+        }
+        double Gb[4];
+        for (int v = 0; v < 4; ++v) Gb[v] = -a.gb[4 * (size_t)L + v] + (R >= 0 ? a.gb[4 * (size_t)R + v] : 0.0);
+        double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
+        for (int p = 0; p < Nt; ++p)
+          for (int v = 0; v < 4; ++v) trLb[gx][p][v] = trRb[Nt - 1 - gx][p][v] = 0.0;
+        adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
+        double* tL = a.trb + (((size_t)L * 3 + le) * Nt + gx) * Nt * 4;
+        for (int k = 0; k < Nt * 4; ++k) atomicAdd(&tL[k], (&trLb[gx][0][0])[k]);
+        if (R >= 0) {
+          double* tR = a.trb + (((size_t)R * 3 + lr) * Nt + (Nt - 1 - gx)) * Nt * 4;
+          for (int k = 0; k < Nt * 4; ++k) atomicAdd(&tR[k], (&trRb[Nt - 1 - gx][0][0])[k]);
+        }
+      }
     }
-    adj::edge_rev<M>(T, in, Gb, Pb, trLb, trRb);
-    double* tL = a.trb + (((size_t)L * 3 + le) * Nt) * Nt * 4;
-    for (int k = 0; k < Nt * Nt * 4; ++k) tL[k] += (&trLb[0][0][0])[k];
-    if (R >= 0) {
-      double* tR = a.trb + (((size_t)R * 3 + lr) * Nt) * Nt * 4;
-      for (int k = 0; k < Nt * Nt * 4; ++k) tR[k] += (&trRb[0][0][0])[k];
-    }
-    for (int c = 0; c < 2; ++c) {
-      atomicAdd(&a.nXb[2 * na + c], Pb[0][c] + (ma ? 0.0 : Pb[3][c]));
-      atomicAdd(&a.nXb[2 * nb_ + c], Pb[1][c] + (mb ? 0.0 : Pb[2][c]));
-      if (mb) atomicAdd(&a.nXnb[2 * nb_ + c], Pb[2][c]);
-      if (ma) atomicAdd(&a.nXnb[2 * na + c], Pb[3][c]);
-    }
+#pragma unroll
+    for (int off = GS / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) Pb[k][c] += __shfl_xor_sync(0xffffffffu, Pb[k][c], off, GS);
+    if (item < n_items && pt == 0)
+      for (int c = 0; c < 2; ++c) {
+        atomicAdd(&a.nXb[2 * na + c], Pb[0][c] + (ma ? 0.0 : Pb[3][c]));
+        atomicAdd(&a.nXb[2 * nb_ + c], Pb[1][c] + (mb ? 0.0 : Pb[2][c]));
+        if (mb) atomicAdd(&a.nXnb[2 * nb_ + c], Pb[2][c]);
+        if (ma) atomicAdd(&a.nXnb[2 * na + c], Pb[3][c]);
+      }
   }
 }
 
@@ -371,16 +396,16 @@ void elem_impl(const Tab& T, const Dev& post, const Dev& live, const Adj& a, int
     cudaFuncSetAttribute(k_adj_elem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     attr = true;
   }
-  const int per_sm = (int)((227 * 1024) / bytes);
+  const int per_sm = (int)((227 * 1024) / (bytes + 1024));
   const int grid = initial ? post.ne : nsm * (per_sm > 0 ? per_sm : 1);
-  k_adj_elem<M><<<grid, 32, bytes, s>>>(T, post, live, a, initial);
+  k_adj_elem<M><<<grid, kElemThreads, bytes, s>>>(T, post, live, a, initial);
 }
 
 template <int M>
 void phase_a_impl(const Tab& T, const Dev& live, const Dev& post, const Adj& a, int nsm, cudaStream_t s) {
   k_adj_commit<<<nsm * 2, 128, 0, s>>>(live, a);
   k_adj_update<<<nsm * 2, 128, 0, s>>>(live, post, a);
-  k_adj_edges<M><<<nsm * 4, 128, 0, s>>>(T, live, a);
+  k_adj_edges<M><<<nsm * 8, 128, 0, s>>>(T, live, a);
   k_adj_nodes<M><<<nsm * 4, 64, 0, s>>>(T, live, a);
 }
 

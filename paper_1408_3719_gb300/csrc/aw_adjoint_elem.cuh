@@ -78,6 +78,45 @@ struct TeamWarp {
   }
 };
 
+// the threads of a block; red = shared scratch of one double per warp; every
+// thread calls sync, sum and any
+struct TeamBlock {
+  int rank, size;
+  double* red;
+  AW_HD void sync() const {
+#ifdef __CUDA_ARCH__
+    __syncthreads();
+#endif
+  }
+  AW_HD double sum(double v) const {
+#ifdef __CUDA_ARCH__
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((rank & 31) == 0) red[rank >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (size >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+#else
+    return v;
+#endif
+  }
+  AW_HD void add(double* p, double v) const {
+#ifdef __CUDA_ARCH__
+    atomicAdd(p, v);
+#else
+    *p += v;
+#endif
+  }
+  AW_HD int any(int f) const {
+#ifdef __CUDA_ARCH__
+    return __syncthreads_or(f);
+#else
+    return f;
+#endif
+  }
+};
+
 AW_HD inline double tri_area(const double* X) {
   return 0.5 * ((X[2] - X[0]) * (X[5] - X[1]) - (X[3] - X[1]) * (X[4] - X[0]));
 }
@@ -183,6 +222,7 @@ struct ReconRev {
   double omtb[kNSten][4], dot[4];
   double chb[kNSten][S::NU][4], cb[kNSten][S::NU][4];
   double lam[kNSten][S::NU][4];
+  double nsym[kNSten][S::NU][S::NU];  // -(lam c^T + c lam^T): adjoint of the symmetric normal matrix
 };
 
 template <int M>
@@ -322,15 +362,18 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp, const
     tp.e1[s][r] = sg + 1e-14;
   }
   tm.sync();
+  for (int it = tm.rank; it < kNSten * 4; it += tm.size) {
+    const int s = it / 4, r = it % 4;
+    tp.om[s][r] = 0.0;
+    if (!in.ok[s]) continue;
+    const double e1 = tp.e1[s][r], e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
+    tp.om[s][r] = (s == 0 ? 1e5 : 1.0) / e8;
+  }
+  tm.sync();
   for (int r = tm.rank; r < 4; r += tm.size) {
     double tot = 0.0;
-    for (int s = 0; s < kNSten; ++s) {
-      tp.om[s][r] = 0.0;
-      if (!in.ok[s]) continue;
-      const double e1 = tp.e1[s][r], e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
-      tp.om[s][r] = (s == 0 ? 1e5 : 1.0) / e8;
-      tot += tp.om[s][r];
-    }
+    for (int s = 0; s < kNSten; ++s)
+      if (in.ok[s]) tot += tp.om[s][r];
     tp.tot[r] = tot;
   }
   tm.sync();
@@ -457,10 +500,11 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
   // eigenvectors of the direction n and the state Q, then n = g / |g|
   if (tm.rank == 0) {
     double nxb = 0.0, nyb = 0.0;
-    const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
+    const double g = T.gamma, rho = in.Q[0], irho = 1.0 / rho, u = in.Q[1] * irho, v = in.Q[2] * irho;
+    const double nx = tp.nx, ny = tp.ny;
     const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
-    const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny;
-    const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), ia = 1.0 / a;
+    const double a = sqrt(g * p * irho), ia = 1.0 / a, H = (in.Q[3] + p) * irho, un = u * nx + v * ny;
+    const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) * ia * ia;
     double ub = 0, vb = 0, ab = 0, Hb = 0, unb = 0, utb = 0, q2b = 0, b1b = 0, b2b = 0, iab = 0;
     const double* R_ = sc.Rb;
     ub += R_[4]; ab -= R_[4] * nx; nxb -= R_[4] * a;
@@ -493,7 +537,7 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     b1b += 0.5 * L_[15];
     // b2 = b1 q2, b1 = (g-1)/a^2, ia = 1/a
     b1b += b2b * q2; q2b += b2b * b1;
-    ab += b1b * (-2.0 * b1 / a);
+    ab += b1b * (-2.0 * b1 * ia);
     ab -= iab * ia * ia;
     // q2, un, ut
     ub += q2b * u; vb += q2b * v;
@@ -501,19 +545,19 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     ub -= utb * ny; vb += utb * nx; nyb -= utb * u; nxb += utb * v;
     // H = (E + p)/rho, a = sqrt(g p / rho)
     double rhob = 0.0, pb = 0.0, Eb = 0.0;
-    Eb += Hb / rho; pb += Hb / rho; rhob -= Hb * H / rho;
-    pb += ab * g / (2.0 * a * rho); rhob -= ab * a / (2.0 * rho);
+    Eb += Hb * irho; pb += Hb * irho; rhob -= Hb * H * irho;
+    pb += ab * g * 0.5 * ia * irho; rhob -= ab * a * 0.5 * irho;
     // p = (g-1)(E - rho (u^2+v^2)/2)
     Eb += pb * (g - 1.0); rhob -= pb * (g - 1.0) * 0.5 * (u * u + v * v);
     ub -= pb * (g - 1.0) * rho * u; vb -= pb * (g - 1.0) * rho * v;
     // u = Q1 / rho, v = Q2 / rho
-    pQ[1] += ub / rho; rhob -= ub * u / rho;
-    pQ[2] += vb / rho; rhob -= vb * v / rho;
+    pQ[1] += ub * irho; rhob -= ub * u * irho;
+    pQ[2] += vb * irho; rhob -= vb * v * irho;
     pQ[0] += rhob;
     pQ[3] += Eb;
     if (tp.gn > 0.0) {
-      const double dn = tp.nx * nxb + tp.ny * nyb;
-      const double gxb = (nxb - tp.nx * dn) / tp.gn, gyb = (nyb - tp.ny * dn) / tp.gn;
+      const double dn = tp.nx * nxb + tp.ny * nyb, ign = 1.0 / tp.gn;
+      const double gxb = (nxb - tp.nx * dn) * ign, gyb = (nyb - tp.ny * dn) * ign;
       sc.cb[0][0][0] += gxb * tp.J[0] + gyb * tp.J[1];
       sc.cb[0][1][0] += gxb * tp.J[2] + gyb * tp.J[3];
       pJ[0] += gxb * tp.c[0][0][0];
@@ -533,6 +577,14 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     for (int a = 0; a < NU; ++a) sc.lam[s][a][v] = y[a];
   }
   tm.sync();
+  for (int it = tm.rank; it < kNSten * NU * NU; it += tm.size) {
+    const int s = it / (NU * NU), k = (it / NU) % NU, bb = it % NU;
+    if (!in.ok[s]) continue;
+    double acc = 0.0;
+    for (int v = 0; v < 4; ++v) acc -= sc.lam[s][k][v] * tp.c[s][bb][v] + sc.lam[s][bb][v] * tp.c[s][k][v];
+    sc.nsym[s][k][bb] = acc;
+  }
+  tm.sync();
   // each member row: its adjoint from every stencil that holds it, then the
   // reverse of the row (basis averages over the virtual member, Qv - Q)
   const double* X = in.X;
@@ -547,14 +599,9 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
       for (int m = 1; m < NE; ++m) {
         if (in.st[s][m] != ri) continue;
         const double(*lam)[4] = sc.lam[s];
-        const double(*c)[4] = tp.c[s];
         for (int k = 0; k < NU; ++k) {
           double acc = 0.0;
-          for (int bb = 0; bb < NU; ++bb) {
-            double nkb = 0.0;  // Nb[k][bb] + Nb[bb][k], Nb = -lam c^T
-            for (int v = 0; v < 4; ++v) nkb -= lam[k][v] * c[bb][v] + lam[bb][v] * c[k][v];
-            acc += nkb * r[bb];
-          }
+          for (int bb = 0; bb < NU; ++bb) acc += sc.nsym[s][k][bb] * r[bb];
           for (int v = 0; v < 4; ++v) acc += lam[k][v] * r[NU + v];
           rb[k] += acc;
         }
@@ -645,145 +692,73 @@ struct PredTables {
   double vd[6][S::Nt];            // vertex k, component c -> [2k + c], powers 1..Nt
 };
 
-// work arrays of the predictor (forward iterate, nodal P and V) and of its
-// reverse
+// work arrays of the predictor (forward iterate, nodal fluxes, P and V) and
+// of its reverse
 template <int M>
 struct PredWork {
   using S = Sz<M>;
-  double q[S::Nst][4], x[S::Nst][2], P[S::Nst][4], V[S::Nst][2];
+  double q[S::Nst][4], x[S::Nst][2], F[S::Nst][4], G[S::Nst][4], P[S::Nst][4], V[S::Nst][2];
 };
 template <int M>
 struct PredRev {
   using S = Sz<M>;
   double qb[S::Nst][4], xb[S::Nst][2], qo[S::Nst][4], xo[S::Nst][2], Pb[S::Nst][4], Vb[S::Nst][2];
+  double F[S::Nst][4], G[S::Nst][4];
+  // node-local adjoints of the derivative sums at each node: Q_xi, Q_eta,
+  // f_xi, f_eta, g_xi, g_eta (4 each), x_xi, x_eta, y_xi, y_eta, x_tau, y_tau
+  double dq[S::Nst][6][4], dx[S::Nst][6];
 };
 
-// nodal P and V of slice t of iterate (q, x); stat = iteration 0 (no mesh
-// motion yet, so xi_t = eta_t = 0)
-template <int M>
-AW_HD inline void pred_node(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
-                            bool stat, double* P, double* V) {
-  using S = Sz<M>;
-  constexpr int Mc = S::Mc, Nt = S::Nt;
+// Euler fluxes and mesh velocity of one node (one reciprocal of rho)
+AW_HD inline void node_fluxes(const Tab& T, const double* q, double* f, double* g, double* V) {
   const double gm1 = T.gamma - 1.0;
-  double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
-  double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
-  double xx = 0, xe = 0, yx = 0, ye = 0;
-  for (int r = 0; r < Mc; ++r) {
-    const double a = T.Dxi[s][r], b = T.Deta[s][r];
-    const int lr = t * Mc + r;
-    double f[4], g[4];
-    euler_fg(gm1, q[lr], f, g);
-    for (int v = 0; v < 4; ++v) {
-      Qx[v] += a * q[lr][v]; Qe[v] += b * q[lr][v];
-      fx[v] += a * f[v]; fe[v] += b * f[v];
-      gx[v] += a * g[v]; ge[v] += b * g[v];
-    }
-    xx += a * x[lr][0]; xe += b * x[lr][0];
-    yx += a * x[lr][1]; ye += b * x[lr][1];
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  f[0] = q[1]; f[1] = q[1] * u + p; f[2] = q[1] * v; f[3] = u * (q[3] + p);
+  g[0] = q[2]; g[1] = q[2] * u; g[2] = q[2] * v + p; g[3] = v * (q[3] + p);
+  if (V) {
+    V[0] = T.eulerian ? 0.0 : u;
+    V[1] = T.eulerian ? 0.0 : v;
   }
-  double xt = 0.0, yt = 0.0;
-  if (!stat) {
-    for (int u = 0; u < Nt; ++u) {
-      xt += T.Dtau[t][u] * x[u * Mc + s][0];
-      yt += T.Dtau[t][u] * x[u * Mc + s][1];
-    }
-    xt *= idt;
-    yt *= idt;
-  }
-  const double idet = 1.0 / (xx * ye - xe * yx);
-  const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
-  const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
-  for (int v = 0; v < 4; ++v) {
-    const double fs = -(fx[v] * xix + fe[v] * etx + gx[v] * xiy + ge[v] * ety);
-    P[v] = fs - (Qx[v] * xit + Qe[v] * ett);
-  }
-  const double* qs = q[t * Mc + s];
-  V[0] = T.eulerian ? 0.0 : qs[1] / qs[0];
-  V[1] = T.eulerian ? 0.0 : qs[2] / qs[0];
 }
 
-// reverse of pred_node: adds (through tm.add) to qb, xb of the whole iterate
-template <int M, class Tm>
-AW_HD inline void pred_node_rev(const Tab& T, const double (*q)[4], const double (*x)[2], int t, int s, double idt,
-                                bool stat, const double* Pb, const double* Vb, double (*qb)[4], double (*xb)[2],
-                                const Tm& tm) {
+// the derivative sums and metric terms of node (t, s) of an iterate
+struct NodeGeo {
+  double Qx[4], Qe[4], fx[4], fe[4], gx[4], ge[4];
+  double xx, xe, yx, ye, xt, yt, idet, xix, xiy, etx, ety, xit, ett;
+};
+
+template <int M>
+AW_HD inline void node_geo(const Tab& T, const double (*q)[4], const double (*x)[2], const double (*F)[4],
+                           const double (*G)[4], int t, int s, double idt, bool stat, NodeGeo& n) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt;
-  const double gm1 = T.gamma - 1.0;
-  double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
-  double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
-  double xx = 0, xe = 0, yx = 0, ye = 0;
+  for (int v = 0; v < 4; ++v) n.Qx[v] = n.Qe[v] = n.fx[v] = n.fe[v] = n.gx[v] = n.ge[v] = 0.0;
+  n.xx = n.xe = n.yx = n.ye = 0.0;
   for (int r = 0; r < Mc; ++r) {
     const double a = T.Dxi[s][r], b = T.Deta[s][r];
     const int lr = t * Mc + r;
-    double f[4], g[4];
-    euler_fg(gm1, q[lr], f, g);
     for (int v = 0; v < 4; ++v) {
-      Qx[v] += a * q[lr][v]; Qe[v] += b * q[lr][v];
-      fx[v] += a * f[v]; fe[v] += b * f[v];
-      gx[v] += a * g[v]; ge[v] += b * g[v];
+      n.Qx[v] += a * q[lr][v]; n.Qe[v] += b * q[lr][v];
+      n.fx[v] += a * F[lr][v]; n.fe[v] += b * F[lr][v];
+      n.gx[v] += a * G[lr][v]; n.ge[v] += b * G[lr][v];
     }
-    xx += a * x[lr][0]; xe += b * x[lr][0];
-    yx += a * x[lr][1]; ye += b * x[lr][1];
+    n.xx += a * x[lr][0]; n.xe += b * x[lr][0];
+    n.yx += a * x[lr][1]; n.ye += b * x[lr][1];
   }
-  double xt = 0.0, yt = 0.0;
+  n.xt = n.yt = 0.0;
   if (!stat) {
     for (int u = 0; u < Nt; ++u) {
-      xt += T.Dtau[t][u] * x[u * Mc + s][0];
-      yt += T.Dtau[t][u] * x[u * Mc + s][1];
+      n.xt += T.Dtau[t][u] * x[u * Mc + s][0];
+      n.yt += T.Dtau[t][u] * x[u * Mc + s][1];
     }
-    xt *= idt;
-    yt *= idt;
+    n.xt *= idt;
+    n.yt *= idt;
   }
-  const double idet = 1.0 / (xx * ye - xe * yx);
-  const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
-  const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
-  double Qxb[4], Qeb[4], fxb[4], feb[4], gxb[4], geb[4];
-  double xixb = 0, xiyb = 0, etxb = 0, etyb = 0, xitb = 0, ettb = 0;
-  for (int v = 0; v < 4; ++v) {
-    Qxb[v] = -Pb[v] * xit; Qeb[v] = -Pb[v] * ett;
-    xitb -= Pb[v] * Qx[v]; ettb -= Pb[v] * Qe[v];
-    fxb[v] = -Pb[v] * xix; feb[v] = -Pb[v] * etx; gxb[v] = -Pb[v] * xiy; geb[v] = -Pb[v] * ety;
-    xixb -= Pb[v] * fx[v]; etxb -= Pb[v] * fe[v]; xiyb -= Pb[v] * gx[v]; etyb -= Pb[v] * ge[v];
-  }
-  double xtb = 0, ytb = 0;
-  xixb -= xitb * xt; xiyb -= xitb * yt; xtb -= xitb * xix; ytb -= xitb * xiy;
-  etxb -= ettb * xt; etyb -= ettb * yt; xtb -= ettb * etx; ytb -= ettb * ety;
-  double xxb = 0, xeb = 0, yxb = 0, yeb = 0, idb = 0;
-  yeb += xixb * idet; idb += xixb * ye;
-  xeb -= xiyb * idet; idb -= xiyb * xe;
-  yxb -= etxb * idet; idb -= etxb * yx;
-  xxb += etyb * idet; idb += etyb * xx;
-  const double detb = -idb * idet * idet;
-  xxb += detb * ye; yeb += detb * xx; xeb -= detb * yx; yxb -= detb * xe;
-  if (!stat) {
-    for (int u = 0; u < Nt; ++u) {
-      tm.add(&xb[u * Mc + s][0], idt * T.Dtau[t][u] * xtb);
-      tm.add(&xb[u * Mc + s][1], idt * T.Dtau[t][u] * ytb);
-    }
-  }
-  for (int r = 0; r < Mc; ++r) {
-    const double a = T.Dxi[s][r], b = T.Deta[s][r];
-    const int lr = t * Mc + r;
-    tm.add(&xb[lr][0], a * xxb + b * xeb);
-    tm.add(&xb[lr][1], a * yxb + b * yeb);
-    double fb[4], gb[4], qr[4];
-    for (int v = 0; v < 4; ++v) {
-      qr[v] = a * Qxb[v] + b * Qeb[v];
-      fb[v] = a * fxb[v] + b * feb[v];
-      gb[v] = a * gxb[v] + b * geb[v];
-    }
-    euler_fg_rev(gm1, q[lr], fb, gb, qr);
-    for (int v = 0; v < 4; ++v) tm.add(&qb[lr][v], qr[v]);
-  }
-  if (!T.eulerian) {
-    const int l = t * Mc + s;
-    const double ir = 1.0 / q[l][0];
-    tm.add(&qb[l][1], Vb[0] * ir);
-    tm.add(&qb[l][2], Vb[1] * ir);
-    tm.add(&qb[l][0], -(Vb[0] * q[l][1] + Vb[1] * q[l][2]) * ir * ir);
-  }
+  n.idet = 1.0 / (n.xx * n.ye - n.xe * n.yx);
+  n.xix = n.ye * n.idet; n.xiy = -n.xe * n.idet; n.etx = -n.yx * n.idet; n.ety = n.xx * n.idet;
+  n.xit = -(n.xix * n.xt + n.xiy * n.yt);
+  n.ett = -(n.etx * n.xt + n.ety * n.yt);
 }
 
 template <int M, class Tm>
@@ -800,15 +775,22 @@ AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X
   tm.sync();
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
   for (int it = 0; it < nit; ++it) {
+    const int nsl = it == 0 ? 1 : Nt;
     for (int l = tm.rank; l < Nst; l += tm.size) {
       for (int v = 0; v < 4; ++v) tp.q[it][l][v] = wk.q[l][v];
       tp.x[it][l][0] = wk.x[l][0];
       tp.x[it][l][1] = wk.x[l][1];
+      if (l < nsl * Mc) node_fluxes(T, wk.q[l], wk.F[l], wk.G[l], wk.V[l]);
     }
     tm.sync();
-    const int nsl = it == 0 ? 1 : Nt;
-    for (int l = tm.rank; l < nsl * Mc; l += tm.size)
-      pred_node<M>(T, tp.q[it], tp.x[it], l / Mc, l % Mc, idt, it == 0, wk.P[l], wk.V[l]);
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
+      NodeGeo n;
+      node_geo<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, idt, it == 0, n);
+      for (int v = 0; v < 4; ++v) {
+        const double fs = -(n.fx[v] * n.xix + n.fe[v] * n.etx + n.gx[v] * n.xiy + n.ge[v] * n.ety);
+        wk.P[l][v] = fs - (n.Qx[v] * n.xit + n.Qe[v] * n.ett);
+      }
+    }
     tm.sync();
     for (int l = Mc + tm.rank; l < Nst; l += tm.size) {
       const int t = l / Mc, s = l % Mc;
@@ -881,7 +863,8 @@ AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X
 }
 
 // Reverse of pred_fwd: tb = dJ/d(tables); adds to wb (Mc x 4, each node by
-// one rank) and Xb (6, rank 0).
+// one rank) and Xb (6, rank 0).  Every reverse sum is a gather: each node's
+// adjoint is written by one rank only.
 template <int M, class Tm>
 AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, const PredTables<M>& tb,
                     double (*wb)[4], double* Xb, PredRev<M>& wk, const Tm& tm) {
@@ -907,11 +890,12 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
       for (int k = 0; k < 3; ++k) {
         if (T.vnode[k] != r) continue;
         const double* qq = tp.qf[l];
+        const double ir = 1.0 / qq[0];
         for (int c = 0; c < 2; ++c) {
           double velb = 0.0;
           for (int p = 0; p < Nt; ++p) velb += T.VtInv[p][tt] * tb.vd[2 * k + c][p] / (p + 1);
-          wk.qb[l][1 + c] += velb / qq[0];
-          wk.qb[l][0] -= velb * qq[1 + c] / (qq[0] * qq[0]);
+          wk.qb[l][1 + c] += velb * ir;
+          wk.qb[l][0] -= velb * qq[1 + c] * ir * ir;
         }
       }
     wk.xb[l][0] = wk.xb[l][1] = 0.0;
@@ -920,6 +904,8 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
   // Picard iterations in reverse
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
   for (int it = nit - 1; it >= 0; --it) {
+    const int nsl = it == 0 ? 1 : Nt;
+    const bool stat = it == 0;
     for (int l = tm.rank; l < Nst; l += tm.size) {
       const int u = l / Mc, s = l % Mc;
       double P[4] = {0, 0, 0, 0}, V[2] = {0, 0};
@@ -950,11 +936,69 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
         for (int v = 0; v < 4; ++v) wk.qo[l][v] = 0.0;
         wk.xo[l][0] = wk.xo[l][1] = 0.0;
       }
+      if (l < nsl * Mc) node_fluxes(T, tp.q[it][l], wk.F[l], wk.G[l], nullptr);
     }
     tm.sync();
-    const int nsl = it == 0 ? 1 : Nt;
-    for (int l = tm.rank; l < nsl * Mc; l += tm.size)
-      pred_node_rev<M>(T, tp.q[it], tp.x[it], l / Mc, l % Mc, idt, it == 0, wk.Pb[l], wk.Vb[l], wk.qo, wk.xo, tm);
+    // node-local reverse of P at every node that computed one
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
+      NodeGeo n;
+      node_geo<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, idt, stat, n);
+      const double* Pb = wk.Pb[l];
+      double xixb = 0, xiyb = 0, etxb = 0, etyb = 0, xitb = 0, ettb = 0;
+      for (int v = 0; v < 4; ++v) {
+        wk.dq[l][0][v] = -Pb[v] * n.xit; wk.dq[l][1][v] = -Pb[v] * n.ett;
+        xitb -= Pb[v] * n.Qx[v]; ettb -= Pb[v] * n.Qe[v];
+        wk.dq[l][2][v] = -Pb[v] * n.xix; wk.dq[l][3][v] = -Pb[v] * n.etx;
+        wk.dq[l][4][v] = -Pb[v] * n.xiy; wk.dq[l][5][v] = -Pb[v] * n.ety;
+        xixb -= Pb[v] * n.fx[v]; etxb -= Pb[v] * n.fe[v]; xiyb -= Pb[v] * n.gx[v]; etyb -= Pb[v] * n.ge[v];
+      }
+      double xtb = 0, ytb = 0;
+      xixb -= xitb * n.xt; xiyb -= xitb * n.yt; xtb -= xitb * n.xix; ytb -= xitb * n.xiy;
+      etxb -= ettb * n.xt; etyb -= ettb * n.yt; xtb -= ettb * n.etx; ytb -= ettb * n.ety;
+      double xxb = 0, xeb = 0, yxb = 0, yeb = 0, idb = 0;
+      yeb += xixb * n.idet; idb += xixb * n.ye;
+      xeb -= xiyb * n.idet; idb -= xiyb * n.xe;
+      yxb -= etxb * n.idet; idb -= etxb * n.yx;
+      xxb += etyb * n.idet; idb += etyb * n.xx;
+      const double detb = -idb * n.idet * n.idet;
+      xxb += detb * n.ye; yeb += detb * n.xx; xeb -= detb * n.yx; yxb -= detb * n.xe;
+      wk.dx[l][0] = xxb; wk.dx[l][1] = xeb; wk.dx[l][2] = yxb; wk.dx[l][3] = yeb;
+      wk.dx[l][4] = stat ? 0.0 : xtb;
+      wk.dx[l][5] = stat ? 0.0 : ytb;
+    }
+    tm.sync();
+    // gather onto every node of the iterate
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
+      const int t = l / Mc, r = l % Mc;
+      double qa[4] = {0, 0, 0, 0}, fb[4] = {0, 0, 0, 0}, gb[4] = {0, 0, 0, 0}, x0 = 0.0, x1 = 0.0;
+      for (int s = 0; s < Mc; ++s) {
+        const double a = T.Dxi[s][r], b = T.Deta[s][r];
+        const int ls = t * Mc + s;
+        for (int v = 0; v < 4; ++v) {
+          qa[v] += a * wk.dq[ls][0][v] + b * wk.dq[ls][1][v];
+          fb[v] += a * wk.dq[ls][2][v] + b * wk.dq[ls][3][v];
+          gb[v] += a * wk.dq[ls][4][v] + b * wk.dq[ls][5][v];
+        }
+        x0 += a * wk.dx[ls][0] + b * wk.dx[ls][1];
+        x1 += a * wk.dx[ls][2] + b * wk.dx[ls][3];
+      }
+      if (!stat)
+        for (int tt = 0; tt < Nt; ++tt) {
+          x0 += idt * T.Dtau[tt][t] * wk.dx[tt * Mc + r][4];
+          x1 += idt * T.Dtau[tt][t] * wk.dx[tt * Mc + r][5];
+        }
+      const double* q = tp.q[it][l];
+      euler_fg_rev(T.gamma - 1.0, q, fb, gb, qa);
+      if (!T.eulerian) {
+        const double ir = 1.0 / q[0];
+        qa[1] += wk.Vb[l][0] * ir;
+        qa[2] += wk.Vb[l][1] * ir;
+        qa[0] -= (wk.Vb[l][0] * q[1] + wk.Vb[l][1] * q[2]) * ir * ir;
+      }
+      for (int v = 0; v < 4; ++v) wk.qo[l][v] += qa[v];
+      wk.xo[l][0] += x0;
+      wk.xo[l][1] += x1;
+    }
     tm.sync();
     for (int l = tm.rank; l < Nst; l += tm.size) {
       for (int v = 0; v < 4; ++v) wk.qb[l][v] = wk.qo[l][v];
@@ -982,6 +1026,9 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
   tm.sync();
 }
 
+// ---------------------------------------------------------------------------
+// One swept edge surface
+// ---------------------------------------------------------------------------
 template <int M>
 struct EdgeIn {
   using S = Sz<M>;
@@ -1138,85 +1185,92 @@ AW_HD void edge_fwd(const Tab& T, const EdgeIn<M>& in, double* G) {
     }
 }
 
+// reverse of the Gauss point (gx, gt) of edge_fwd: adds to Pb[4][2] and the
+// two traces' adjoints (row gx of the left trace, row Nt-1-gx of the right)
+template <int M>
+AW_HD void edge_point_rev(const Tab& T, const EdgeIn<M>& in, int gx, int gt, const double* Gb, double (*Pb)[2],
+                          double (*trLb)[Sz<M>::Nt][4], double (*trRb)[Sz<M>::Nt][4]) {
+  constexpr int Nt = Sz<M>::Nt;
+  const double g = T.gamma;
+  double qm[4], qp[4], n[3], dchi[3], dtau[3], tl, tr;
+  edge_point<M>(T, in, gx, gt, qm, qp, n, dchi, dtau, &tl, &tr);
+  const double wq = T.glw[gx] * T.glw[gt];
+  double Fb[4];
+  for (int v = 0; v < 4; ++v) Fb[v] = wq * Gb[v];
+  double qmb[4] = {0, 0, 0, 0}, qpb[4] = {0, 0, 0, 0}, nb[3] = {0, 0, 0};
+  // F = (Fm + Fp)/2 - smax (qp - qm)/2
+  const double sm = speed_of(g, qm, n), sp = speed_of(g, qp, n), smax = fmax(sm, sp);
+  double half[4], smaxb = 0.0;
+  for (int v = 0; v < 4; ++v) {
+    half[v] = 0.5 * Fb[v];
+    smaxb -= 0.5 * Fb[v] * (qp[v] - qm[v]);
+    qpb[v] -= 0.5 * smax * Fb[v];
+    qmb[v] += 0.5 * smax * Fb[v];
+  }
+  side_flux_rev(g, qm, n, half, qmb, nb);
+  side_flux_rev(g, qp, n, half, qpb, nb);
+  if (sm >= sp) speed_rev(g, qm, n, smaxb, qmb, nb);
+  else speed_rev(g, qp, n, smaxb, qpb, nb);
+  // right state
+  if (in.has_R) {
+    double tp_ = 1.0;
+    for (int p = 0; p < Nt; ++p) {
+      for (int v = 0; v < 4; ++v) trRb[Nt - 1 - gx][p][v] += qpb[v] * tp_;
+      tp_ *= tr;
+    }
+  } else {
+    for (int v = 0; v < 4; ++v) qmb[v] += (v == 1 || v == 2) ? 0.0 : qpb[v];
+    const double nn = n[0] * n[0] + n[1] * n[1];
+    if (in.bc == 0 && nn > 0.0) {
+      const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+      qmb[1] += qpb[1];
+      qmb[2] += qpb[2];
+      const double mnb = -2.0 * (qpb[1] * n[0] + qpb[2] * n[1]);
+      nb[0] -= 2.0 * mn * qpb[1];
+      nb[1] -= 2.0 * mn * qpb[2];
+      qmb[1] += mnb * n[0] / nn;
+      qmb[2] += mnb * n[1] / nn;
+      nb[0] += mnb * qm[1] / nn;
+      nb[1] += mnb * qm[2] / nn;
+      const double nnb = -mnb * mn / nn;
+      nb[0] += 2.0 * n[0] * nnb;
+      nb[1] += 2.0 * n[1] * nnb;
+    } else {
+      qmb[1] += qpb[1];
+      qmb[2] += qpb[2];
+    }
+  }
+  {
+    double tp_ = 1.0;
+    for (int p = 0; p < Nt; ++p) {
+      for (int v = 0; v < 4; ++v) trLb[gx][p][v] += qmb[v] * tp_;
+      tp_ *= tl;
+    }
+  }
+  // n = dchi x dtau (spatial components of the corners only)
+  double dchib[3], dtaub[3];
+  dchib[0] = dtau[1] * nb[2] - dtau[2] * nb[1];
+  dchib[1] = dtau[2] * nb[0] - dtau[0] * nb[2];
+  dchib[2] = dtau[0] * nb[1] - dtau[1] * nb[0];
+  dtaub[0] = nb[1] * dchi[2] - nb[2] * dchi[1];
+  dtaub[1] = nb[2] * dchi[0] - nb[0] * dchi[2];
+  dtaub[2] = nb[0] * dchi[1] - nb[1] * dchi[0];
+  const double chi = T.glx[gx], tau = T.glx[gt];
+  for (int c = 0; c < 2; ++c) {
+    Pb[1][c] += (1.0 - tau) * dchib[c]; Pb[0][c] -= (1.0 - tau) * dchib[c];
+    Pb[2][c] += tau * dchib[c]; Pb[3][c] -= tau * dchib[c];
+    Pb[3][c] += (1.0 - chi) * dtaub[c]; Pb[0][c] -= (1.0 - chi) * dtaub[c];
+    Pb[2][c] += chi * dtaub[c]; Pb[1][c] -= chi * dtaub[c];
+  }
+}
+
 // reverse of edge_fwd: adds to Pb[4][2] and the two traces' adjoints
 template <int M>
 AW_HD void edge_rev(const Tab& T, const EdgeIn<M>& in, const double* Gb, double (*Pb)[2], double (*trLb)[Sz<M>::Nt][4],
                     double (*trRb)[Sz<M>::Nt][4]) {
   constexpr int Nt = Sz<M>::Nt;
-  const double g = T.gamma;
   for (int gx = 0; gx < Nt; ++gx)
-    for (int gt = 0; gt < Nt; ++gt) {
-      double qm[4], qp[4], n[3], dchi[3], dtau[3], tl, tr;
-      edge_point<M>(T, in, gx, gt, qm, qp, n, dchi, dtau, &tl, &tr);
-      const double wq = T.glw[gx] * T.glw[gt];
-      double Fb[4];
-      for (int v = 0; v < 4; ++v) Fb[v] = wq * Gb[v];
-      double qmb[4] = {0, 0, 0, 0}, qpb[4] = {0, 0, 0, 0}, nb[3] = {0, 0, 0};
-      // F = (Fm + Fp)/2 - smax (qp - qm)/2
-      const double sm = speed_of(g, qm, n), sp = speed_of(g, qp, n), smax = fmax(sm, sp);
-      double half[4], smaxb = 0.0;
-      for (int v = 0; v < 4; ++v) {
-        half[v] = 0.5 * Fb[v];
-        smaxb -= 0.5 * Fb[v] * (qp[v] - qm[v]);
-        qpb[v] -= 0.5 * smax * Fb[v];
-        qmb[v] += 0.5 * smax * Fb[v];
-      }
-      side_flux_rev(g, qm, n, half, qmb, nb);
-      side_flux_rev(g, qp, n, half, qpb, nb);
-      if (sm >= sp) speed_rev(g, qm, n, smaxb, qmb, nb);
-      else speed_rev(g, qp, n, smaxb, qpb, nb);
-      // right state
-      if (in.has_R) {
-        double tp_ = 1.0;
-        for (int p = 0; p < Nt; ++p) {
-          for (int v = 0; v < 4; ++v) trRb[Nt - 1 - gx][p][v] += qpb[v] * tp_;
-          tp_ *= tr;
-        }
-      } else {
-        for (int v = 0; v < 4; ++v) qmb[v] += (v == 1 || v == 2) ? 0.0 : qpb[v];
-        const double nn = n[0] * n[0] + n[1] * n[1];
-        if (in.bc == 0 && nn > 0.0) {
-          const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
-          qmb[1] += qpb[1];
-          qmb[2] += qpb[2];
-          const double mnb = -2.0 * (qpb[1] * n[0] + qpb[2] * n[1]);
-          nb[0] -= 2.0 * mn * qpb[1];
-          nb[1] -= 2.0 * mn * qpb[2];
-          qmb[1] += mnb * n[0] / nn;
-          qmb[2] += mnb * n[1] / nn;
-          nb[0] += mnb * qm[1] / nn;
-          nb[1] += mnb * qm[2] / nn;
-          const double nnb = -mnb * mn / nn;
-          nb[0] += 2.0 * n[0] * nnb;
-          nb[1] += 2.0 * n[1] * nnb;
-        } else {
-          qmb[1] += qpb[1];
-          qmb[2] += qpb[2];
-        }
-      }
-      {
-        double tp_ = 1.0;
-        for (int p = 0; p < Nt; ++p) {
-          for (int v = 0; v < 4; ++v) trLb[gx][p][v] += qmb[v] * tp_;
-          tp_ *= tl;
-        }
-      }
-      // n = dchi x dtau (spatial components of the corners only)
-      double dchib[3], dtaub[3];
-      dchib[0] = dtau[1] * nb[2] - dtau[2] * nb[1];
-      dchib[1] = dtau[2] * nb[0] - dtau[0] * nb[2];
-      dchib[2] = dtau[0] * nb[1] - dtau[1] * nb[0];
-      dtaub[0] = nb[1] * dchi[2] - nb[2] * dchi[1];
-      dtaub[1] = nb[2] * dchi[0] - nb[0] * dchi[2];
-      dtaub[2] = nb[0] * dchi[1] - nb[1] * dchi[0];
-      const double chi = T.glx[gx], tau = T.glx[gt];
-      for (int c = 0; c < 2; ++c) {
-        Pb[1][c] += (1.0 - tau) * dchib[c]; Pb[0][c] -= (1.0 - tau) * dchib[c];
-        Pb[2][c] += tau * dchib[c]; Pb[3][c] -= tau * dchib[c];
-        Pb[3][c] += (1.0 - chi) * dtaub[c]; Pb[0][c] -= (1.0 - chi) * dtaub[c];
-        Pb[2][c] += chi * dtaub[c]; Pb[1][c] -= chi * dtaub[c];
-      }
-    }
+    for (int gt = 0; gt < Nt; ++gt) edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
 }
 
 // ---------------------------------------------------------------------------
