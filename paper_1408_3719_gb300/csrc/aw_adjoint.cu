@@ -14,6 +14,7 @@
 // k_ready, k_nodes and k_edges on the restored sweep-start state.  Scatters to
 // other elements and nodes use atomics; the slots an element owns (its
 // tables, its edges' traces) are written by one thread only.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cstdio>
@@ -59,7 +60,7 @@ struct ElemWork {
 constexpr int kElemThreads = 128;
 
 template <int M>
-__global__ void __launch_bounds__(kElemThreads) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
+__global__ void __launch_bounds__(kElemThreads, 4) k_adj_elem(Tab T, Dev post, Dev live, Adj a, int initial) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, NE = S::NE, MaxU = S::MaxU, NT = kElemThreads;
   extern __shared__ double smem_elem[];
@@ -394,9 +395,10 @@ void elem_impl(const Tab& T, const Dev& post, const Dev& live, const Adj& a, int
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_adj_elem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_adj_elem<M>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     attr = true;
   }
-  const int per_sm = (int)((227 * 1024) / (bytes + 1024));
+  const int per_sm = std::min(4, (int)((227 * 1024) / (bytes + 1024)));
   const int grid = initial ? post.ne : nsm * (per_sm > 0 ? per_sm : 1);
   k_adj_elem<M><<<grid, kElemThreads, bytes, s>>>(T, post, live, a, initial);
 }
