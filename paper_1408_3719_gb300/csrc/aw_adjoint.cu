@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
     const int item = base + threadIdx.x;
     const int q = item / GS, pt = item % GS;
     double Pb[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    int na = 0, nb_ = 0;
+    double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
+    int na = 0, nb_ = 0, gxl = -1, Ll = 0, lel = 0, Rl = -1, lrl = 0;
     bool ma = false, mb = false;
     if (item < n_items) {
       const int ed = d.active_list[q];
@@ -279,16 +280,29 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
         }
         double Gb[4];
         for (int v = 0; v < 4; ++v) Gb[v] = -a.gb[4 * (size_t)L + v] + (R >= 0 ? a.gb[4 * (size_t)R + v] : 0.0);
-        double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
         for (int p = 0; p < Nt; ++p)
           for (int v = 0; v < 4; ++v) trLb[gx][p][v] = trRb[Nt - 1 - gx][p][v] = 0.0;
         adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
-        double* tL = a.trb + (((size_t)L * 3 + le) * Nt + gx) * Nt * 4;
-        for (int k = 0; k < Nt * 4; ++k) atomicAdd(&tL[k], (&trLb[gx][0][0])[k]);
-        if (R >= 0) {
-          double* tR = a.trb + (((size_t)R * 3 + lr) * Nt + (Nt - 1 - gx)) * Nt * 4;
-          for (int k = 0; k < Nt * 4; ++k) atomicAdd(&tR[k], (&trRb[Nt - 1 - gx][0][0])[k]);
-        }
+        gxl = gx;
+        Ll = L; lel = le; Rl = R; lrl = lr;
+      }
+    }
+    // the Nt points of one Gauss row (gx) are consecutive lanes: sum their
+    // trace adjoints onto the row's first lane, which owns the edge's slots
+    // (each element edge belongs to one swept edge only)
+#pragma unroll
+    for (int k = 0; k < Nt * 4; ++k) {
+      double l_ = gxl >= 0 ? (&trLb[gxl][0][0])[k] : 0.0, r_ = gxl >= 0 ? (&trRb[Nt - 1 - gxl][0][0])[k] : 0.0;
+      double ls = l_, rs = r_;
+#pragma unroll
+      for (int o = 1; o < Nt; ++o) {
+        const double lo = __shfl_down_sync(0xffffffffu, l_, o), ro = __shfl_down_sync(0xffffffffu, r_, o);
+        ls += lo;
+        rs += ro;
+      }
+      if (gxl >= 0 && pt % Nt == 0) {
+        a.trb[(((size_t)Ll * 3 + lel) * Nt + gxl) * Nt * 4 + k] += ls;
+        if (Rl >= 0) a.trb[(((size_t)Rl * 3 + lrl) * Nt + (Nt - 1 - gxl)) * Nt * 4 + k] += rs;
       }
     }
 #pragma unroll
@@ -307,56 +321,122 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
   }
 }
 
-constexpr int kMaxVal = 32;  // Voronoi elements of one node the reverse can hold
-
-template <int M>
-__global__ void __launch_bounds__(64) k_adj_nodes(Tab T, Dev d, Adj a) {
-  constexpr int Nt = M + 1;
-  const int n_moved = d.cnt->n_moved;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_moved; q += gridDim.x * blockDim.x) {
-    const int n = d.moved_list[q];
-    const double Db[2] = {a.nXnb[2 * n], a.nXnb[2 * n + 1]};
-    a.nXb[2 * n] += Db[0];
-    a.nXb[2 * n + 1] += Db[1];
-    const int p0 = d.v2e_ptr[n], nv = d.v2e_ptr[n + 1] - p0;
-    if (nv > kMaxVal) {
-      set_error(d.cnt, -7, -1 - n);
-      continue;
+// Node solver reversed with 8 lanes per moved node, one Voronoi element per
+// lane (strided): D = sum mu_j D_j / sum mu_j with mu_j = rho_j |T_j|.
+__global__ void k_adj_nodes_grp(Tab T, Dev d, Adj a) {
+  constexpr int GS = 8;
+  const int Nt = T.Nt;
+  const int n_items = d.cnt->n_moved * GS;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
+    const int item = base + threadIdx.x;
+    const int q = item / GS, lane = item % GS;
+    const bool live = item < n_items;
+    int n = 0, p0 = 0, p1 = 0, ty = 0;
+    double Db[2] = {0.0, 0.0};
+    long long tk0 = 0, tk1 = 0;
+    if (live) {
+      n = d.moved_list[q];
+      Db[0] = a.nXnb[2 * n];
+      Db[1] = a.nXnb[2 * n + 1];
+      if (lane == 0) {
+        a.nXb[2 * n] += Db[0];
+        a.nXb[2 * n + 1] += Db[1];
+      }
+      ty = d.node_type[n];
+      if (ty == 1) {  // the wall projection is symmetric
+        const double nx = d.node_n[2 * n], ny = d.node_n[2 * n + 1], dn = Db[0] * nx + Db[1] * ny;
+        Db[0] -= dn * nx;
+        Db[1] -= dn * ny;
+      }
+      p0 = d.v2e_ptr[n];
+      p1 = d.v2e_ptr[n + 1];
+      tk0 = d.nt[n];
+      tk1 = d.ntn[n];
     }
-    adj::NodeElem<M> el[kMaxVal];
-    const long long tk0 = d.nt[n], tk1 = d.ntn[n];
-    for (int k = 0; k < nv; ++k) {
-      const int j = d.v2e[p0 + k], lk = d.v2e_loc[p0 + k];
-      el[k].rho = d.Q[4 * (size_t)j];
-      for (int c = 0; c < 6; ++c) el[k].X[c] = d.X[6 * (size_t)j + c];
+    // displacement of each Voronoi element's vertex over [tau0, tau1]
+    auto disp = [&](int j, int k, double* D) {
+      D[0] = D[1] = 0.0;
       const long long dtj = d.dt[j];
-      el[k].dts = 0.0;
-      el[k].tau0 = el[k].tau1 = 0.0;
-      for (int c = 0; c < 2; ++c)
-        for (int p = 0; p < Nt; ++p) el[k].vd[c][p] = d.vdisp[(((size_t)j * 3 + lk) * 2 + c) * Nt + p];
+      if (dtj <= 0) return;
+      const double idtj = 1.0 / (double)dtj;
+      const double tau0 = (double)(tk0 - d.t[j]) * idtj, tau1 = (double)(tk1 - d.t[j]) * idtj;
+      const double* vd = d.vdisp + ((size_t)j * 3 + k) * 2 * Nt;
+      const double dts = (double)dtj * d.etick[j];
+      for (int c = 0; c < 2; ++c) {
+        double a0 = vd[c * Nt + Nt - 1], a1 = a0;
+        for (int pp = Nt - 2; pp >= 0; --pp) {
+          a0 = a0 * tau0 + vd[c * Nt + pp];
+          a1 = a1 * tau1 + vd[c * Nt + pp];
+        }
+        D[c] = dts * (a1 * tau1 - a0 * tau0);
+      }
+    };
+    double num0 = 0.0, num1 = 0.0, den = 0.0;
+    if (live)
+      for (int p = p0 + lane; p < p1; p += GS) {
+        const int j = d.v2e[p];
+        const double mu = d.Q[4 * (size_t)j] * adj::tri_area(d.X + 6 * (size_t)j);
+        double D[2];
+        disp(j, d.v2e_loc[p], D);
+        num0 += mu * D[0];
+        num1 += mu * D[1];
+        den += mu;
+      }
+#pragma unroll
+    for (int off = GS / 2; off > 0; off >>= 1) {
+      num0 += __shfl_xor_sync(0xffffffffu, num0, off, GS);
+      num1 += __shfl_xor_sync(0xffffffffu, num1, off, GS);
+      den += __shfl_xor_sync(0xffffffffu, den, off, GS);
+    }
+    if (!live || ty == 2) continue;
+    const double iden = 1.0 / den, D0 = num0 * iden, D1 = num1 * iden;
+    const double n0b = Db[0] * iden, n1b = Db[1] * iden, denb = -(Db[0] * D0 + Db[1] * D1) * iden;
+    for (int p = p0 + lane; p < p1; p += GS) {
+      const int j = d.v2e[p], k = d.v2e_loc[p];
+      const double* X = d.X + 6 * (size_t)j;
+      const double rho = d.Q[4 * (size_t)j], area = adj::tri_area(X), mu = rho * area;
+      double D[2];
+      disp(j, k, D);
+      const double mub = n0b * D[0] + n1b * D[1] + denb;
+      atomicAdd(&a.Qb[4 * (size_t)j], mub * area);
+      double Xb[6] = {0, 0, 0, 0, 0, 0};
+      adj::tri_area_rev(X, mub * rho, Xb);
+      for (int c = 0; c < 6; ++c) atomicAdd(&a.Xb[6 * (size_t)j + c], Xb[c]);
+      const long long dtj = d.dt[j];
       if (dtj > 0) {
+        // D = dts (sum_p vd[p] tau1^(p+1) - sum_p vd[p] tau0^(p+1)); element j's
+        // vertex k is this node only, so its slot has one writer
         const double idtj = 1.0 / (double)dtj;
-        el[k].tau0 = (double)(tk0 - d.t[j]) * idtj;
-        el[k].tau1 = (double)(tk1 - d.t[j]) * idtj;
-        el[k].dts = (double)dtj * d.etick[j];
+        const double tau0 = (double)(tk0 - d.t[j]) * idtj, tau1 = (double)(tk1 - d.t[j]) * idtj;
+        const double dts = (double)dtj * d.etick[j];
+        double* vdb = a.vdb + ((size_t)j * 3 + k) * 2 * Nt;
+        double pw1 = tau1, pw0 = tau0;
+        for (int pp = 0; pp < Nt; ++pp) {
+          vdb[pp] += n0b * mu * dts * (pw1 - pw0);
+          vdb[Nt + pp] += n1b * mu * dts * (pw1 - pw0);
+          pw1 *= tau1;
+          pw0 *= tau0;
+        }
       }
     }
-    double rhob[kMaxVal], Xb[kMaxVal][6], vdb[kMaxVal][2][Nt];
-    for (int k = 0; k < nv; ++k) {
-      rhob[k] = 0.0;
-      for (int c = 0; c < 6; ++c) Xb[k][c] = 0.0;
-      for (int c = 0; c < 2; ++c)
-        for (int p = 0; p < Nt; ++p) vdb[k][c][p] = 0.0;
-    }
-    adj::node_rev<M>(nv, el, d.node_type[n], d.node_n + 2 * (size_t)n, Db, rhob, Xb, vdb);
-    for (int k = 0; k < nv; ++k) {
-      const int j = d.v2e[p0 + k], lk = d.v2e_loc[p0 + k];
-      atomicAdd(&a.Qb[4 * (size_t)j], rhob[k]);
-      for (int c = 0; c < 6; ++c) atomicAdd(&a.Xb[6 * (size_t)j + c], Xb[k][c]);
-      // element j's vertex lk is this node only: its slot has one writer
-      for (int c = 0; c < 2; ++c)
-        for (int p = 0; p < Nt; ++p) a.vdb[(((size_t)j * 3 + lk) * 2 + c) * Nt + p] += vdb[k][c][p];
-    }
+  }
+}
+
+// one launch copying several 8-byte arrays (the state arrays of a snapshot)
+struct CopyList {
+  const unsigned long long* src[16];
+  unsigned long long* dst[16];
+  long long n[16];
+  int count;
+};
+
+__global__ void k_multi_copy(CopyList cl) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < cl.count; ++k) {
+    const unsigned long long* __restrict__ s = cl.src[k];
+    unsigned long long* __restrict__ dd = cl.dst[k];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cl.n[k]; i += stride) dd[i] = s[i];
   }
 }
 
@@ -408,7 +488,7 @@ void phase_a_impl(const Tab& T, const Dev& live, const Dev& post, const Adj& a, 
   k_adj_commit<<<nsm * 2, 128, 0, s>>>(live, a);
   k_adj_update<<<nsm * 2, 128, 0, s>>>(live, post, a);
   k_adj_edges<M><<<nsm * 8, 128, 0, s>>>(T, live, a);
-  k_adj_nodes<M><<<nsm * 4, 64, 0, s>>>(T, live, a);
+  k_adj_nodes_grp<<<nsm * 8, 128, 0, s>>>(T, live, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -720,6 +800,18 @@ void launch_adj_phase_a(const Tab& T, const Dev& live, const Dev& post, const Ad
 
 void launch_adj_reset(const Dev& d, const Counters* saved, cudaStream_t s) {
   k_adj_reset<<<1, 32, 0, s>>>(d.cnt, saved);
+}
+
+void launch_multi_copy(const void* const* src, void* const* dst, const long long* n8, int count, int nsm,
+                       cudaStream_t s) {
+  CopyList cl{};
+  cl.count = count;
+  for (int k = 0; k < count; ++k) {
+    cl.src[k] = (const unsigned long long*)src[k];
+    cl.dst[k] = (unsigned long long*)dst[k];
+    cl.n[k] = n8[k];
+  }
+  k_multi_copy<<<nsm * 4, 256, 0, s>>>(cl);
 }
 
 void launch_adj_grad(const Dev& d, const Adj& a, double* gxy, int nsm, cudaStream_t s) {

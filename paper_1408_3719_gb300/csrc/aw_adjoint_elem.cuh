@@ -223,6 +223,7 @@ struct ReconRev {
   double chb[kNSten][S::NU][4], cb[kNSten][S::NU][4];
   double lam[kNSten][S::NU][4];
   double nsym[kNSten][S::NU][S::NU];  // -(lam c^T + c lam^T): adjoint of the symmetric normal matrix
+  double rowb[S::MaxU + 1][S::NU + 4];  // adjoint of every member row
 };
 
 template <int M>
@@ -585,33 +586,30 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
     sc.nsym[s][k][bb] = acc;
   }
   tm.sync();
-  // each member row: its adjoint from every stencil that holds it, then the
-  // reverse of the row (basis averages over the virtual member, Qv - Q)
+  // adjoint of every member row: the contributions of each stencil entry,
+  // one item per (stencil, entry, row component), summed in shared memory
+  for (int k = tm.rank; k < (in.nU + 1) * (NU + 4); k += tm.size) (&sc.rowb[0][0])[k] = 0.0;
+  tm.sync();
+  for (int it = tm.rank; it < kNSten * (NE - 1) * (NU + 4); it += tm.size) {
+    const int s = it / ((NE - 1) * (NU + 4)), m = 1 + (it / (NU + 4)) % (NE - 1), k = it % (NU + 4);
+    if (!in.ok[s]) continue;
+    const int ri = in.st[s][m];
+    const double* r = tp.rows[ri];
+    double acc = 0.0;
+    if (k < NU) {
+      for (int bb = 0; bb < NU; ++bb) acc += sc.nsym[s][k][bb] * r[bb];
+      for (int v = 0; v < 4; ++v) acc += sc.lam[s][k][v] * r[NU + v];
+    } else {
+      for (int a = 0; a < NU; ++a) acc += sc.lam[s][a][k - NU] * r[a];
+    }
+    tm.add(&sc.rowb[ri][k], acc);
+  }
+  tm.sync();
+  // reverse of each row: basis averages over the virtual member, Qv - Q
   const double* X = in.X;
   const double* J = tp.J;
   for (int u = tm.rank; u < in.nU; u += tm.size) {
-    const int ri = u + 1;
-    const double* r = tp.rows[ri];
-    double rb[NU + 4];
-    for (int k = 0; k < NU + 4; ++k) rb[k] = 0.0;
-    for (int s = 0; s < kNSten; ++s) {
-      if (!in.ok[s]) continue;
-      for (int m = 1; m < NE; ++m) {
-        if (in.st[s][m] != ri) continue;
-        const double(*lam)[4] = sc.lam[s];
-        for (int k = 0; k < NU; ++k) {
-          double acc = 0.0;
-          for (int bb = 0; bb < NU; ++bb) acc += sc.nsym[s][k][bb] * r[bb];
-          for (int v = 0; v < 4; ++v) acc += lam[k][v] * r[NU + v];
-          rb[k] += acc;
-        }
-        for (int v = 0; v < 4; ++v) {
-          double acc = 0.0;
-          for (int a = 0; a < NU; ++a) acc += lam[a][v] * r[a];
-          rb[NU + v] += acc;
-        }
-      }
-    }
+    const double* rb = sc.rowb[u + 1];
     for (int v = 0; v < 4; ++v) {
       Qvb[u][v] += rb[NU + v];
       pQ[v] -= rb[NU + v];
@@ -707,42 +705,30 @@ struct PredRev {
   // node-local adjoints of the derivative sums at each node: Q_xi, Q_eta,
   // f_xi, f_eta, g_xi, g_eta (4 each), x_xi, x_eta, y_xi, y_eta, x_tau, y_tau
   double dq[S::Nst][6][4], dx[S::Nst][6];
+  double part[S::Nst][4][6];  // per variable: adjoints of xi_t, eta_t, xi_x, eta_x, xi_y, eta_y
+  double fgq[S::Nst][3][4];   // per variable: gathered adjoints of q, f, g at a node
+  double geo[S::Nst][13];     // metric terms of every node (xx xe yx ye xt yt idet xix xiy etx ety xit ett)
 };
 
-// Euler fluxes and mesh velocity of one node (one reciprocal of rho)
-AW_HD inline void node_fluxes(const Tab& T, const double* q, double* f, double* g, double* V) {
-  const double gm1 = T.gamma - 1.0;
-  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
-  const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
-  f[0] = q[1]; f[1] = q[1] * u + p; f[2] = q[1] * v; f[3] = u * (q[3] + p);
-  g[0] = q[2]; g[1] = q[2] * u; g[2] = q[2] * v + p; g[3] = v * (q[3] + p);
-  if (V) {
-    V[0] = T.eulerian ? 0.0 : u;
-    V[1] = T.eulerian ? 0.0 : v;
-  }
-}
-
-// the derivative sums and metric terms of node (t, s) of an iterate
-struct NodeGeo {
-  double Qx[4], Qe[4], fx[4], fe[4], gx[4], ge[4];
+// the metric terms of node (t, s) and the derivative sums of one variable v
+struct NodeGeoV {
+  double Qx, Qe, fx, fe, gx, ge;
   double xx, xe, yx, ye, xt, yt, idet, xix, xiy, etx, ety, xit, ett;
 };
 
 template <int M>
-AW_HD inline void node_geo(const Tab& T, const double (*q)[4], const double (*x)[2], const double (*F)[4],
-                           const double (*G)[4], int t, int s, double idt, bool stat, NodeGeo& n) {
+AW_HD inline void node_geo_v(const Tab& T, const double (*q)[4], const double (*x)[2], const double (*F)[4],
+                             const double (*G)[4], int t, int s, int v, double idt, bool stat, NodeGeoV& n) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt;
-  for (int v = 0; v < 4; ++v) n.Qx[v] = n.Qe[v] = n.fx[v] = n.fe[v] = n.gx[v] = n.ge[v] = 0.0;
+  n.Qx = n.Qe = n.fx = n.fe = n.gx = n.ge = 0.0;
   n.xx = n.xe = n.yx = n.ye = 0.0;
   for (int r = 0; r < Mc; ++r) {
     const double a = T.Dxi[s][r], b = T.Deta[s][r];
     const int lr = t * Mc + r;
-    for (int v = 0; v < 4; ++v) {
-      n.Qx[v] += a * q[lr][v]; n.Qe[v] += b * q[lr][v];
-      n.fx[v] += a * F[lr][v]; n.fe[v] += b * F[lr][v];
-      n.gx[v] += a * G[lr][v]; n.ge[v] += b * G[lr][v];
-    }
+    n.Qx += a * q[lr][v]; n.Qe += b * q[lr][v];
+    n.fx += a * F[lr][v]; n.fe += b * F[lr][v];
+    n.gx += a * G[lr][v]; n.ge += b * G[lr][v];
     n.xx += a * x[lr][0]; n.xe += b * x[lr][0];
     n.yx += a * x[lr][1]; n.ye += b * x[lr][1];
   }
@@ -759,6 +745,19 @@ AW_HD inline void node_geo(const Tab& T, const double (*q)[4], const double (*x)
   n.xix = n.ye * n.idet; n.xiy = -n.xe * n.idet; n.etx = -n.yx * n.idet; n.ety = n.xx * n.idet;
   n.xit = -(n.xix * n.xt + n.xiy * n.yt);
   n.ett = -(n.etx * n.xt + n.ety * n.yt);
+}
+
+// Euler fluxes and mesh velocity of one node (one reciprocal of rho)
+AW_HD inline void node_fluxes(const Tab& T, const double* q, double* f, double* g, double* V) {
+  const double gm1 = T.gamma - 1.0;
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+  const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  f[0] = q[1]; f[1] = q[1] * u + p; f[2] = q[1] * v; f[3] = u * (q[3] + p);
+  g[0] = q[2]; g[1] = q[2] * u; g[2] = q[2] * v + p; g[3] = v * (q[3] + p);
+  if (V) {
+    V[0] = T.eulerian ? 0.0 : u;
+    V[1] = T.eulerian ? 0.0 : v;
+  }
 }
 
 template <int M, class Tm>
@@ -783,13 +782,12 @@ AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X
       if (l < nsl * Mc) node_fluxes(T, wk.q[l], wk.F[l], wk.G[l], wk.V[l]);
     }
     tm.sync();
-    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
-      NodeGeo n;
-      node_geo<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, idt, it == 0, n);
-      for (int v = 0; v < 4; ++v) {
-        const double fs = -(n.fx[v] * n.xix + n.fe[v] * n.etx + n.gx[v] * n.xiy + n.ge[v] * n.ety);
-        wk.P[l][v] = fs - (n.Qx[v] * n.xit + n.Qe[v] * n.ett);
-      }
+    for (int it4 = tm.rank; it4 < nsl * Mc * 4; it4 += tm.size) {
+      const int l = it4 / 4, v = it4 % 4;
+      NodeGeoV n;
+      node_geo_v<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, v, idt, it == 0, n);
+      const double fs = -(n.fx * n.xix + n.fe * n.etx + n.gx * n.xiy + n.ge * n.ety);
+      wk.P[l][v] = fs - (n.Qx * n.xit + n.Qe * n.ett);
     }
     tm.sync();
     for (int l = Mc + tm.rank; l < Nst; l += tm.size) {
@@ -870,22 +868,25 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
                     double (*wb)[4], double* Xb, PredRev<M>& wk, const Tm& tm) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
-  // tables: the adjoint of every node of the final predictor
+  // tables: the adjoint of every node of the final predictor (per variable,
+  // then the vertex velocities per node)
+  for (int it4 = tm.rank; it4 < Nst * 4; it4 += tm.size) {
+    const int l = it4 / 4, v = it4 % 4, tt = l / Mc, r = l % Mc;
+    double acc = 0.0;
+    for (int e = 0; e < 3; ++e)
+      for (int g = 0; g < Nt; ++g) {
+        double valb = 0.0;
+        for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.tr[e][g][p][v];
+        acc += T.Tr[e][g][r] * valb;
+      }
+    double valb = 0.0;
+    for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.av[p][v];
+    acc += T.wavg[r] * valb;
+    wk.qb[l][v] = acc;
+  }
+  tm.sync();
   for (int l = tm.rank; l < Nst; l += tm.size) {
     const int tt = l / Mc, r = l % Mc;
-    for (int v = 0; v < 4; ++v) {
-      double acc = 0.0;
-      for (int e = 0; e < 3; ++e)
-        for (int g = 0; g < Nt; ++g) {
-          double valb = 0.0;
-          for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.tr[e][g][p][v];
-          acc += T.Tr[e][g][r] * valb;
-        }
-      double valb = 0.0;
-      for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.av[p][v];
-      acc += T.wavg[r] * valb;
-      wk.qb[l][v] = acc;
-    }
     if (!T.eulerian)
       for (int k = 0; k < 3; ++k) {
         if (T.vnode[k] != r) continue;
@@ -939,18 +940,35 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
       if (l < nsl * Mc) node_fluxes(T, tp.q[it][l], wk.F[l], wk.G[l], nullptr);
     }
     tm.sync();
-    // node-local reverse of P at every node that computed one
+    // node-local reverse of P at every node that computed one: per variable,
+    // then the metric terms of the node
+    for (int it4 = tm.rank; it4 < nsl * Mc * 4; it4 += tm.size) {
+      const int l = it4 / 4, v = it4 % 4;
+      NodeGeoV n;
+      node_geo_v<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, v, idt, stat, n);
+      if (v == 0) {
+        double* g = wk.geo[l];
+        g[0] = n.xx; g[1] = n.xe; g[2] = n.yx; g[3] = n.ye; g[4] = n.xt; g[5] = n.yt; g[6] = n.idet;
+        g[7] = n.xix; g[8] = n.xiy; g[9] = n.etx; g[10] = n.ety; g[11] = n.xit; g[12] = n.ett;
+      }
+      const double Pb = wk.Pb[l][v];
+      wk.dq[l][0][v] = -Pb * n.xit; wk.dq[l][1][v] = -Pb * n.ett;
+      wk.dq[l][2][v] = -Pb * n.xix; wk.dq[l][3][v] = -Pb * n.etx;
+      wk.dq[l][4][v] = -Pb * n.xiy; wk.dq[l][5][v] = -Pb * n.ety;
+      double* pt = wk.part[l][v];
+      pt[0] = -Pb * n.Qx; pt[1] = -Pb * n.Qe;
+      pt[2] = -Pb * n.fx; pt[3] = -Pb * n.fe; pt[4] = -Pb * n.gx; pt[5] = -Pb * n.ge;
+    }
+    tm.sync();
     for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
-      NodeGeo n;
-      node_geo<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, idt, stat, n);
-      const double* Pb = wk.Pb[l];
-      double xixb = 0, xiyb = 0, etxb = 0, etyb = 0, xitb = 0, ettb = 0;
+      NodeGeoV n;
+      const double* g = wk.geo[l];
+      n.xx = g[0]; n.xe = g[1]; n.yx = g[2]; n.ye = g[3]; n.xt = g[4]; n.yt = g[5]; n.idet = g[6];
+      n.xix = g[7]; n.xiy = g[8]; n.etx = g[9]; n.ety = g[10]; n.xit = g[11]; n.ett = g[12];
+      double xitb = 0, ettb = 0, xixb = 0, etxb = 0, xiyb = 0, etyb = 0;
       for (int v = 0; v < 4; ++v) {
-        wk.dq[l][0][v] = -Pb[v] * n.xit; wk.dq[l][1][v] = -Pb[v] * n.ett;
-        xitb -= Pb[v] * n.Qx[v]; ettb -= Pb[v] * n.Qe[v];
-        wk.dq[l][2][v] = -Pb[v] * n.xix; wk.dq[l][3][v] = -Pb[v] * n.etx;
-        wk.dq[l][4][v] = -Pb[v] * n.xiy; wk.dq[l][5][v] = -Pb[v] * n.ety;
-        xixb -= Pb[v] * n.fx[v]; etxb -= Pb[v] * n.fe[v]; xiyb -= Pb[v] * n.gx[v]; etyb -= Pb[v] * n.ge[v];
+        const double* pt = wk.part[l][v];
+        xitb += pt[0]; ettb += pt[1]; xixb += pt[2]; etxb += pt[3]; xiyb += pt[4]; etyb += pt[5];
       }
       double xtb = 0, ytb = 0;
       xixb -= xitb * n.xt; xiyb -= xitb * n.yt; xtb -= xitb * n.xix; ytb -= xitb * n.xiy;
@@ -967,18 +985,30 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
       wk.dx[l][5] = stat ? 0.0 : ytb;
     }
     tm.sync();
-    // gather onto every node of the iterate
-    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
+    // gather onto every node of the iterate: per variable, then per node
+    for (int it4 = tm.rank; it4 < nsl * Mc * 4; it4 += tm.size) {
+      const int l = it4 / 4, v = it4 % 4;
       const int t = l / Mc, r = l % Mc;
-      double qa[4] = {0, 0, 0, 0}, fb[4] = {0, 0, 0, 0}, gb[4] = {0, 0, 0, 0}, x0 = 0.0, x1 = 0.0;
+      double qa = 0.0, fb = 0.0, gb = 0.0;
       for (int s = 0; s < Mc; ++s) {
         const double a = T.Dxi[s][r], b = T.Deta[s][r];
         const int ls = t * Mc + s;
-        for (int v = 0; v < 4; ++v) {
-          qa[v] += a * wk.dq[ls][0][v] + b * wk.dq[ls][1][v];
-          fb[v] += a * wk.dq[ls][2][v] + b * wk.dq[ls][3][v];
-          gb[v] += a * wk.dq[ls][4][v] + b * wk.dq[ls][5][v];
-        }
+        qa += a * wk.dq[ls][0][v] + b * wk.dq[ls][1][v];
+        fb += a * wk.dq[ls][2][v] + b * wk.dq[ls][3][v];
+        gb += a * wk.dq[ls][4][v] + b * wk.dq[ls][5][v];
+      }
+      wk.fgq[l][0][v] = qa;
+      wk.fgq[l][1][v] = fb;
+      wk.fgq[l][2][v] = gb;
+    }
+    tm.sync();
+    for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
+      const int t = l / Mc, r = l % Mc;
+      double qa[4], x0 = 0.0, x1 = 0.0;
+      for (int v = 0; v < 4; ++v) qa[v] = wk.fgq[l][0][v];
+      for (int s = 0; s < Mc; ++s) {
+        const double a = T.Dxi[s][r], b = T.Deta[s][r];
+        const int ls = t * Mc + s;
         x0 += a * wk.dx[ls][0] + b * wk.dx[ls][1];
         x1 += a * wk.dx[ls][2] + b * wk.dx[ls][3];
       }
@@ -988,7 +1018,7 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
           x1 += idt * T.Dtau[tt][t] * wk.dx[tt * Mc + r][5];
         }
       const double* q = tp.q[it][l];
-      euler_fg_rev(T.gamma - 1.0, q, fb, gb, qa);
+      euler_fg_rev(T.gamma - 1.0, q, wk.fgq[l][1], wk.fgq[l][2], qa);
       if (!T.eulerian) {
         const double ir = 1.0 / q[0];
         qa[1] += wk.Vb[l][0] * ir;

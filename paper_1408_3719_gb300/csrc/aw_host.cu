@@ -749,10 +749,18 @@ int snap_copy(aw_ctx* c, const aw_ctx::Snap& s, bool save) {
       {d.avgc, s.avgc, ne * Nt * 4 * sizeof(double)}, {d.vdisp, s.vdisp, ne * 6 * Nt * sizeof(double)},
       {d.nX, s.nX, 2 * nn * sizeof(double)}, {d.t, s.t, ne * sizeof(long long)}, {d.dt, s.dt, ne * sizeof(long long)},
       {d.count, s.count, ne * sizeof(long long)}, {d.nt, s.nt, nn * sizeof(long long)}};
+  const void* src[13];
+  void* dst[13];
+  long long n8[13];
+  int k = 0;
   for (auto& a : arr) {
-    if (save) CK(cudaMemcpyAsync(a.snap, a.live, a.bytes, cudaMemcpyDeviceToDevice, c->stream));
-    else CK(cudaMemcpyAsync(a.live, a.snap, a.bytes, cudaMemcpyDeviceToDevice, c->stream));
+    src[k] = save ? a.live : a.snap;
+    dst[k] = save ? a.snap : a.live;
+    n8[k] = (long long)(a.bytes / 8);
+    ++k;
   }
+  launch_multi_copy(src, dst, n8, k, c->nsm, c->stream);
+  CK(cudaGetLastError());
   if (save) {
     CK(cudaMemcpyAsync(s.cnt, d.cnt, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
   } else {

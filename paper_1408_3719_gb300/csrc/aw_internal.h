@@ -161,6 +161,9 @@ void launch_adj_phase_a(const Tab& tab, const Dev& live, const Dev& post, const 
 // device copy of the counters) != 0 the other fields are copied from it
 void launch_adj_reset(const Dev& d, const Counters* saved, cudaStream_t s);
 void launch_adj_grad(const Dev& d, const Adj& a, double* gxy, int nsm, cudaStream_t s);
+// copies count arrays of n8[k] 8-byte words from src[k] to dst[k] in one launch (count <= 16)
+void launch_multi_copy(const void* const* src, void* const* dst, const long long* n8, int count, int nsm,
+                       cudaStream_t s);
 // host-side check of every element-level reverse against central
 // differences of its forward; report[0..3]: recon, predictor, edge, node
 int adjoint_selftest(const Tab& tab, unsigned long long seed, double* report);
