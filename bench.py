@@ -202,6 +202,9 @@ def run_ours(args, rank, world):
     s.load_state(Q)
     sizes = s.sizes()
     peak_gflops = aleweno.fp64_peak_gflops()
+    # tile shapes picked by the library's autotuner on this state (it times
+    # the same sweeps for every shape and restores the state)
+    tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
     for _ in range(args.warmup):
         s.sweep()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
@@ -294,6 +297,8 @@ def run_ours(args, rank, world):
                 "clocks": clk,
                 "kernels": {k: {"ms": v, "share": v / share_tot} for k, v in kms.items()},
                 "kernels_note": f"CUDA-event times over a second pass of {ksweeps} sweeps ({prof_updates} updates)",
+                "tiles": tiles,
+                "autotune_ms": {f"recon_half={k[0]},pred_wide={k[1]},bpsm={k[2]}": v for k, v in tune_ms.items()},
                 "fp64_peak_gflops": peak_gflops}
         print(json.dumps(line), flush=True)
     s.close()
@@ -340,6 +345,7 @@ def run_batched(args):
     b.load_batch(meshes, t_ends)
     t_pre = time.perf_counter() - t0
     b.load_state(np.concatenate(qs))
+    tiles, tune_ms = b.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (b.get_tiles(), {})
     for _ in range(args.warmup):
         b.enqueue(1)
     ub, msb = timed([b], args.steps)
@@ -363,8 +369,11 @@ def run_batched(args):
                                    f"P{args.order} LTS, one sweep over the batch per step",
                        "n_tris": n_tris, "instances": len(inst), "preprocessing_s": t_pre,
                        "l2": "256 MiB write between timed sweeps"},
+            "tiles": tiles, "autotune_ms": {f"recon_half={k[0]},pred_wide={k[1]},bpsm={k[2]}": v
+                                             for k, v in tune_ms.items()},
             "per_instance_loop": {"value": vl, "unit": UNIT, "ms_per_step": msl / args.steps,
-                                  "note": "same instances, one context per instance, one sweep of each per step"},
+                                  "note": "same instances, one context per instance (default tiles), one sweep "
+                                          "of each per step"},
             "batched_over_loop": vb / vl}
     print(json.dumps(line), flush=True)
 
@@ -468,6 +477,7 @@ def main():
     ap.add_argument("--e2e-sweeps", type=int, default=200)
     ap.add_argument("--workload", default="explosion", choices=["explosion", "batched", "adjoint"])
     ap.add_argument("--vortex-n", type=int, default=158)
+    ap.add_argument("--tune-sweeps", type=int, default=10)
     ap.add_argument("--adj-sweeps", type=int, default=50)
     ap.add_argument("--ckpt", type=int, default=10)
     ap.add_argument("--instances", type=int, default=256)

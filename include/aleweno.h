@@ -216,6 +216,25 @@ int aw_adjoint_forward(aw_ctx* ctx, int64_t n_sweeps, int64_t ckpt_every);
 int aw_adjoint(aw_ctx* ctx, const double* dJdQ, const double* dJdX, const double* dJdxy,
                double* dJdQ0, double* dJdxy0);
 
+/* Tile shapes of the sweep kernels; they change no result, only speed.
+ * tiles[0] = 1 halves the reconstruction's elements per block (16/8/4 for
+ * P1/P2/P3 by default), tiles[1] = 1 runs the predictor on 256-thread blocks
+ * (default 128), tiles[2] = blocks per SM of the kernels that loop over a
+ * sweep's lists (default 8, range 1..64).  Setting them re-captures the sweep
+ * graph.  No counterpart in the paper. */
+int aw_set_tiles(aw_ctx* ctx, const int32_t* tiles);
+int aw_get_tiles(aw_ctx* ctx, int32_t* tiles);
+
+/* Autotuner of the tile shapes on the loaded state: each of 12 candidates
+ * (tiles[0] in {0,1} x tiles[1] in {0,1} x tiles[2] in {4,8,16}; candidate k
+ * = tiles[0]*6 + tiles[1]*3 + index of tiles[2]) runs the same n_sweeps
+ * sweeps from the current state, timed with CUDA events on the context's
+ * stream; ms[k] (NULL to skip) receives each time and best[3] the fastest
+ * shape, which the context keeps.  The state is restored afterwards.  Needs
+ * one extra copy of the state in device memory.  No counterpart in the
+ * paper. */
+int aw_autotune(aw_ctx* ctx, int64_t n_sweeps, double* ms, int32_t* best);
+
 /* Host-only check of the adjoint's element-level pieces (no GPU needed): for
  * order M and a seed, each reverse (reconstruction, predictor, edge flux,
  * node solver) is compared with central differences of its forward on

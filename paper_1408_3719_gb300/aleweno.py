@@ -26,7 +26,8 @@ EXPORTED = ["aw_create", "aw_destroy", "aw_last_error", "aw_load_mesh", "aw_load
             "aw_get_update_counts", "aw_get_elem_arrays", "aw_set_elem_arrays", "aw_get_node_arrays",
             "aw_set_node_arrays", "aw_diagnostics", "aw_sizes", "aw_profile_enable", "aw_profile_read",
             "aw_kernel_name", "aw_ready_set_noalloc", "aw_measure_fp64_peak", "aw_load_state_xy", "aw_schedule",
-            "aw_get_schedule", "aw_adjoint_forward", "aw_adjoint", "aw_adjoint_selftest"]
+            "aw_get_schedule", "aw_adjoint_forward", "aw_adjoint", "aw_adjoint_selftest", "aw_set_tiles",
+            "aw_get_tiles", "aw_autotune"]
 
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +90,9 @@ def load(path: str | None = None):
             lib.aw_adjoint_forward.argtypes = [P, i64, i64]
             lib.aw_adjoint.argtypes = [P, P, P, P, P, P]
             lib.aw_adjoint_selftest.argtypes = [C.c_int, C.c_uint64, P]
+            lib.aw_set_tiles.argtypes = [P, P]
+            lib.aw_get_tiles.argtypes = [P, P]
+            lib.aw_autotune.argtypes = [P, i64, P, P]
             _lib = lib
     return _lib
 
@@ -227,6 +231,24 @@ class Solver:
         self._check(self.lib.aw_adjoint(self.h, _ptr(_f64(dJdQ)), _ptr(_f64(dJdX)), _ptr(_f64(dJdxy)), _ptr(gQ),
                                         _ptr(gxy)))
         return gQ, gxy
+
+    def set_tiles(self, recon_half=0, pred_wide=0, bpsm=8):
+        t = np.array([recon_half, pred_wide, bpsm], np.int32)
+        self._check(self.lib.aw_set_tiles(self.h, _ptr(t)))
+
+    def get_tiles(self):
+        t = np.zeros(3, np.int32)
+        self._check(self.lib.aw_get_tiles(self.h, _ptr(t)))
+        return dict(recon_half=int(t[0]), pred_wide=int(t[1]), bpsm=int(t[2]))
+
+    def autotune(self, n_sweeps=20):
+        """Time the 12 tile shapes on the loaded state, keep the fastest;
+        returns (chosen tiles, {(recon_half, pred_wide, bpsm): ms})."""
+        ms = np.zeros(12)
+        best = np.zeros(3, np.int32)
+        self._check(self.lib.aw_autotune(self.h, n_sweeps, _ptr(ms), _ptr(best)))
+        table = {(k // 6, (k // 3) % 2, (4, 8, 16)[k % 3]): float(ms[k]) for k in range(12)}
+        return dict(recon_half=int(best[0]), pred_wide=int(best[1]), bpsm=int(best[2])), table
 
     def sweep(self):
         n = C.c_int64(0)

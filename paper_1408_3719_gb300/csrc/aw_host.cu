@@ -35,6 +35,7 @@ struct aw_ctx {
   double* d_corner0 = nullptr;  // element corners at t = 0
   std::vector<double> etick_h, ntick_h;  // seconds per tick of each element / node
   cudaGraphExec_t graph_exec = nullptr;  // one captured sweep
+  Tiles tiles;                           // tile shapes of the sweep kernels
   std::vector<int> tri_h;                // host copies for aw_load_state_xy
   std::vector<double> cshift_h;
   bool fresh = false;                    // a state was loaded and no sweep has run since
@@ -715,7 +716,7 @@ int adj_alloc(aw_ctx* c, void** p, size_t bytes) {
   return AW_OK;
 }
 
-int snap_alloc(aw_ctx* c, aw_ctx::Snap* s) {
+int snap_alloc(aw_ctx* c, aw_ctx::Snap* s, std::vector<void*>* owner = nullptr) {
   const size_t ne = c->ne, nn = c->nn, Nt = c->tab.Nt;
   const size_t nd[9] = {4 * ne, 4 * ne, 4 * ne, 6 * ne, ne * c->tab.Nst * 4, ne * 3 * Nt * Nt * 4, ne * Nt * 4,
                         ne * 6 * Nt, 2 * nn};
@@ -726,8 +727,13 @@ int snap_alloc(aw_ctx* c, aw_ctx::Snap* s) {
   for (size_t k : nl) bytes += pad(k * sizeof(long long));
   bytes += pad(sizeof(Counters));
   void* base = nullptr;
-  int rc = adj_alloc(c, &base, bytes);
-  if (rc) return rc;
+  int rc;
+  if (owner) {
+    if (cudaMalloc(&base, bytes) != cudaSuccess) return set_err(c, AW_ERR_CUDA, "cudaMalloc of %zu bytes failed", bytes);
+    owner->push_back(base);
+  } else if ((rc = adj_alloc(c, &base, bytes))) {
+    return rc;
+  }
   char* p = (char*)base;
   double** dp[9] = {&s->Q, &s->QM, &s->HM, &s->X, &s->qhat, &s->trace, &s->avgc, &s->vdisp, &s->nX};
   for (int k = 0; k < 9; ++k) { *dp[k] = (double*)p; p += pad(nd[k] * sizeof(double)); }
@@ -997,7 +1003,7 @@ static int load_state_impl(aw_ctx* c, const double* Q, const double* xy) {
     CK(cudaStreamSynchronize(c->stream));
   }
 
-  launch_initial(c->tab, d, c->nsm, c->stream);
+  launch_initial(c->tab, d, c->nsm, c->stream, c->tiles);
   CK(cudaGetLastError());
   int rc = sync_counters(c);
   if (rc) return rc;
@@ -1025,7 +1031,7 @@ static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   if (!c->prof && !c->graph_exec) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    launch_sweep(c->tab, c->d, c->nsm, c->stream, nullptr);
+    launch_sweep(c->tab, c->d, c->nsm, c->stream, nullptr, c->tiles);
     CK(cudaStreamEndCapture(c->stream, &g));
     CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
     cudaGraphDestroy(g);
@@ -1035,7 +1041,7 @@ static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
       std::vector<cudaEvent_t> evs(kNumKernels + 1);
       for (auto& e : evs) CK(cudaEventCreate(&e));
       c->prof_pending.push_back(evs);
-      launch_sweep(c->tab, c->d, c->nsm, c->stream, c->prof_pending.back().data());
+      launch_sweep(c->tab, c->d, c->nsm, c->stream, c->prof_pending.back().data(), c->tiles);
     } else {
       CK(cudaGraphLaunch(c->graph_exec, c->stream));
     }
@@ -1399,6 +1405,100 @@ int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* 
   if (gQ0) CK(cudaMemcpy(gQ0, a.Qb, 4 * ne * sizeof(double), cudaMemcpyDefault));
   if (gxy0) CK(cudaMemcpy(gxy0, c->d_gxy, 2 * nn * sizeof(double), cudaMemcpyDefault));
   return AW_OK;
+}
+
+int aw_set_tiles(aw_ctx* c, const int32_t* tiles) {
+  if (!c || !tiles) return AW_ERR_INVALID_ARG;
+  if (tiles[0] < 0 || tiles[0] > 1 || tiles[1] < 0 || tiles[1] > 1 || tiles[2] < 1 || tiles[2] > 64)
+    return set_err(c, AW_ERR_INVALID_ARG, "tiles: recon_half and pred_wide are 0 or 1, blocks per SM in [1, 64]");
+  CK(cudaStreamSynchronize(c->stream));
+  c->tiles.recon_half = tiles[0];
+  c->tiles.pred_wide = tiles[1];
+  c->tiles.bpsm = tiles[2];
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  return AW_OK;
+}
+
+int aw_get_tiles(aw_ctx* c, int32_t* tiles) {
+  if (!c || !tiles) return AW_ERR_INVALID_ARG;
+  tiles[0] = c->tiles.recon_half;
+  tiles[1] = c->tiles.pred_wide;
+  tiles[2] = c->tiles.bpsm;
+  return AW_OK;
+}
+
+int aw_autotune(aw_ctx* c, int64_t n_sweeps, double* ms, int32_t* best) {
+  if (!c || n_sweeps < 1) return AW_ERR_INVALID_ARG;
+  if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<void*> owned;
+  aw_ctx::Snap keep{};
+  int rc = snap_alloc(c, &keep, &owned);
+  auto done = [&](int code) {
+    cudaStreamSynchronize(c->stream);
+    for (void* p : owned) cudaFree(p);
+    return code;
+  };
+  if (rc) return done(rc);
+  const bool fresh = c->fresh;
+  const bool prof = c->prof;
+  c->prof = false;
+  if ((rc = snap_copy(c, keep, true))) return done(rc);
+  const Tiles start = c->tiles;
+  Tiles best_t = start;
+  double best_ms = 1e300;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  static const int kBpsm[3] = {4, 8, 16};
+  for (int k = 0; k < 12; ++k) {  // candidate k: recon_half = k / 6, pred_wide = (k / 3) % 2, bpsm = kBpsm[k % 3]
+    c->tiles.recon_half = k / 6;
+    c->tiles.pred_wide = (k / 3) % 2;
+    c->tiles.bpsm = kBpsm[k % 3];
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    // the first sweep captures this shape's graph; every candidate then times
+    // the same sweeps from the same state
+    if ((rc = snap_copy(c, keep, false)) || (rc = do_sweeps(c, 1, nullptr, false))) break;
+    if ((rc = snap_copy(c, keep, false))) break;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = AW_ERR_CUDA; break; }
+    if ((rc = do_sweeps(c, n_sweeps, nullptr, false))) break;
+    float t = 0.0f;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      rc = set_err(c, AW_ERR_CUDA, "autotune: event timing failed");
+      break;
+    }
+    if (ms) ms[k] = t;
+    if (t < best_ms) {
+      best_ms = t;
+      best_t = c->tiles;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tiles = rc ? start : best_t;
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  int rc2 = snap_copy(c, keep, false);
+  c->prof = prof;
+  c->fresh = fresh;
+  if (rc || rc2) return done(rc ? rc : rc2);
+  if ((rc = sync_counters(c))) return done(rc);
+  if ((rc = check_device_error(c))) return done(rc);
+  if (best) {
+    best[0] = c->tiles.recon_half;
+    best[1] = c->tiles.pred_wide;
+    best[2] = c->tiles.bpsm;
+  }
+  return done(AW_OK);
 }
 
 int aw_adjoint_selftest(int order_M, uint64_t seed, double* report) {

@@ -142,11 +142,21 @@ struct Counters {
   long long updates_since_sync;
 };
 
+// Tile shapes of a sweep's kernels (they change no arithmetic): recon_half
+// halves the reconstruction's elements per block, pred_wide runs the
+// predictor on 256-thread blocks instead of 128, bpsm = blocks per SM of the
+// persistent kernels that loop over the sweep's lists.
+struct Tiles {
+  int recon_half = 0;
+  int pred_wide = 0;
+  int bpsm = 8;
+};
+
 // kernel launchers (aw_kernels.cu)
 constexpr int kNumKernels = 8;  // launches per sweep
 const char* kernel_name(int k);
-void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev);
-void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl);
+void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, const Tiles& tl);
 void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 double measure_fp64_peak();
 // k_ready, k_nodes, k_edges of one sweep: ready/moved/active/touched lists

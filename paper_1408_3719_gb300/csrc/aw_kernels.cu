@@ -547,16 +547,16 @@ __global__ void k_products(Tab T, Dev d) {
 // Cooperative predictor: one thread per (element, space-time node), G
 // elements per 128-thread block, the element's nodal arrays in shared memory.
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int TH = 128>
 struct PredShape {
   static constexpr int Mc = (M + 1) * (M + 2) / 2, Nt = M + 1, Nst = Mc * Nt;
-  static constexpr int kThreads = 128;
+  static constexpr int kThreads = TH;
   static constexpr int G = kThreads / Nst;
 };
 
-template <int M>
-__global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial, int gts) {
-  using S = PredShape<M>;
+template <int M, int TH>
+__global__ void __launch_bounds__(TH) k_predict_coop(Tab T, Dev d, int initial, int gts) {
+  using S = PredShape<M, TH>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst, G = S::G;
   __shared__ double sq[G][Nst][4], sf[G][Nst][4], sg[G][Nst][4], sP[G][Nst][4];
   __shared__ double sx[G][Nst][2], sV[G][Nst][2];
@@ -789,10 +789,13 @@ __global__ void __launch_bounds__(128) k_predict_coop(Tab T, Dev d, int initial,
 // equation entries, stencils, characteristic fields, output nodes).
 // ---------------------------------------------------------------------------
 template <int M>
+constexpr int recon_g_default() { return M == 1 ? 16 : (M == 2 ? 8 : 4); }
+
+template <int M, int GG = recon_g_default<M>()>
 struct ReconShape {
   static constexpr int Mc = (M + 1) * (M + 2) / 2, NU = Mc - 1, NE = 2 * Mc;
   static constexpr int MaxU = kNSten * (NE - 1);
-  static constexpr int G = M == 1 ? 16 : (M == 2 ? 8 : 4);
+  static constexpr int G = GG;
   static constexpr int kThreads = 256;
   static constexpr int NL = NU * (NU + 1) / 2;      // lower triangle of the normal matrix
   static constexpr int NN = NL + 4 * NU;           // + right-hand sides
@@ -813,9 +816,9 @@ struct ReconShape {
   static constexpr size_t bytes = nDbl * 8 + nInt * 4 + (size_t)G * kNSten * NE;
 };
 
-template <int M>
+template <int M, int GG>
 __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial) {
-  using S = ReconShape<M>;
+  using S = ReconShape<M, GG>;
   constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE, MaxU = S::MaxU, G = S::G, NL = S::NL, NN = S::NN, RW = S::RW;
   extern __shared__ double smem[];
   double* sRow = smem + S::oRow;
@@ -1185,34 +1188,47 @@ __global__ void k_fill_counters_initial(Dev d) {
 }
 
 // The reconstruction and predictor grids cover every element (the pre-
-// processing phase) or a few blocks per SM that loop over the ready list.
-template <int M>
-void launch_recon(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial) {
-  using S = ReconShape<M>;
+// processing phase) or bpsm blocks per SM that loop over the ready list.
+template <int M, int GG>
+void launch_recon_g(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial, int bpsm) {
+  using S = ReconShape<M, GG>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_recon_coop<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaFuncSetAttribute(k_recon_coop<M, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     attr = true;
   }
   const int need = (d.ne + S::G - 1) / S::G;
-  const int grid = initial ? need : std::min(need, nsm * 8);
-  k_recon_coop<M><<<grid, S::kThreads, S::bytes, s>>>(T, d, initial);
+  const int grid = initial ? need : std::min(need, nsm * bpsm);
+  k_recon_coop<M, GG><<<grid, S::kThreads, S::bytes, s>>>(T, d, initial);
 }
 
 template <int M>
-void launch_predict(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial) {
-  using S = PredShape<M>;
+void launch_recon(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial, const Tiles& tl) {
+  constexpr int G0 = recon_g_default<M>();
+  if (tl.recon_half) launch_recon_g<M, G0 / 2>(T, d, nsm, s, initial, tl.bpsm);
+  else launch_recon_g<M, G0>(T, d, nsm, s, initial, tl.bpsm);
+}
+
+template <int M, int TH>
+void launch_predict_t(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial, int bpsm) {
+  using S = PredShape<M, TH>;
   const int need = (d.ne + S::G - 1) / S::G;
-  const int grid = initial ? need : std::min(need, nsm * 8);
-  k_predict_coop<M><<<grid, S::kThreads, 0, s>>>(T, d, initial, T.gts);
+  const int grid = initial ? need : std::min(need, nsm * bpsm);
+  k_predict_coop<M, TH><<<grid, S::kThreads, 0, s>>>(T, d, initial, T.gts);
+}
+
+template <int M>
+void launch_predict(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial, const Tiles& tl) {
+  if (tl.pred_wide) launch_predict_t<M, 256>(T, d, nsm, s, initial, tl.bpsm);
+  else launch_predict_t<M, 128>(T, d, nsm, s, initial, tl.bpsm);
 }
 
 // ev (optional): kNumKernels + 1 events recorded on s around the launches,
 // for per-kernel CUDA-event timing on the launching stream.
 template <int M>
-void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev) {
+void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl) {
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
-  const int grid_w = nsm * 8;
+  const int grid_w = nsm * tl.bpsm;
   int k = 0;
   auto mark = [&]() { if (ev) cudaEventRecord(ev[k++], s); };
   mark(); k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
@@ -1220,17 +1236,17 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
   mark(); k_flux_grp<M><<<grid_w * 4, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
-  mark(); launch_recon<M>(T, d, nsm, s, 0);
-  mark(); launch_predict<M>(T, d, nsm, s, 0);
+  mark(); launch_recon<M>(T, d, nsm, s, 0, tl);
+  mark(); launch_predict<M>(T, d, nsm, s, 0, tl);
   mark(); k_finish<<<grid_w, kBlock, 0, s>>>(T, d);
   mark();
 }
 
 template <int M>
-void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, const Tiles& tl) {
   k_fill_counters_initial<<<1, 32, 0, s>>>(d);
-  launch_recon<M>(T, d, nsm, s, 1);
-  launch_predict<M>(T, d, nsm, s, 1);
+  launch_recon<M>(T, d, nsm, s, 1, tl);
+  launch_predict<M>(T, d, nsm, s, 1, tl);
 }
 
 template <int M>
@@ -1264,19 +1280,19 @@ const char* kernel_name(int k) {
   return (k >= 0 && k < kNumKernels) ? names[k] : nullptr;
 }
 
-void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev) {
+void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl) {
   switch (T.M) {
-    case 1: sweep_impl<1>(T, d, nsm, s, ev); break;
-    case 2: sweep_impl<2>(T, d, nsm, s, ev); break;
-    default: sweep_impl<3>(T, d, nsm, s, ev); break;
+    case 1: sweep_impl<1>(T, d, nsm, s, ev, tl); break;
+    case 2: sweep_impl<2>(T, d, nsm, s, ev, tl); break;
+    default: sweep_impl<3>(T, d, nsm, s, ev, tl); break;
   }
 }
 
-void launch_initial(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
+void launch_initial(const Tab& T, const Dev& d, int nsm, cudaStream_t s, const Tiles& tl) {
   switch (T.M) {
-    case 1: initial_impl<1>(T, d, nsm, s); break;
-    case 2: initial_impl<2>(T, d, nsm, s); break;
-    default: initial_impl<3>(T, d, nsm, s); break;
+    case 1: initial_impl<1>(T, d, nsm, s, tl); break;
+    case 2: initial_impl<2>(T, d, nsm, s, tl); break;
+    default: initial_impl<3>(T, d, nsm, s, tl); break;
   }
 }
 
