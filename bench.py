@@ -204,7 +204,11 @@ def run_ours(args, rank, world):
     peak_gflops = aleweno.fp64_peak_gflops()
     # tile shapes picked by the library's autotuner on this state (it times
     # the same sweeps for every shape and restores the state)
-    tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
+    if args.tiles:
+        s.set_tiles(*[int(v) for v in args.tiles.split(",")])
+        tiles, tune_ms = s.get_tiles(), {}
+    else:
+        tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
     for _ in range(args.warmup):
         s.sweep()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
@@ -345,7 +349,11 @@ def run_batched(args):
     b.load_batch(meshes, t_ends)
     t_pre = time.perf_counter() - t0
     b.load_state(np.concatenate(qs))
-    tiles, tune_ms = b.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (b.get_tiles(), {})
+    if args.tiles:
+        b.set_tiles(*[int(v) for v in args.tiles.split(",")])
+        tiles, tune_ms = b.get_tiles(), {}
+    else:
+        tiles, tune_ms = b.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (b.get_tiles(), {})
     for _ in range(args.warmup):
         b.enqueue(1)
     ub, msb = timed([b], args.steps)
@@ -478,6 +486,8 @@ def main():
     ap.add_argument("--workload", default="explosion", choices=["explosion", "batched", "adjoint"])
     ap.add_argument("--vortex-n", type=int, default=158)
     ap.add_argument("--tune-sweeps", type=int, default=10)
+    ap.add_argument("--tiles", default=None,
+                    help="recon_half,pred_wide,bpsm: fixed tile shapes instead of the autotuner")
     ap.add_argument("--adj-sweeps", type=int, default=50)
     ap.add_argument("--ckpt", type=int, default=10)
     ap.add_argument("--instances", type=int, default=256)
