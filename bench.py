@@ -485,7 +485,7 @@ def main():
     ap.add_argument("--e2e-sweeps", type=int, default=200)
     ap.add_argument("--workload", default="explosion", choices=["explosion", "batched", "adjoint"])
     ap.add_argument("--vortex-n", type=int, default=158)
-    ap.add_argument("--tune-sweeps", type=int, default=10)
+    ap.add_argument("--tune-sweeps", type=int, default=20)
     ap.add_argument("--tiles", default=None,
                     help="recon_half,pred_wide,bpsm: fixed tile shapes instead of the autotuner")
     ap.add_argument("--adj-sweeps", type=int, default=50)

@@ -148,7 +148,8 @@ int aw_diagnostics(aw_ctx* ctx, double* out);
 int aw_sizes(aw_ctx* ctx, int64_t* out);
 
 /* Per-kernel timing of sweeps with CUDA events recorded on the context's
- * stream between the launches.  aw_profile_enable(ctx, 1) resets and starts
+ * stream between the launches (a second captured graph with an event record
+ * between the kernels; each profiled sweep waits for its last event).  aw_profile_enable(ctx, 1) resets and starts
  * it; aw_profile_read fills ms[k] (total milliseconds of kernel k over the
  * profiled sweeps, k < the return value) and *sweeps, and returns the number
  * of kernels per sweep; aw_kernel_name(k) names kernel k (NULL if out of
@@ -228,9 +229,9 @@ int aw_get_tiles(aw_ctx* ctx, int32_t* tiles);
 /* Autotuner of the tile shapes on the loaded state: each of 12 candidates
  * (tiles[0] in {0,1} x tiles[1] in {0,1} x tiles[2] in {4,8,16}; candidate k
  * = tiles[0]*6 + tiles[1]*3 + index of tiles[2]) runs the same n_sweeps
- * sweeps from the current state, timed with CUDA events on the context's
- * stream; ms[k] (NULL to skip) receives each time and best[3] the fastest
- * shape, which the context keeps.  The state is restored afterwards.  Needs
+ * sweeps from the current state twice, timed with CUDA events on the
+ * context's stream; ms[k] (NULL to skip) receives the faster of the two
+ * times and best[3] the fastest shape, which the context keeps.  The state is restored afterwards.  Needs
  * one extra copy of the state in device memory.  No counterpart in the
  * paper. */
 int aw_autotune(aw_ctx* ctx, int64_t n_sweeps, double* ms, int32_t* best);

@@ -1068,29 +1068,35 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
       sSig[(e * kNSten + s) * 4 + r] = sg;
     }
     __syncthreads();
-    // P6: nonlinear weights and the weighted characteristic coefficients
-    for (int item = tid; item < G * 4; item += nth) {
-      const int e = item / 4, r = item % 4;
+    // P6: nonlinear weights (one item per element, stencil and field; the
+    // weight overwrites its sigma), then the weighted characteristic
+    // coefficients (one item per element, coefficient and field)
+    for (int item = tid; item < G * kNSten * 4; item += nth) {
+      const int e = item / (kNSten * 4), s = (item / 4) % kNSten;
       if (!sVal[e]) continue;
-      double om[kNSten], tot = 0.0;
-#pragma unroll
-      for (int s = 0; s < kNSten; ++s) {
-        om[s] = 0.0;
-        if (!sOk[e * kNSten + s]) continue;
-        const double e1 = sSig[(e * kNSten + s) * 4 + r] + 1e-14;
+      double om = 0.0;
+      if (sOk[e * kNSten + s]) {
+        const double e1 = sSig[item] + 1e-14;
         const double e2 = e1 * e1, e4 = e2 * e2, e8 = e4 * e4;
-        om[s] = (s == 0 ? 1e5 : 1.0) / e8;
-        tot += om[s];
+        om = (s == 0 ? 1e5 : 1.0) / e8;
       }
+      sSig[item] = om;
+    }
+    __syncthreads();
+    for (int item = tid; item < G * NU * 4; item += nth) {
+      const int e = item / (NU * 4), l = (item / 4) % NU, r = item % 4;
+      if (!sVal[e]) continue;
+      const double* om = sSig + (size_t)e * kNSten * 4 + r;
+      double tot = 0.0;
+#pragma unroll
+      for (int s = 0; s < kNSten; ++s)
+        if (sOk[e * kNSten + s]) tot += om[4 * s];
       const double itot = 1.0 / tot;
+      double acc = 0.0;
 #pragma unroll
-      for (int l = 0; l < NU; ++l) {
-        double acc = 0.0;
-#pragma unroll
-        for (int s = 0; s < kNSten; ++s)
-          if (sOk[e * kNSten + s]) acc += (om[s] * itot) * sCh[((size_t)(e * kNSten + s) * NU + l) * 4 + r];
-        sWc[(e * NU + l) * 4 + r] = acc;
-      }
+      for (int s = 0; s < kNSten; ++s)
+        if (sOk[e * kNSten + s]) acc += (om[4 * s] * itot) * sCh[((size_t)(e * kNSten + s) * NU + l) * 4 + r];
+      sWc[(e * NU + l) * 4 + r] = acc;
     }
     __syncthreads();
     // P7: back to conserved variables
@@ -1150,27 +1156,42 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
     __syncthreads();
     // P9: positivity scaling of w_h at the lattice nodes (density first, then
     // pressure through its chord bound; the scaling of Zhang and Shu), then
-    // the nodal values go to the predictor
-    if (tid < G && sVal[tid]) {
-      const int e = tid;
-      const double* Qi = sEl + e * 16 + 6;
-      double* w = sW0 + (size_t)e * Mc * 4;
-      const double rho_min = 1e-8 * Qi[0], p_i = pressure(T, Qi), p_min = 1e-8 * p_i;
-      for (int pass = 0; pass < 2; ++pass) {
-        double theta = 1.0;
-        for (int s = 0; s < Mc; ++s) {
-          const double* ws = w + 4 * s;
-          if (pass == 0 && ws[0] < rho_min) theta = fmin(theta, (Qi[0] - rho_min) / (Qi[0] - ws[0]));
-          if (pass == 1) {
-            const double ps = pressure(T, ws);
-            if (ps < p_min) theta = fmin(theta, (p_i - p_min) / (p_i - ps));
-          }
+    // the nodal values go to the predictor.  Per pass: one candidate theta per
+    // node, the element's minimum, the scaling.
+    for (int pass = 0; pass < 2; ++pass) {
+      double* cand = sSig;  // [G][Mc], free after P6
+      for (int item = tid; item < G * Mc; item += nth) {
+        const int e = item / Mc;
+        if (!sVal[e]) continue;
+        const double* Qi = sEl + e * 16 + 6;
+        const double* ws = sW0 + (size_t)item * 4;
+        double th = 1.0;
+        if (pass == 0) {
+          const double rho_min = 1e-8 * Qi[0];
+          if (ws[0] < rho_min) th = (Qi[0] - rho_min) / (Qi[0] - ws[0]);
+        } else {
+          const double p_i = pressure(T, Qi), p_min = 1e-8 * p_i, ps = pressure(T, ws);
+          if (ps < p_min) th = (p_i - p_min) / (p_i - ps);
         }
-        if (theta < 1.0)
-          for (int k = 0; k < Mc * 4; ++k) w[k] = Qi[k % 4] + theta * (w[k] - Qi[k % 4]);
+        cand[item] = th;
       }
+      __syncthreads();
+      for (int e = tid; e < G; e += nth) {
+        double theta = 1.0;
+        if (sVal[e])
+          for (int k = 0; k < Mc; ++k) theta = fmin(theta, cand[e * Mc + k]);
+        sDt[e * 4] = theta;  // free after P8
+      }
+      __syncthreads();
+      for (int item = tid; item < G * Mc * 4; item += nth) {
+        const int e = item / (Mc * 4);
+        const double theta = sDt[e * 4];
+        if (!sVal[e] || !(theta < 1.0)) continue;
+        const double qi = sEl[e * 16 + 6 + item % 4];
+        sW0[item] = qi + theta * (sW0[item] - qi);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int item = tid; item < G * Mc * 4; item += nth) {
       const int e = item / (Mc * 4);
       if (!sVal[e]) continue;
@@ -1230,7 +1251,9 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
   const int grid_w = nsm * tl.bpsm;
   int k = 0;
-  auto mark = [&]() { if (ev) cudaEventRecord(ev[k++], s); };
+  // external record nodes when captured into a graph (a plain record would only
+  // order the capture)
+  auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[k++], s, cudaEventRecordExternal); };
   mark(); k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
   mark(); k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
   mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
