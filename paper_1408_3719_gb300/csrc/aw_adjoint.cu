@@ -71,6 +71,34 @@ __global__ void __launch_bounds__(kElemThreads, 4) k_adj_elem(Tab T, Dev post, D
   const int n = initial ? post.ne : live.cnt->n_ready;
   for (int pos = blockIdx.x; pos < n; pos += gridDim.x) {
     const int i = initial ? pos : live.ready_list[pos];
+    // adjoints of the element's new tables (overwritten by this sweep, so
+    // their adjoint restarts from zero before phase A).  Where they are all
+    // zero the element's reverse contributes exact zeros: skip it.
+    int nz = 0;
+    {
+      double* tr = a.trb + (size_t)i * 3 * Nt * Nt * 4;
+      double* av = a.avb + (size_t)i * Nt * 4;
+      double* vd = a.vdb + (size_t)i * 6 * Nt;
+      for (int k = lane; k < 3 * Nt * Nt * 4; k += NT) {
+        const double v = tr[k];
+        (&W.tb.tr[0][0][0][0])[k] = v;
+        nz |= v != 0.0;
+        tr[k] = 0.0;
+      }
+      for (int k = lane; k < Nt * 4; k += NT) {
+        const double v = av[k];
+        (&W.tb.av[0][0])[k] = v;
+        nz |= v != 0.0;
+        av[k] = 0.0;
+      }
+      for (int k = lane; k < 6 * Nt; k += NT) {
+        const double v = vd[k];
+        (&W.tb.vd[0][0])[k] = v;
+        nz |= v != 0.0;
+        vd[k] = 0.0;
+      }
+    }
+    if (!tm.any(nz)) continue;
     const long long ti = post.t[i];
     const int u0 = post.u_ptr[i], nU = post.u_ptr[i + 1] - u0;
     const double dts = (double)post.dt[i] * post.etick[i];
@@ -136,17 +164,6 @@ __global__ void __launch_bounds__(kElemThreads, 4) k_adj_elem(Tab T, Dev post, D
       tm.sync();
       continue;
     }
-    // adjoints of the element's new tables (overwritten by this sweep, so
-    // their adjoint restarts from zero before phase A)
-    {
-      double* tr = a.trb + (size_t)i * 3 * Nt * Nt * 4;
-      double* av = a.avb + (size_t)i * Nt * 4;
-      double* vd = a.vdb + (size_t)i * 6 * Nt;
-      for (int k = lane; k < 3 * Nt * Nt * 4; k += NT) { (&W.tb.tr[0][0][0][0])[k] = tr[k]; tr[k] = 0.0; }
-      for (int k = lane; k < Nt * 4; k += NT) { (&W.tb.av[0][0])[k] = av[k]; av[k] = 0.0; }
-      for (int k = lane; k < 6 * Nt; k += NT) { (&W.tb.vd[0][0])[k] = vd[k]; vd[k] = 0.0; }
-    }
-    tm.sync();
     adj::pred_rev<M>(T, nit, dts, W.pt, W.tb, W.wb, W.Xb, W.sc.pr, tm);
     adj::recon_rev<M>(T, W.in, W.rt, W.wb, W.Xb, W.Qb, W.Xvb, W.Qvb, W.sc.rr, tm);
     for (int u = lane; u < nU; u += NT) {
@@ -228,29 +245,33 @@ __global__ void k_adj_update(Dev live, Dev post, Adj a) {
   }
 }
 
-// One lane per Gauss point: GS lanes (a power of two >= (M+1)^2) per active
-// edge; the corner adjoints are summed over the points by a xor-shuffle tree,
-// the trace adjoints (slots of this edge only) by atomics.
+// One lane per Gauss point: (M+1)^2 consecutive lanes per active edge,
+// 32 / (M+1)^2 edges per warp; the corner adjoints are summed over the points
+// by a shuffle tree within the edge's lanes, the trace adjoints of one Gauss
+// row onto the row's first lane.
 template <int M>
 __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
-  constexpr int Nt = M + 1, NP = Nt * Nt, GS = NP <= 4 ? 4 : 16;
+  constexpr int Nt = M + 1, NP = Nt * Nt, EPW = 32 / NP;
   const int epoch = d.cnt->epoch;
-  const int n_items = d.cnt->n_active * GS;
+  const int n_active = d.cnt->n_active;
+  const int n_items = (n_active + EPW - 1) / EPW * 32;
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
     const int item = base + threadIdx.x;
-    const int q = item / GS, pt = item % GS;
+    const int lane = item & 31, slot = lane / NP, pt = lane % NP;
+    const int q = (item >> 5) * EPW + slot;
+    const bool valid = item < n_items && slot < EPW && q < n_active;
     double Pb[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
     int na = 0, nb_ = 0, gxl = -1, Ll = 0, lel = 0, Rl = -1, lrl = 0;
     bool ma = false, mb = false;
-    if (item < n_items) {
+    if (valid) {
       const int ed = d.active_list[q];
       na = d.edge_nodes[2 * ed];
       nb_ = d.edge_nodes[2 * ed + 1];
       ma = d.node_moved[na] == epoch;
       mb = d.node_moved[nb_] == epoch;
-      if (pt < NP) {
+      {
         const int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
         const int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
         const int le1 = le == 2 ? 0 : le + 1;
@@ -282,7 +303,9 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
         for (int v = 0; v < 4; ++v) Gb[v] = -a.gb[4 * (size_t)L + v] + (R >= 0 ? a.gb[4 * (size_t)R + v] : 0.0);
         for (int p = 0; p < Nt; ++p)
           for (int v = 0; v < 4; ++v) trLb[gx][p][v] = trRb[Nt - 1 - gx][p][v] = 0.0;
-        adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
+        // a zero flux adjoint contributes exact zeros
+        if (Gb[0] != 0.0 || Gb[1] != 0.0 || Gb[2] != 0.0 || Gb[3] != 0.0)
+          adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
         gxl = gx;
         Ll = L; lel = le; Rl = R; lrl = lr;
       }
@@ -306,12 +329,17 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
       }
     }
 #pragma unroll
-    for (int off = GS / 2; off > 0; off >>= 1)
+    for (int off = 1; off < NP; off <<= 1) {
+      const bool in = pt + off < NP;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) Pb[k][c] += __shfl_xor_sync(0xffffffffu, Pb[k][c], off, GS);
-    if (item < n_items && pt == 0)
+        for (int c = 0; c < 2; ++c) {
+          const double o = __shfl_down_sync(0xffffffffu, Pb[k][c], off);
+          if (in) Pb[k][c] += o;
+        }
+    }
+    if (valid && pt == 0)
       for (int c = 0; c < 2; ++c) {
         atomicAdd(&a.nXb[2 * na + c], Pb[0][c] + (ma ? 0.0 : Pb[3][c]));
         atomicAdd(&a.nXb[2 * nb_ + c], Pb[1][c] + (mb ? 0.0 : Pb[2][c]));
@@ -372,8 +400,10 @@ __global__ void k_adj_nodes_grp(Tab T, Dev d, Adj a) {
         D[c] = dts * (a1 * tau1 - a0 * tau0);
       }
     };
+    // a zero position adjoint contributes exact zeros
+    const bool work = live && ty != 2 && (Db[0] != 0.0 || Db[1] != 0.0);
     double num0 = 0.0, num1 = 0.0, den = 0.0;
-    if (live)
+    if (work)
       for (int p = p0 + lane; p < p1; p += GS) {
         const int j = d.v2e[p];
         const double mu = d.Q[4 * (size_t)j] * adj::tri_area(d.X + 6 * (size_t)j);
@@ -389,7 +419,7 @@ __global__ void k_adj_nodes_grp(Tab T, Dev d, Adj a) {
       num1 += __shfl_xor_sync(0xffffffffu, num1, off, GS);
       den += __shfl_xor_sync(0xffffffffu, den, off, GS);
     }
-    if (!live || ty == 2) continue;
+    if (!work) continue;
     const double iden = 1.0 / den, D0 = num0 * iden, D1 = num1 * iden;
     const double n0b = Db[0] * iden, n1b = Db[1] * iden, denb = -(Db[0] * D0 + Db[1] * D1) * iden;
     for (int p = p0 + lane; p < p1; p += GS) {

@@ -56,6 +56,7 @@ struct aw_ctx {
   double* d_gxy = nullptr;
   long long adj_n = 0, adj_k = 0;
   bool adj_ready = false;
+  bool last_seg_kept = false;  // slots hold the last segment's sweep-start states
 };
 
 namespace {
@@ -1332,11 +1333,20 @@ int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
   for (auto& s : c->ckpt)
     if ((rc = snap_alloc(c, &s))) return rc;
   if ((rc = snap_alloc(c, &c->fin))) return rc;
+  c->slots.resize(ckpt_every + 1);
+  for (auto& s : c->slots)
+    if ((rc = snap_alloc(c, &s))) return rc;
+  c->last_seg_kept = false;
   if ((rc = snap_copy(c, c->ckpt[0], true))) return rc;
+  // the last segment is the first one the reverse pass needs: keep its
+  // sweep-start states now instead of recomputing them
+  const int64_t last_s0 = n_sweeps > 0 ? (n_sweeps - 1) / ckpt_every * ckpt_every : 0;
   for (int64_t m = 1; m <= n_sweeps; ++m) {
     if ((rc = do_sweeps(c, 1, nullptr, false))) return rc;
     if (m % ckpt_every == 0 && (rc = snap_copy(c, c->ckpt[m / ckpt_every], true))) return rc;
+    if (m > last_s0 && (rc = snap_copy(c, c->slots[m - last_s0], true))) return rc;
   }
+  c->last_seg_kept = n_sweeps > 0;
   if ((rc = snap_copy(c, c->fin, true))) return rc;
   if ((rc = sync_counters(c))) return rc;
   if ((rc = check_device_error(c))) return rc;
@@ -1364,11 +1374,7 @@ int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* 
     if ((rc = adj_alloc(c, &p, 2 * nn * sizeof(double)))) return rc;
     c->d_gxy = (double*)p;
   }
-  if ((int64_t)c->slots.size() < c->adj_k + 1) {
-    c->slots.resize(c->adj_k + 1);
-    for (auto& s : c->slots)
-      if ((rc = snap_alloc(c, &s))) return rc;
-  }
+
   CK(cudaStreamSynchronize(c->stream));
   // seed with dJ / d(final state)
   if (dJdQ) CK(cudaMemcpyAsync(a.Qb, dJdQ, 4 * ne * sizeof(double), cudaMemcpyDefault, c->stream));
@@ -1387,12 +1393,16 @@ int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* 
   const int64_t nseg = (n + k - 1) / k;
   for (int64_t seg = nseg - 1; seg >= 0; --seg) {
     const int64_t s0 = seg * k, s1 = std::min(s0 + k, n), len = s1 - s0;
-    // recompute the segment from its checkpoint, keeping every sweep-start state
-    if ((rc = snap_copy(c, c->ckpt[seg], false))) return rc;
-    for (int64_t j = 1; j <= len; ++j) {
-      if ((rc = do_sweeps(c, 1, nullptr, false))) return rc;
-      if ((rc = snap_copy(c, c->slots[j], true))) return rc;
+    // recompute the segment from its checkpoint, keeping every sweep-start
+    // state (the last segment's are kept by the forward run)
+    if (!(seg == nseg - 1 && c->last_seg_kept)) {
+      if ((rc = snap_copy(c, c->ckpt[seg], false))) return rc;
+      for (int64_t j = 1; j <= len; ++j) {
+        if ((rc = do_sweeps(c, 1, nullptr, false))) return rc;
+        if ((rc = snap_copy(c, c->slots[j], true))) return rc;
+      }
     }
+    c->last_seg_kept = false;
     for (int64_t j = len - 1; j >= 0; --j) {
       const aw_ctx::Snap& pre = j == 0 ? c->ckpt[seg] : c->slots[j];
       if ((rc = snap_copy(c, pre, false))) return rc;

@@ -257,20 +257,24 @@ __device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const do
   for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
 }
 
-// One lane per Gauss point: GS lanes (a power of two >= (M+1)^2) per swept
-// edge, the point contributions summed by a fixed xor-shuffle tree.
+// One lane per Gauss point: (M+1)^2 consecutive lanes per swept edge,
+// 32 / (M+1)^2 edges per warp, the point contributions summed by a fixed
+// shuffle tree within each edge's lanes.
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
-  constexpr int Nt = M + 1, NP = Nt * Nt, GS = NP <= 4 ? 4 : 16;
+  constexpr int Nt = M + 1, NP = Nt * Nt, EPW = 32 / NP;
   const int epoch = d.cnt->epoch;
-  const int n_items = d.cnt->n_active * GS;
+  const int n_active = d.cnt->n_active;
+  const int n_items = (n_active + EPW - 1) / EPW * 32;
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
     const int item = base + threadIdx.x;
-    const int q = item / GS, pt = item % GS;
+    const int lane = item & 31, slot = lane / NP, pt = lane % NP;
+    const int q = (item >> 5) * EPW + slot;
+    const bool valid = item < n_items && slot < EPW && q < n_active;
     double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
     int ed = -1;
-    if (item < n_items && pt < NP) {
+    if (valid) {
       ed = d.active_list[q];
       const int gx = pt / Nt, gt = pt % Nt;
       const int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
@@ -346,13 +350,20 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       for (int c = 0; c < 3; ++c) Nn[c] = wq * n[c];
     }
 #pragma unroll
-    for (int off = GS / 2; off > 0; off >>= 1) {
+    for (int off = 1; off < NP; off <<= 1) {
+      const bool in = pt + off < NP;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) G[v] += __shfl_xor_sync(0xffffffffu, G[v], off, GS);
+      for (int v = 0; v < 4; ++v) {
+        const double o = __shfl_down_sync(0xffffffffu, G[v], off);
+        if (in) G[v] += o;
+      }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Nn[c] += __shfl_xor_sync(0xffffffffu, Nn[c], off, GS);
+      for (int c = 0; c < 3; ++c) {
+        const double o = __shfl_down_sync(0xffffffffu, Nn[c], off);
+        if (in) Nn[c] += o;
+      }
     }
-    if (pt == 0 && item < n_items) {
+    if (pt == 0 && valid) {
       ed = d.active_list[q];
       double* g = d.G + 4 * (size_t)ed;
       double* nn = d.N + 4 * (size_t)ed;
