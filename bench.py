@@ -69,6 +69,32 @@ def recon_flops(M: int, members: float) -> float:
     return members * per_member + 7 * per_stencil + weights + dt
 
 
+def hbm_bytes_per_update(M: int, sw_per_elem: float) -> float:
+    """Compulsory DRAM bytes of one element update with perfect on-chip reuse
+    in a sweep: read its state, ticks, corners and node data (~28 words) and
+    its predictor tables (4 N_st words), write the new predictor and tables
+    (4 N_st words), state and nodes (~30 words); read its stencil and total
+    stencil index lists (7 n_e + |S^W| int32)."""
+    Mc = (M + 1) * (M + 2) // 2
+    Nst = Mc * (M + 1)
+    return 8.0 * (28 + 4 * Nst + 4 * Nst + 30) + 4.0 * (7 * 2 * Mc + sw_per_elem)
+
+
+def host_info():
+    """CPU model and core count of the host running the oracle."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model, "machine": platform.machine(), "cores_available": os.cpu_count()}
+
+
 def flux_flops(M: int) -> float:
     Nt = M + 1
     per_point = 30 + 2 * 4 * 2 * (Nt - 1) + 6 + 2 * 25 + 25 + 4 * 4
@@ -173,7 +199,8 @@ def run_reference(args, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"explosion EP1 disc sample, P{args.order} LTS",
                                             "n_tris": info["n_tris"]},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -256,6 +283,18 @@ def run_ours(args, rank, world):
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured FP64 DFMA throughput (aw_measure_fp64_peak, this run)",
                 "flops_per_update": model[dom]}
+    # the HBM roofline this FP64-bound path is far from: compulsory bytes per
+    # update x update rate, against the measured copy bandwidth
+    bpu = hbm_bytes_per_update(args.order, sizes["sw_entries"] / n_tris)
+    hbm_peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    hbm = {"bytes_per_update": bpu, "achieved_GBs": value * bpu / 1e9, "peak_GBs": hbm_peak,
+           "frac": (value * bpu / 1e9 / hbm_peak) if hbm_peak else None,
+           "note": "algorithmic (compulsory) bytes; the path is bound by the FP64 pipe, see roofline"}
 
     # end to end through the C ABI with host buffers: state upload + initial
     # phase, the same number of sweeps, state download
@@ -283,7 +322,7 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and args.cpu_baseline:
         rate, info = cpu_sample(args.order, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle (serial C, FP64) on a {info['n_tris']}-triangle graded disc with the same EP1 "
                          f"data and P{args.order} LTS scheme, {info['sweeps']} sweeps from t=0 "
                          f"({info['updates']} updates, {info['seconds']:.1f} s), pre-processing untimed"}
@@ -297,7 +336,8 @@ def run_ours(args, rank, world):
                            "n_tris": n_tris, "order_M": args.order, "parallelism": f"replicas x{world}",
                            "l2": "256 MiB write between timed sweeps (L2 is 129 MB)",
                            "updates_timed": int(updates_all), "sw_entries_per_elem": sizes["sw_entries"] / n_tris},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": len(kms) * args.steps,
+                "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": len(kms) * args.steps,
                 "clocks": clk,
                 "kernels": {k: {"ms": v, "share": v / share_tot} for k, v in kms.items()},
                 "kernels_note": f"CUDA-event times over a second pass of {ksweeps} sweeps ({prof_updates} updates)",
@@ -310,17 +350,38 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def shard_instances(sizes, world):
+    """Independent instances over ranks, largest first to the least-loaded
+    rank (deterministic); returns the instance indices of every rank."""
+    parts = [[] for _ in range(world)]
+    load = [0] * world
+    for k in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        parts[r].append(k)
+        load[r] += sizes[k]
+    return [sorted(p) for p in parts]
+
+
+def run_batched(args, rank=0, world=1):
     """Config 4: many independent explosion / shock-tube instances advanced by
     one sweep over the batch, against a loop that runs the same instances one
-    context at a time on the same GPU."""
+    context at a time on the same GPU.  With N ranks the instances are
+    sharded (no collective on the data path: each rank advances its own
+    batch; only the timings are reduced)."""
     import torch
     from paper_1408_3719_gb300 import aleweno
     from paper_1408_3719_gb300 import workloads as W
 
-    torch.cuda.set_device(0)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     aleweno.load()
-    inst = W.batched_instances(args.instances, lo=args.min_tris, hi=args.max_tris)
+    inst_all = W.batched_instances(args.instances, lo=args.min_tris, hi=args.max_tris)
+    part = shard_instances([int(d["mesh"]["tri"].shape[0]) for d in inst_all], world)[rank]
+    inst = [inst_all[k] for k in part]
     meshes, qs, t_ends = [d["mesh"] for d in inst], [d["q"] for d in inst], [d["t_end"] for d in inst]
     n_tris = sum(int(m["tri"].shape[0]) for m in meshes)
     stream = torch.cuda.Stream()
@@ -369,13 +430,21 @@ def run_batched(args):
     ul, msl = timed(loop, args.steps)
     for s in loop:
         s.close()
+    msb, ub = aggregate(msb, ub, dist, "cuda")
+    msl, ul = aggregate(msl, ul, dist, "cuda")
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    n_tris = sum(int(d["mesh"]["tri"].shape[0]) for d in inst_all)
     vb, vl = ub / (msb * 1e-3), ul / (msl * 1e-3)
-    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": msb / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched: {len(inst)} explosion/shock-tube instances, {n_tris} triangles, "
+    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": msb / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched: {len(inst_all)} explosion/shock-tube instances, {n_tris} triangles, "
                                    f"P{args.order} LTS, one sweep over the batch per step",
-                       "n_tris": n_tris, "instances": len(inst), "preprocessing_s": t_pre,
+                       "n_tris": n_tris, "instances": len(inst_all), "preprocessing_s": t_pre,
+                       "parallelism": f"instances sharded over {world} rank(s), largest first",
                        "l2": "256 MiB write between timed sweeps"},
             "tiles": tiles, "autotune_ms": {f"recon_half={k[0]},pred_wide={k[1]},bpsm={k[2]}": v
                                              for k, v in tune_ms.items()},
@@ -513,8 +582,7 @@ def main():
     if args.workload == "batched":
         if args.order == 3 and "--order" not in sys.argv:
             args.order = 2
-        if rank == 0:
-            run_batched(args)
+        run_batched(args, rank, world)
         return
     if args.impl == "reference":
         run_reference(args, rank)

@@ -4,6 +4,8 @@ element updates."""
 import os
 import socket
 
+import numpy as np
+
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -40,3 +42,16 @@ def test_aggregate_over_two_gloo_ranks():
 def test_aggregate_single_process():
     import bench
     assert bench.aggregate(3.0, 7) == (3.0, 7.0)
+
+
+def test_batched_instances_are_sharded_once_and_balanced():
+    import bench
+    rng = np.random.default_rng(3)
+    sizes = [int(x) for x in np.exp(rng.uniform(np.log(2000), np.log(60000), 256))]
+    for world in (1, 2, 3, 8):
+        parts = bench.shard_instances(sizes, world)
+        assert sorted(k for p in parts for k in p) == list(range(len(sizes)))
+        loads = [sum(sizes[k] for k in p) for p in parts]
+        # largest-first greedy: no rank exceeds the mean by more than one instance
+        assert max(loads) <= sum(sizes) / world + max(sizes)
+        assert parts == bench.shard_instances(sizes, world)  # deterministic
