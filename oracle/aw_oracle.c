@@ -47,6 +47,13 @@
  *     characteristic field of dF/dQ.n at Q_i, n the direction of the density
  *     gradient of the central-stencil polynomial; the least-squares fits
  *     themselves are linear and use the conserved variables (eq. intConsRec).
+ *  R11 positivity safeguards: scaling of w_h at the lattice nodes (density,
+ *     then pressure), predictor fallback to w_h (not in the paper).
+ *  R12 schedule log: oc_schedule records each element's dt ticks per update
+ *     count and replays them, so that runs from perturbed data follow the
+ *     base run's schedule (used by the central differences of the adjoint).
+ *  R14 Osher-type flux: the path integral of |A_n^V| (eq. osher) by 3-point
+ *     Gauss-Legendre quadrature on [0, 1] along the straight path (eq. path).
  */
 #include "aw_oracle.h"
 
@@ -931,6 +938,64 @@ static void rusanov(const oc_ctx* c, const double* qm, const double* qp, const d
   }
 }
 
+/* Osher-type ALE flux (eq. osher) on the straight-line path Psi(s) = q- +
+   s (q+ - q-) (eq. path).  The path integral of |A_n^V(Psi(s))| is taken by
+   3-point Gauss-Legendre quadrature on [0, 1] (reading R14).  At each node
+   |A| = R |Lambda| R^-1: the eigenvalues of the ALE Jacobian of F.n_xy + q n_t
+   are |n_xy| (u_n - c, u_n, u_n, u_n + c) + n_t, and R holds the
+   eigenvectors of dF/dQ.n with n = n_xy / |n_xy| (x if n_xy vanishes);
+   R^-1 is the numerical inverse. */
+static void osher(const oc_ctx* c, const double* qm, const double* qp, const double* n, double* F) {
+  double fm[4], gm[4], fp[4], gp[4];
+  euler_flux(c, qm, fm, gm);
+  euler_flux(c, qp, fp, gp);
+  double nxy = sqrt(n[0] * n[0] + n[1] * n[1]);
+  double nx = 1.0, ny = 0.0;
+  if (nxy > 0.0) {
+    nx = n[0] / nxy;
+    ny = n[1] / nxy;
+  }
+  double dq[4], D[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int v = 0; v < 4; ++v) dq[v] = qp[v] - qm[v];
+  const double r15 = sqrt(15.0) / 10.0;
+  const double sp[3] = {0.5 - r15, 0.5, 0.5 + r15}, sw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  for (int gq = 0; gq < 3; ++gq) {
+    double q[4];
+    for (int v = 0; v < 4; ++v) q[v] = qm[v] + sp[gq] * dq[v];
+    double g = c->cfg.gamma, rho = q[0], u = q[1] / rho, v = q[2] / rho, p = pressure(c, q);
+    double a = sqrt(g * p / rho), H = (q[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
+    double R[16] = {1.0, 1.0, 0.0, 1.0,
+                    u - a * nx, u, -ny, u + a * nx,
+                    v - a * ny, v, nx, v + a * ny,
+                    H - a * un, 0.5 * (u * u + v * v), ut, H + a * un};
+    double Rinv[16];
+    invert(R, Rinv, 4);
+    double lam[4] = {nxy * (un - a) + n[2], nxy * un + n[2], nxy * un + n[2], nxy * (un + a) + n[2]};
+    double w[4];
+    for (int k = 0; k < 4; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < 4; ++j) acc += Rinv[4 * k + j] * dq[j];
+      w[k] = fabs(lam[k]) * acc;
+    }
+    for (int i = 0; i < 4; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < 4; ++k) acc += R[4 * i + k] * w[k];
+      D[i] += sw[gq] * acc;
+    }
+  }
+  for (int v = 0; v < 4; ++v) {
+    double Fm = fm[v] * n[0] + gm[v] * n[1] + qm[v] * n[2];
+    double Fp = fp[v] * n[0] + gp[v] * n[1] + qp[v] * n[2];
+    F[v] = 0.5 * (Fm + Fp) - 0.5 * D[v];
+  }
+}
+
+/* the numerical flux of the configuration (eq. rusanov or eq. osher) */
+static void num_flux(const oc_ctx* c, const double* qm, const double* qp, const double* n, double* F) {
+  if (c->cfg.flux == 1) osher(c, qm, qp, n, F);
+  else rusanov(c, qm, qp, n, F);
+}
+
 static void boundary_state(int bc, const double* q, const double* n, double* qb) {
   for (int v = 0; v < 4; ++v) qb[v] = q[v];
   if (bc == 0) {
@@ -1344,7 +1409,7 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
 
 int oc_create(const oc_config* cfg, oc_ctx** out) {
   if (!cfg || !out || cfg->order_M < 1 || cfg->order_M > MAXM || !(cfg->t_end > 0) || cfg->time_quantum_log2 < 1 ||
-      cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1))
+      cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->flux < 0 || cfg->flux > 1)
     return OC_INVALID;
   oc_ctx* c = (oc_ctx*)calloc(1, sizeof(oc_ctx));
   c->cfg = *cfg;
@@ -1618,7 +1683,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
           boundary_state(c->edge_bc[ed], qm, n, qp);
         }
         double F[4];
-        rusanov(c, qm, qp, n, F);
+        num_flux(c, qm, qp, n, F);
         for (int v = 0; v < 4; ++v) G[4 * ed + v] += wq * F[v];
         for (int d = 0; d < 3; ++d) N[3 * ed + d] += wq * n[d];
       }
@@ -1795,7 +1860,7 @@ int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const dou
     memcpy(qp, qR, sizeof qp);
   else
     boundary_state(bc, qL, n3, qp);
-  rusanov(c, qL, qp, n3, out);
+  num_flux(c, qL, qp, n3, out);
   return OC_OK;
 }
 

@@ -35,6 +35,7 @@ typedef struct {
   int gts;              /* 1: global time step (min of local steps) */
   int predictor_iters;  /* Picard iterations of eq. CGfinal; <=0 means M+1 */
   int mesh_velocity;    /* 0: V = v (Lagrangian-type), 1: V = 0 (Eulerian) */
+  int flux;             /* 0: Rusanov-type (eq. rusanov), 1: Osher-type (eq. osher) */
 } oc_config;
 
 int oc_create(const oc_config* cfg, oc_ctx** out);
@@ -72,6 +73,7 @@ int oc_get_stencils(const oc_ctx* c, int64_t i, int32_t* members, int32_t* sw, i
 int oc_reconstruct_eval(oc_ctx* c, int64_t i, int64_t npts, const double* xy, double* out);
 int oc_predict_debug(oc_ctx* c, const double* X6, double dt_sec, const double* w_nodal,
                      double* qhat_out);
+/* the configuration's numerical flux; qR NULL: boundary state of type bc */
 int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const double* n3,
                   int bc, double* out);
 int oc_eval_qh(const oc_ctx* c, const double* qhat, int64_t npts, const double* pts, double* out);
