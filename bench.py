@@ -158,20 +158,20 @@ def aggregate(ms: float, updates: int, dist=None, device="cpu"):
     return float(mx[0]), float(sm[1])
 
 
-def workload(order: int, hc: float):
+def workload(order: int, hc: float, flux: str = "rusanov"):
     from paper_1408_3719_gb300 import workloads as W
     mesh, Q = W.explosion(hc)
-    return mesh, Q, dict(order_M=order, t_end=0.25, time_quantum_log2=20)
+    return mesh, Q, dict(order_M=order, t_end=0.25, time_quantum_log2=20, flux=flux)
 
 
-def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = None):
+def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = None, flux: str = "rusanov"):
     """The oracle on a bounded sample: the same generator and scheme on a
     ~26k-triangle disc; setup untimed; sweeps timed until `seconds` elapse
     (or `steps` sweeps)."""
     from oracle.pyoracle import Oracle
     from paper_1408_3719_gb300 import workloads as W
     mesh, Q = W.explosion(0.005)
-    o = Oracle(order_M=order, t_end=0.25)
+    o = Oracle(order_M=order, t_end=0.25, flux=flux)
     o.load_mesh(mesh)
     o.load_state(Q)
     for _ in range(warmup):
@@ -187,17 +187,21 @@ def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = 
     return ups / el, dict(sweeps=sweeps, updates=ups, seconds=el, n_tris=int(mesh["tri"].shape[0]))
 
 
+def _flux_tag(args):
+    return "" if args.flux == "rusanov" else f", {args.flux} flux"
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    rate, info = cpu_sample(args.order, 0, warmup=args.warmup, steps=args.steps)
+    rate, info = cpu_sample(args.order, 0, warmup=args.warmup, steps=args.steps, flux=args.flux)
     sample = (f"oracle (plain serial C, FP64) on a {info['n_tris']}-triangle graded disc, same EP1 data and "
-              f"P{args.order} LTS scheme; {info['sweeps']} timed sweeps ({info['updates']} updates) after "
+              f"P{args.order} LTS scheme, {args.flux} flux; {info['sweeps']} timed sweeps ({info['updates']} updates) after "
               f"{args.warmup} warm-up sweeps; pre-processing untimed")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * info["seconds"] / info["sweeps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"explosion EP1 disc sample, P{args.order} LTS",
+            "data": "synthetic", "config": {"workload": f"explosion EP1 disc sample, P{args.order} LTS{_flux_tag(args)}",
                                             "n_tris": info["n_tris"]},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "host": host_info()},
@@ -216,7 +220,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     aleweno.load()
-    mesh, Q, cfg = workload(args.order, args.hc)
+    mesh, Q, cfg = workload(args.order, args.hc, args.flux)
     n_tris = int(mesh["tri"].shape[0])
     # a dedicated (non-default) stream: the library launches on it and the
     # CUDA events below are recorded on it
@@ -321,7 +325,7 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_baseline:
-        rate, info = cpu_sample(args.order, args.cpu_seconds)
+        rate, info = cpu_sample(args.order, args.cpu_seconds, flux=args.flux)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle (serial C, FP64) on a {info['n_tris']}-triangle graded disc with the same EP1 "
                          f"data and P{args.order} LTS scheme, {info['sweeps']} sweeps from t=0 "
@@ -332,7 +336,7 @@ def run_ours(args, rank, world):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"cylindrical explosion EP1 on a graded disc, {n_tris} triangles, "
-                                       f"P{args.order} LTS, CFL 0.5, t_end 0.25",
+                                       f"P{args.order} LTS, CFL 0.5, t_end 0.25{_flux_tag(args)}",
                            "n_tris": n_tris, "order_M": args.order, "parallelism": f"replicas x{world}",
                            "l2": "256 MiB write between timed sweeps (L2 is 129 MB)",
                            "updates_timed": int(updates_all), "sw_entries_per_elem": sizes["sw_entries"] / n_tris},
@@ -565,6 +569,8 @@ def main():
                     help="recon_half,pred_wide,bpsm: fixed tile shapes instead of the autotuner")
     ap.add_argument("--adj-sweeps", type=int, default=50)
     ap.add_argument("--ckpt", type=int, default=10)
+    ap.add_argument("--flux", default="rusanov", choices=["rusanov", "osher"],
+                    help="numerical flux of the explosion workload and its oracle sample")
     ap.add_argument("--objective", default="disc", choices=["disc", "global"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--min-tris", type=int, default=2000)

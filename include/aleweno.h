@@ -58,6 +58,8 @@ typedef struct {
   int predictor_iters;    /* Picard iterations of eq. CGfinal; <= 0 selects M+1 */
   int mesh_velocity;      /* 0: V = v, the fluid velocity (Sec. 3); 1: V = 0 (Eulerian) */
   void* cuda_stream;      /* cudaStream_t to run on, or NULL for a stream the context creates */
+  int flux;               /* 0: Rusanov-type ALE flux (eq. rusanov); 1: Osher-type ALE flux (eq. osher)
+                             on the straight path (eq. path), path integral by 3-point Gauss-Legendre */
 } aw_config;
 
 /* Create a context (Sec. 2.1 set-up).  INVALID_ARG on an unsupported config. */
@@ -211,8 +213,9 @@ int aw_get_schedule(aw_ctx* ctx, int64_t* out);
  * memory: (n_sweeps / ckpt_every + ckpt_every + 3) copies of the state.  The
  * context is left in the final state; aw_adjoint may be called again for
  * another J.  STATE if a positivity safeguard (scaling of w_h, predictor
- * fallback) acted in one of the sweeps: the map has a kink there.  No
- * counterpart in the paper. */
+ * fallback) acted in one of the sweeps: the map has a kink there.  The
+ * adjoint covers the Rusanov-type flux (flux = 0); INVALID_ARG otherwise.
+ * No counterpart in the paper. */
 int aw_adjoint_forward(aw_ctx* ctx, int64_t n_sweeps, int64_t ckpt_every);
 int aw_adjoint(aw_ctx* ctx, const double* dJdQ, const double* dJdX, const double* dJdxy,
                double* dJdQ0, double* dJdxy0);

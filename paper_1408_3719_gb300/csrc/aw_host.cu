@@ -166,6 +166,7 @@ int build_tab(aw_ctx* c) {
   T.eulerian = c->cfg.mesh_velocity == 1;
   T.gts = c->cfg.gts ? 1 : 0;
   T.nit = c->cfg.predictor_iters > 0 ? c->cfg.predictor_iters : M + 1;
+  T.flux = c->cfg.flux;
   const int Mc = T.Mc, Nt = T.Nt;
   // lattice nodes: rows of constant eta, xi fastest
   int s = 0;
@@ -792,7 +793,7 @@ int aw_create(const aw_config* cfg, aw_ctx** out) {
   *out = nullptr;
   if (cfg->order_M < 1 || cfg->order_M > kMaxM || !(cfg->t_end > 0) || cfg->time_quantum_log2 < 1 ||
       cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->mesh_velocity < 0 ||
-      cfg->mesh_velocity > 1)
+      cfg->mesh_velocity > 1 || cfg->flux < 0 || cfg->flux > 1)
     return AW_ERR_INVALID_ARG;
   aw_ctx* c = new aw_ctx();
   c->cfg = *cfg;
@@ -1319,6 +1320,7 @@ int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
   if (!c->fresh) return set_err(c, AW_ERR_STATE, "aw_adjoint_forward starts from a state just loaded");
   if (c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint is for local time stepping");
+  if (c->cfg.flux != 0) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers the Rusanov-type flux");
   CK(cudaStreamSynchronize(c->stream));
   for (void* p : c->adj_allocs) cudaFree(p);
   c->adj_allocs.clear();

@@ -24,6 +24,7 @@ struct Tab {
   int eulerian;         // mesh velocity V = 0
   int gts;              // global time step
   int nit;              // Picard iterations
+  int flux;             // 0 Rusanov-type, 1 Osher-type ALE flux
   double lat[kMaxMc][2];
   int vnode[3];
   double Dxi[kMaxMc][kMaxMc], Deta[kMaxMc][kMaxMc];

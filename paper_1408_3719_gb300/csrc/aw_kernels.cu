@@ -257,6 +257,65 @@ __device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const do
   for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
 }
 
+// Osher-type ALE flux (eq. osher) on the straight path Psi(s) = q- + s (q+ -
+// q-) (eq. path), the path integral by 3-point Gauss-Legendre quadrature:
+// at each path node |A| dq = R |Lambda| L dq with the eigenvalues
+// |n_xy| (u_n - c, u_n, u_n, u_n + c) + n_t of the ALE Jacobian and the
+// eigenvectors R, L = R^-1 of dF/dQ.n, n = n_xy / |n_xy|.
+__device__ __forceinline__ void osher(const Tab& T, const double* qm, const double* qp, const double* n,
+                                      double* F) {
+  const double g = T.gamma, gm1 = g - 1.0;
+  double rim = 1.0 / qm[0], rip = 1.0 / qp[0];
+  double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
+  double pm = gm1 * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
+  double pp = gm1 * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
+  double wm = um * n[0] + vm * n[1] + n[2], wp = up * n[0] + vp * n[1] + n[2];
+  double vnm = um * n[0] + vm * n[1], vnp = up * n[0] + vp * n[1];
+  const double nxy = sqrt(n[0] * n[0] + n[1] * n[1]);
+  double nx = 1.0, ny = 0.0;
+  if (nxy > 0.0) {
+    const double inx = 1.0 / nxy;
+    nx = n[0] * inx;
+    ny = n[1] * inx;
+  }
+  double dq[4], D[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int v = 0; v < 4; ++v) dq[v] = qp[v] - qm[v];
+  const double r15 = 0.38729833462074168852;  // sqrt(15) / 10
+#pragma unroll
+  for (int gq = 0; gq < 3; ++gq) {
+    const double s = gq == 0 ? 0.5 - r15 : (gq == 1 ? 0.5 : 0.5 + r15);
+    const double ws = gq == 1 ? 8.0 / 18.0 : 5.0 / 18.0;
+    double q[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = qm[v] + s * dq[v];
+    const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir;
+    const double p = gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+    const double a = sqrt(g * p * ir), ia = 1.0 / a, H = (q[3] + p) * ir;
+    const double un = u * nx + v * ny, ut = -u * ny + v * nx, q2 = 0.5 * (u * u + v * v);
+    const double b1 = gm1 * ia * ia, b2 = b1 * q2;
+    // characteristic amplitudes L dq, scaled by |lambda|
+    double c0 = 0.5 * (b2 + un * ia) * dq[0] - 0.5 * (b1 * u + nx * ia) * dq[1] - 0.5 * (b1 * v + ny * ia) * dq[2] +
+                0.5 * b1 * dq[3];
+    double c1 = (1.0 - b2) * dq[0] + b1 * u * dq[1] + b1 * v * dq[2] - b1 * dq[3];
+    double c2 = -ut * dq[0] - ny * dq[1] + nx * dq[2];
+    double c3 = 0.5 * (b2 - un * ia) * dq[0] - 0.5 * (b1 * u - nx * ia) * dq[1] - 0.5 * (b1 * v - ny * ia) * dq[2] +
+                0.5 * b1 * dq[3];
+    c0 *= ws * fabs(nxy * (un - a) + n[2]);
+    c1 *= ws * fabs(nxy * un + n[2]);
+    c2 *= ws * fabs(nxy * un + n[2]);
+    c3 *= ws * fabs(nxy * (un + a) + n[2]);
+    D[0] += c0 + c1 + c3;
+    D[1] += (u - a * nx) * c0 + u * c1 - ny * c2 + (u + a * nx) * c3;
+    D[2] += (v - a * ny) * c0 + v * c1 + nx * c2 + (v + a * ny) * c3;
+    D[3] += (H - a * un) * c0 + q2 * c1 + ut * c2 + (H + a * un) * c3;
+  }
+  const double Fm[4] = {qm[0] * wm, qm[1] * wm + pm * n[0], qm[2] * wm + pm * n[1], qm[3] * wm + pm * vnm};
+  const double Fp[4] = {qp[0] * wp, qp[1] * wp + pp * n[0], qp[2] * wp + pp * n[1], qp[3] * wp + pp * vnp};
+#pragma unroll
+  for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * D[v];
+}
+
 // One lane per Gauss point: (M+1)^2 consecutive lanes per swept edge,
 // 32 / (M+1)^2 edges per warp, the point contributions summed by a fixed
 // shuffle tree within each edge's lanes.
@@ -343,7 +402,8 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
         }
       }
       double F[4];
-      rusanov(T, qm, qp, n, F);
+      if (T.flux == 1) osher(T, qm, qp, n, F);
+      else rusanov(T, qm, qp, n, F);
 #pragma unroll
       for (int v = 0; v < 4; ++v) G[v] = wq * F[v];
 #pragma unroll

@@ -4,6 +4,9 @@
     python -m paper_1408_3719_gb300.runs vortex --n 45 90 179 [--order 3]
     python -m paper_1408_3719_gb300.runs explosion [--order 2] [--hc 0.00114] [--gts]
 
+``--flux osher`` selects the Osher-type ALE flux instead of the Rusanov-type
+one for any case.
+
 Each prints one JSON line per run: element updates, productive sweeps, wall
 time, updates/s, and the accuracy measure of the configuration (density L1
 error against the exact Riemann solution for the shock tube, Sec. 3.2; L2
@@ -51,15 +54,16 @@ def _run(mesh, Q, **cfg):
     t2 = time.perf_counter()
     e = s.get_elem()
     info = dict(n_tris=int(mesh["tri"].shape[0]), order_M=cfg.get("order_M"), gts=bool(cfg.get("gts", False)),
+                flux=cfg.get("flux", "rusanov"),
                 sweeps=sweeps, updates=updates, setup_s=t1 - t0, run_s=t2 - t1,
                 updates_per_s=updates / max(t2 - t1, 1e-12), gcl_max=s.diag()["gcl_max"])
     s.close()
     return e, info
 
 
-def sod(order=1, gts=True, nx=100, ny=10):
+def sod(order=1, gts=True, nx=100, ny=10, flux="rusanov"):
     mesh, Q = W.sod_tube(nx, ny)
-    e, info = _run(mesh, Q, order_M=order, t_end=0.2, gts=gts)
+    e, info = _run(mesh, Q, order_M=order, t_end=0.2, gts=gts, flux=flux)
     A = _areas(e["X"])
     cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
     ex = exact.sample(cx, 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1))
@@ -67,9 +71,9 @@ def sod(order=1, gts=True, nx=100, ny=10):
     return info
 
 
-def vortex(n, order=3, gts=False):
+def vortex(n, order=3, gts=False, flux="rusanov"):
     mesh, Q = W.vortex(n)
-    e, info = _run(mesh, Q, order_M=order, t_end=1.0, gts=gts)
+    e, info = _run(mesh, Q, order_M=order, t_end=1.0, gts=gts, flux=flux)
     x, w = np.polynomial.legendre.leggauss(6)
     x, w = 0.5 * (x + 1), 0.5 * w
     u, v = np.meshgrid(x, x, indexing="ij")
@@ -87,9 +91,9 @@ def vortex(n, order=3, gts=False):
     return info
 
 
-def explosion(order=2, hc=0.00114, gts=False):
+def explosion(order=2, hc=0.00114, gts=False, flux="rusanov"):
     mesh, Q = W.explosion(hc)
-    e, info = _run(mesh, Q, order_M=order, t_end=0.25, gts=gts)
+    e, info = _run(mesh, Q, order_M=order, t_end=0.25, gts=gts, flux=flux)
     r = np.linalg.norm(e["X"].reshape(-1, 3, 2).mean(1), axis=1)
     info.update(config="explosion EP1", rho_max=float(e["Q"][:, 0].max()), r_max=float(r.max()))
     return info
@@ -102,21 +106,22 @@ def main():
     ap.add_argument("--gts", action="store_true")
     ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
     ap.add_argument("--hc", type=float, default=0.00114)
+    ap.add_argument("--flux", default="rusanov", choices=["rusanov", "osher"])
     a = ap.parse_args()
     aleweno.load()
     if a.case == "sod":
-        print(json.dumps(sod(a.order or 1, a.gts)), flush=True)
+        print(json.dumps(sod(a.order or 1, a.gts, flux=a.flux)), flush=True)
     elif a.case == "vortex":
         prev = None
         for n in a.n:
-            r = vortex(n, a.order or 3, a.gts)
+            r = vortex(n, a.order or 3, a.gts, a.flux)
             if prev:
                 r["order_vs_previous"] = math.log(prev["l2_rho"] / r["l2_rho"]) / math.log(
                     r["h_max_circumdiameter"] / prev["h_max_circumdiameter"]) * -1
             print(json.dumps(r), flush=True)
             prev = r
     else:
-        print(json.dumps(explosion(a.order or 2, a.hc, a.gts)), flush=True)
+        print(json.dumps(explosion(a.order or 2, a.hc, a.gts, a.flux)), flush=True)
 
 
 if __name__ == "__main__":
