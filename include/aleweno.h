@@ -74,7 +74,10 @@ const char* aw_last_error(const aw_ctx* ctx);
  * bc: [n_tris][3] tag of local edge e = (v_e, v_{e+1 mod 3}): -1 interior,
  * 0 slip wall, 1 transmissive; shift: [n_tris][3][2] int8 periodic image of
  * each corner (corner = xy[node] + shift * period) or NULL, with period [2]
- * or NULL (both or neither).  The arrays are copied.  BAD_MESH on invalid input. */
+ * or NULL (both or neither); a zero period component means the mesh is not
+ * periodic in that direction (the shock tubes of Sec. 3.2 are periodic in y
+ * only), a negative one or two zeros are INVALID_ARG.  The arrays are copied.
+ * BAD_MESH on invalid input. */
 int aw_load_mesh(aw_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris,
                  const int32_t* tri, const int8_t* bc, const int8_t* shift,
                  const double* period);

@@ -540,8 +540,9 @@ static void rel_offset(const oc_ctx* c, const double* cen, int64_t i, int64_t j,
   double dy = cen[2 * j + 1] - cen[2 * i + 1];
   int ix = 0, iy = 0;
   if (c->periodic) {
-    ix = -(int)floor(dx / c->period[0] + 0.5);
-    iy = -(int)floor(dy / c->period[1] + 0.5);
+    /* a zero period component: not periodic in that direction */
+    if (c->period[0] > 0.0) ix = -(int)floor(dx / c->period[0] + 0.5);
+    if (c->period[1] > 0.0) iy = -(int)floor(dy / c->period[1] + 0.5);
     dx = dx + ix * c->period[0];
     dy = dy + iy * c->period[1];
   }
@@ -1477,6 +1478,8 @@ int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
     memcpy(c->shift, shift, 6 * n_tris);
     c->period[0] = period[0];
     c->period[1] = period[1];
+    if (!(period[0] >= 0.0 && period[1] >= 0.0 && period[0] + period[1] > 0.0))
+      return fail(c, OC_INVALID, "period components must be >= 0, one of them positive");
   }
   int rc = build_mesh(c, xy);
   if (rc) return rc;

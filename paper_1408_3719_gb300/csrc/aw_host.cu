@@ -342,9 +342,9 @@ inline void centroid_offset(const HostMesh& m, int i, int j, double& dx, double&
   dx = m.cen[2 * j] - m.cen[2 * i];
   dy = m.cen[2 * j + 1] - m.cen[2 * i + 1];
   sx = sy = 0;
-  if (m.periodic) {
-    sx = -(int)std::floor(dx / m.period[0] + 0.5);
-    sy = -(int)std::floor(dy / m.period[1] + 0.5);
+  if (m.periodic) {  // a zero period component: not periodic in that direction
+    if (m.period[0] > 0) sx = -(int)std::floor(dx / m.period[0] + 0.5);
+    if (m.period[1] > 0) sy = -(int)std::floor(dy / m.period[1] + 0.5);
     dx = dx + sx * m.period[0];
     dy = dy + sy * m.period[1];
   }
@@ -855,7 +855,8 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
     if (cudaMemcpy(m.shift.data(), shift, m.shift.size(), cudaMemcpyDefault) != cudaSuccess ||
         cudaMemcpy(m.period, period, 2 * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
       return set_err(c, AW_ERR_CUDA, "copying the periodic data failed");
-    if (!(m.period[0] > 0 && m.period[1] > 0)) return set_err(c, AW_ERR_INVALID_ARG, "period must be positive");
+    if (!(m.period[0] >= 0 && m.period[1] >= 0 && m.period[0] + m.period[1] > 0))
+      return set_err(c, AW_ERR_INVALID_ARG, "period components must be >= 0, one of them positive");
   } else {
     m.shift.assign(6 * n_tris, 0);
   }

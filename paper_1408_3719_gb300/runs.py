@@ -7,6 +7,15 @@
 ``--flux osher`` selects the Osher-type ALE flux instead of the Rusanov-type
 one for any case.
 
+The paper's own set-ups (third order = P2, Osher-type flux, LTS and GTS):
+
+    python -m paper_1408_3719_gb300.runs rp --problem RP1|RP2 [--gts]
+    python -m paper_1408_3719_gb300.runs ep --problem EP1|EP2 [--gts] [--t-end 0.2]
+    python -m paper_1408_3719_gb300.runs table
+
+``table`` runs RP1, RP2, EP1 and EP2 with both time-stepping modes and prints
+the update counts beside those of Tables tab.RPdata and tab.EPdata.
+
 Each prints one JSON line per run: element updates, productive sweeps, wall
 time, updates/s, and the accuracy measure of the configuration (density L1
 error against the exact Riemann solution for the shock tube, Sec. 3.2; L2
@@ -25,7 +34,13 @@ import numpy as np
 
 from . import aleweno
 from . import exact
+from . import radial
 from . import workloads as W
+
+# element updates to the final time printed in Tables tab.RPdata and tab.EPdata
+# (third-order scheme, Osher-type flux): (GTS, LTS)
+PAPER_UPDATES = {"RP1": (10.120404e6, 3.257847e6), "RP2": (23.349964e6, 5.020780e6),
+                 "EP1": (30.804224e6, 12.206887e6), "EP2": (181.412376e6, 38.274477e6)}
 
 
 def _areas(X):
@@ -99,29 +114,110 @@ def explosion(order=2, hc=0.00114, gts=False, flux="rusanov"):
     return info
 
 
+def riemann(case="RP1", order=2, gts=False, flux="osher"):
+    """A shock tube of Sec. 3.2 as the paper sets it up; density L1 error of
+    the averages against the exact solution, weighted by area."""
+    mesh, Q, t_end = W.riemann_problem(case)
+    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux)
+    A = _areas(e["X"])
+    cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
+    left, right, _ = W.RIEMANN_PROBLEMS[case]
+    ex = exact.sample(cx, t_end, 0.0, (left[0], left[1], left[3]), (right[0], right[1], right[3]))
+    info.update(config=case, t_end=t_end, l1_rho=float(np.sum(np.abs(e["Q"][:, 0] - ex[:, 0]) * A) / A.sum()),
+                paper_updates=PAPER_UPDATES[case][0 if gts else 1])
+    return info
+
+
+_REFERENCE = {}
+
+
+def _radial_reference(case, t_end, n):
+    key = (case, t_end, n)
+    if key not in _REFERENCE:
+        inner, outer, _ = W.EXPLOSION_PROBLEMS[case]
+        _REFERENCE[key] = radial.solve((inner[0], inner[1], inner[3]), (outer[0], outer[1], outer[3]),
+                                       r_d=0.5, t_end=t_end, n=n)
+    return _REFERENCE[key]
+
+
+def explosion_paper(case="EP1", order=2, gts=False, flux="osher", t_end=None, n_ref=15000):
+    """An explosion of Sec. 3.3 on the stand-in for mesh m1; density and
+    pressure L1 differences (area-weighted) against the 1D radial reference
+    solution of eqs. inhomEuler on n_ref points, sampled at the centroids."""
+    mesh, Q, t_def = W.explosion_problem(case)
+    t_end = t_def if t_end is None else t_end
+    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux)
+    A = _areas(e["X"])
+    rc = np.linalg.norm(e["X"].reshape(-1, 3, 2).mean(1), axis=1)
+    r, rho, u, p = _radial_reference(case, t_end, n_ref)
+    g = 1.4
+    q = e["Q"]
+    pr = (g - 1) * (q[:, 3] - 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2) / q[:, 0])
+    d_rho = np.abs(q[:, 0] - radial.sample(rc, r, rho))
+    d_p = np.abs(pr - radial.sample(rc, r, p))
+    info.update(config=case, t_end=t_end, l1_rho_vs_radial=float(np.sum(d_rho * A) / A.sum()),
+                l1_p_vs_radial=float(np.sum(d_p * A) / A.sum()), rho_max=float(q[:, 0].max()),
+                rho_max_radial=float(rho.max()), r_max=float(rc.max()),
+                paper_updates=PAPER_UPDATES[case][0 if gts else 1])
+    return info
+
+
+def table(order=2, flux="osher"):
+    """GTS and LTS update counts of RP1, RP2, EP1, EP2 beside the paper's."""
+    out = []
+    for case in ("RP1", "RP2", "EP1", "EP2"):
+        runs = {}
+        for gts in (True, False):
+            try:
+                runs[gts] = riemann(case, order, gts, flux) if case.startswith("RP") else \
+                    explosion_paper(case, order, gts, flux)
+            except RuntimeError as err:
+                runs[gts] = dict(config=case, gts=gts, failed=str(err)[:400])
+            print(json.dumps(runs[gts]), flush=True)
+        if "updates" in runs[True] and "updates" in runs[False]:
+            pg, pl = PAPER_UPDATES[case]
+            row = dict(config=case, gts_updates=runs[True]["updates"], lts_updates=runs[False]["updates"],
+                       ratio=runs[True]["updates"] / runs[False]["updates"], paper_gts=pg, paper_lts=pl,
+                       paper_ratio=pg / pl, n_tris=runs[False]["n_tris"])
+            print(json.dumps(row), flush=True)
+            out.append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sod", "vortex", "explosion"])
+    ap.add_argument("case", choices=["sod", "vortex", "explosion", "rp", "ep", "table"])
+    ap.add_argument("--problem", default=None, help="RP1 | RP2 (rp), EP1 | EP2 (ep)")
+    ap.add_argument("--t-end", type=float, default=None)
     ap.add_argument("--order", type=int, default=None)
     ap.add_argument("--gts", action="store_true")
     ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
     ap.add_argument("--hc", type=float, default=0.00114)
-    ap.add_argument("--flux", default="rusanov", choices=["rusanov", "osher"])
+    ap.add_argument("--flux", default=None, choices=["rusanov", "osher"],
+                    help="default: rusanov for sod/vortex/explosion, osher (the paper's) for rp/ep/table")
     a = ap.parse_args()
     aleweno.load()
-    if a.case == "sod":
-        print(json.dumps(sod(a.order or 1, a.gts, flux=a.flux)), flush=True)
+    paper = a.case in ("rp", "ep", "table")
+    flux = a.flux or ("osher" if paper else "rusanov")
+    if a.case == "rp":
+        print(json.dumps(riemann(a.problem or "RP1", a.order or 2, a.gts, flux)), flush=True)
+    elif a.case == "ep":
+        print(json.dumps(explosion_paper(a.problem or "EP1", a.order or 2, a.gts, flux, a.t_end)), flush=True)
+    elif a.case == "table":
+        table(a.order or 2, flux)
+    elif a.case == "sod":
+        print(json.dumps(sod(a.order or 1, a.gts, flux=flux)), flush=True)
     elif a.case == "vortex":
         prev = None
         for n in a.n:
-            r = vortex(n, a.order or 3, a.gts, a.flux)
+            r = vortex(n, a.order or 3, a.gts, flux)
             if prev:
                 r["order_vs_previous"] = math.log(prev["l2_rho"] / r["l2_rho"]) / math.log(
                     r["h_max_circumdiameter"] / prev["h_max_circumdiameter"]) * -1
             print(json.dumps(r), flush=True)
             prev = r
     else:
-        print(json.dumps(explosion(a.order or 2, a.hc, a.gts, a.flux)), flush=True)
+        print(json.dumps(explosion(a.order or 2, a.hc, a.gts, flux)), flush=True)
 
 
 if __name__ == "__main__":

@@ -134,6 +134,45 @@ def shock_tube_mesh(nx: int = 100, ny: int = 10, lx: float = 1.0, ly: float = 0.
                 name=f"shock_tube_{nx}x{ny}")
 
 
+def tube_mesh_periodic_y(nx: int = 211, ny: int = 21, x0: float = -0.5, lx: float = 1.0,
+                         y0: float = -0.05, ly: float = 0.1, jitter: float = 0.2,
+                         seed: int = SEED_BASE + 4) -> dict:
+    """Jittered grid on [x0, x0+lx] x [y0, y0+ly], periodic in y and
+    transmissive at both x ends (the set-up of the shock tubes of Sec. 3.2);
+    every quad split along its shorter diagonal.  2 nx ny triangles; the
+    default 211 x 21 gives the paper's N_E = 8862 at h ~ 1/200."""
+    rng = SplitMix64(seed)
+    hx, hy = lx / nx, ly / ny
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny), indexing="ij")
+    xy = np.stack([x0 + ii * hx, y0 + jj * hy], axis=-1).reshape(-1, 2).astype(np.float64)
+    inner_x = ((ii > 0) & (ii < nx)).reshape(-1)
+    jx = rng.uniform(xy.shape[0], -jitter * hx, jitter * hx)
+    jy = rng.uniform(xy.shape[0], -jitter * hy, jitter * hy)
+    xy[inner_x, 0] += jx[inner_x]
+    xy[:, 1] += jy
+    period = np.array([0.0, ly])
+    tris, shifts = [], []
+    for i in range(nx):
+        for j in range(ny):
+            corners = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+            ids = [ci * ny + (cj % ny) for ci, cj in corners]
+            sh = [(0, cj // ny) for ci, cj in corners]
+            P = [xy[k] + np.array(s_) * period for k, s_ in zip(ids, sh)]
+            a, b, c, d = range(4)
+            use_ac = np.sum((P[a] - P[c]) ** 2) <= np.sum((P[b] - P[d]) ** 2)
+            pick = [(a, b, c), (a, c, d)] if use_ac else [(a, b, d), (b, c, d)]
+            for t in pick:
+                tris.append([ids[k] for k in t])
+                shifts.append([sh[k] for k in t])
+    tri = np.asarray(tris, dtype=np.int32)
+    shift = np.asarray(shifts, dtype=np.int8)
+    bnd = _boundary_edges(tri)
+    bc = np.where(bnd, BC_TRANSMISSIVE, BC_INTERIOR).astype(np.int8)
+    assert np.all(_signed_areas(xy, tri, shift, period) > 0)
+    return dict(xy=xy, tri=tri, bc=bc, shift=shift, period=period,
+                name=f"tube_periodic_y_{nx}x{ny}")
+
+
 def vortex_grid_mesh(n: int, length: float = 10.0, jitter: float = 0.2,
                      seed: int = SEED_BASE + 1) -> dict:
     """Periodic n x n torus grid on [0,length]^2, every node jittered,
@@ -169,12 +208,13 @@ def vortex_grid_mesh(n: int, length: float = 10.0, jitter: float = 0.2,
 
 
 def disc_mesh(h_centre: float, grading: float = 10.0, radius: float = 1.0,
-              seed: int = SEED_BASE + 2, layer: float = 0.866) -> dict:
+              seed: int = SEED_BASE + 2, layer: float = 0.866, hfun=None) -> dict:
     """Graded disc of the given radius: concentric rings with spacing
-    h(r) = h_centre * grading**(r/radius), stitched by angular merge; a fan
-    closes the centre.  Transmissive rim."""
+    h(r) = h_centre * grading**(r/radius) (or the given ``hfun(r)``),
+    stitched by angular merge; a fan closes the centre.  Transmissive rim."""
     rng = SplitMix64(seed)
-    hfun = lambda r: h_centre * grading ** (r / radius)
+    if hfun is None:
+        hfun = lambda r: h_centre * grading ** (r / radius)
     radii = [0.0]
     r = hfun(0.0)
     while r < radius:
@@ -348,6 +388,48 @@ def explosion(h_centre, seed=SEED_BASE + 2, gamma=1.4, inner=(1, 0, 0, 1), outer
     q = cell_average(mesh, lambda x, y: explosion_state(x, y, inner, outer, radius, gamma),
                      _subtriangle_rule(16))
     return mesh, q
+
+
+# Table tab.iniRP2D: primitive (rho, u, v, p) left and right of x_d = 0, final time
+RIEMANN_PROBLEMS = {
+    "RP1": ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), 0.2),
+    "RP2": ((0.445, 0.698, 0.0, 3.528), (0.5, 0.0, 0.0, 0.571), 0.1),
+}
+
+# Table tab.iniEP2D: primitive inner (r < 0.5) and outer states, final time
+# (EP1's final time is 0.2 in the table and 0.25 in the caption of its figure)
+EXPLOSION_PROBLEMS = {
+    "EP1": ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), 0.25),
+    "EP2": ((1.0, 0.0, 0.0, 1000.0), (1.0, 0.0, 0.0, 0.01), 0.012),
+}
+
+
+def riemann_problem(case="RP1", nx=211, ny=21, seed=SEED_BASE + 4, gamma=1.4):
+    """The shock tubes of Sec. 3.2 as the paper sets them up: [-0.5, 0.5] x
+    [-0.05, 0.05], periodic in y, transmissive in x, discontinuity at x = 0;
+    returns (mesh, Q, t_end)."""
+    left, right, t_end = RIEMANN_PROBLEMS[case]
+    mesh = tube_mesh_periodic_y(nx, ny, seed=seed)
+    q = cell_average(mesh, lambda x, y: riemann_state(x, y, left, right, 0.0, gamma), _subtriangle_rule(16))
+    return mesh, q, t_end
+
+
+def disc_m1_mesh(scale=0.86, seed=SEED_BASE + 5):
+    """Stand-in for the paper's mesh m1 of Sec. 3.3: unit disc with size
+    h = 1/100 for r <= 0.5 and 1/50 beyond r = 0.53 (linear in between, so
+    that no triangle at the interface is worse than elsewhere: smallest angle
+    28 degrees), both multiplied by ``scale``; the default gives 44,097
+    triangles (the paper: N_E = 43756)."""
+    return disc_mesh(0.0, seed=seed,
+                     hfun=lambda r: scale * (0.01 if r <= 0.5 else 0.01 + 0.01 * min(1.0, (r - 0.5) / 0.03)))
+
+
+def explosion_problem(case="EP1", scale=0.86, seed=SEED_BASE + 5, gamma=1.4):
+    """The explosions of Sec. 3.3 on the m1 stand-in; returns (mesh, Q, t_end)."""
+    inner, outer, t_end = EXPLOSION_PROBLEMS[case]
+    mesh = disc_m1_mesh(scale, seed)
+    q = cell_average(mesh, lambda x, y: explosion_state(x, y, inner, outer, 0.5, gamma), _subtriangle_rule(16))
+    return mesh, q, t_end
 
 
 def batched_instances(n_inst=256, lo=2000, hi=60000, seed=SEED_BASE + 3, gamma=1.4, size_scale=1.0):
