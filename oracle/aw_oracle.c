@@ -54,6 +54,10 @@
  *     base run's schedule (used by the central differences of the adjoint).
  *  R14 Osher-type flux: the path integral of |A_n^V| (eq. osher) by 3-point
  *     Gauss-Legendre quadrature on [0, 1] along the straight path (eq. path).
+ *  R15 transmissive boundary state: the outer state of a transmissive edge is
+ *     the boundary element's cell average at the start of the sweep (not the
+ *     inner state at the quadrature point, with which a gas at rest next to
+ *     a transmissive boundary grows from roundoff at M >= 1).
  */
 #include "aw_oracle.h"
 
@@ -1682,6 +1686,9 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
           double cr = 1.0 - chi;
           eval_qh(c, qR, refv[lr][0] + cr * (refv[(lr + 1) % 3][0] - refv[lr][0]),
                   refv[lr][1] + cr * (refv[(lr + 1) % 3][1] - refv[lr][1]), tauR, qp);
+        } else if (c->edge_bc[ed] == 1) {
+          /* transmissive: the boundary element's sweep-start average (R15) */
+          for (int v = 0; v < 4; ++v) qp[v] = c->Q[4 * L + v];
         } else {
           boundary_state(c->edge_bc[ed], qm, n, qp);
         }

@@ -73,7 +73,9 @@ int oc_get_stencils(const oc_ctx* c, int64_t i, int32_t* members, int32_t* sw, i
 int oc_reconstruct_eval(oc_ctx* c, int64_t i, int64_t npts, const double* xy, double* out);
 int oc_predict_debug(oc_ctx* c, const double* X6, double dt_sec, const double* w_nodal,
                      double* qhat_out);
-/* the configuration's numerical flux; qR NULL: boundary state of type bc */
+/* the configuration's numerical flux; qR NULL: boundary state of type bc built
+   from qL (a wall mirrors the normal momentum; transmissive copies qL: in a
+   sweep the transmissive outer state is the element average instead, R15) */
 int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const double* n3,
                   int bc, double* out);
 int oc_eval_qh(const oc_ctx* c, const double* qhat, int64_t npts, const double* pts, double* out);

@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
     const int q = (item >> 5) * EPW + slot;
     const bool valid = item < n_items && slot < EPW && q < n_active;
     double Pb[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    double trLb[Nt][Nt][4], trRb[Nt][Nt][4];
+    double trLb[Nt][Nt][4], trRb[Nt][Nt][4], qgb[4] = {0, 0, 0, 0};
     int na = 0, nb_ = 0, gxl = -1, Ll = 0, lel = 0, Rl = -1, lrl = 0;
+    bool trans = false;
     bool ma = false, mb = false;
     if (valid) {
       const int ed = d.active_list[q];
@@ -292,6 +293,8 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
         for (int k = 0; k < Nt * 4; ++k) (&in.trL[gx][0][0])[k] = cL[gx * Nt * 4 + k];
         in.has_R = R >= 0;
         in.bc = d.edge_bc[ed];
+        trans = R < 0 && in.bc == 1;
+        for (int v = 0; v < 4; ++v) in.qg[v] = trans ? d.Q[4 * (size_t)L + v] : 0.0;
         if (R >= 0) {
           in.tR = (double)d.t[R];
           in.dtR = (double)d.dt[R];
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
           for (int v = 0; v < 4; ++v) trLb[gx][p][v] = trRb[Nt - 1 - gx][p][v] = 0.0;
         // a zero flux adjoint contributes exact zeros
         if (Gb[0] != 0.0 || Gb[1] != 0.0 || Gb[2] != 0.0 || Gb[3] != 0.0)
-          adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
+          adj::edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb, qgb);
         gxl = gx;
         Ll = L; lel = le; Rl = R; lrl = lr;
       }
@@ -339,6 +342,18 @@ __global__ void __launch_bounds__(128) k_adj_edges(Tab T, Dev d, Adj a) {
           if (in) Pb[k][c] += o;
         }
     }
+    // transmissive outer state: the left element's sweep-start average
+#pragma unroll
+    for (int off = 1; off < NP; off <<= 1) {
+      const bool in = pt + off < NP;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double o = __shfl_down_sync(0xffffffffu, qgb[v], off);
+        if (in) qgb[v] += o;
+      }
+    }
+    if (valid && pt == 0 && trans)
+      for (int v = 0; v < 4; ++v) atomicAdd(&a.Qb[4 * (size_t)Ll + v], qgb[v]);
     if (valid && pt == 0)
       for (int c = 0; c < 2; ++c) {
         atomicAdd(&a.nXb[2 * na + c], Pb[0][c] + (ma ? 0.0 : Pb[3][c]));
@@ -696,6 +711,8 @@ double selftest_edge(const Tab& T, Rng& g, int has_R, int bc) {
   in.tL = 90; in.dtL = 100; in.tR = 110; in.dtR = 80;
   in.has_R = has_R;
   in.bc = bc;
+  field(0.2, 0.15, in.qg);
+  in.qg[3] *= 1.6;  // a hotter outer state: no tie of the two wave speeds
   for (int gx = 0; gx < Nt; ++gx) {
     double qa[4], qb[4];
     field(0.3 * gx, 0.1, qa);
@@ -709,17 +726,19 @@ double selftest_edge(const Tab& T, Rng& g, int has_R, int bc) {
       }
     }
   }
-  double Gb[4], dP[4][2], dL[Nt][Nt][4], dR[Nt][Nt][4];
+  double Gb[4], dP[4][2], dL[Nt][Nt][4], dR[Nt][Nt][4], dg[4];
   for (int v = 0; v < 4; ++v) Gb[v] = g.sym();
+  for (int v = 0; v < 4; ++v) dg[v] = 0.1 * g.sym() * in.qg[v];
   for (int k = 0; k < 4; ++k)
     for (int c = 0; c < 2; ++c) dP[k][c] = 0.01 * g.sym();
   for (int k = 0; k < Nt * Nt * 4; ++k) {
     (&dL[0][0][0])[k] = g.sym();
     (&dR[0][0][0])[k] = g.sym();
   }
-  double Pb[4][2] = {}, trLb[Nt][Nt][4] = {}, trRb[Nt][Nt][4] = {};
-  adj::edge_rev<M>(T, in, Gb, Pb, trLb, trRb);
+  double Pb[4][2] = {}, trLb[Nt][Nt][4] = {}, trRb[Nt][Nt][4] = {}, qgb[4] = {};
+  adj::edge_rev<M>(T, in, Gb, Pb, trLb, trRb, qgb);
   double ad = 0.0;
+  for (int v = 0; v < 4; ++v) ad += qgb[v] * dg[v];
   for (int k = 0; k < 4; ++k)
     for (int c = 0; c < 2; ++c) ad += Pb[k][c] * dP[k][c];
   for (int k = 0; k < Nt * Nt * 4; ++k) ad += (&trLb[0][0][0])[k] * (&dL[0][0][0])[k] + (&trRb[0][0][0])[k] * (&dR[0][0][0])[k];
@@ -727,6 +746,7 @@ double selftest_edge(const Tab& T, Rng& g, int has_R, int bc) {
     adj::EdgeIn<M> p = in;
     for (int k = 0; k < 4; ++k)
       for (int c = 0; c < 2; ++c) p.P[k][c] += eps * dP[k][c];
+    for (int v = 0; v < 4; ++v) p.qg[v] += eps * dg[v];
     for (int k = 0; k < Nt * Nt * 4; ++k) {
       (&p.trL[0][0][0])[k] += eps * (&dL[0][0][0])[k];
       (&p.trR[0][0][0])[k] += eps * (&dR[0][0][0])[k];

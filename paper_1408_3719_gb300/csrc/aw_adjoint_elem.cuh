@@ -1068,6 +1068,7 @@ struct EdgeIn {
   double trL[S::Nt][S::Nt][4];    // left trace: Gauss point, tau power, variable
   double trR[S::Nt][S::Nt][4];    // right trace, its own Gauss point order
   double tL, dtL, tR, dtR;        // ticks of the two sides
+  double qg[4];                   // transmissive outer state: the left element's average
   int has_R, bc;                  // bc 0 wall, 1 transmissive (no right side)
 };
 
@@ -1188,6 +1189,8 @@ AW_HD inline void edge_point(const Tab& T, const EdgeIn<M>& in, int gx, int gt, 
       for (int p = Nt - 2; p >= 0; --p) acc = acc * *tr + in.trR[Nt - 1 - gx][p][v];
       qp[v] = acc;
     }
+  } else if (in.bc == 1) {
+    for (int v = 0; v < 4; ++v) qp[v] = in.qg[v];
   } else {
     for (int v = 0; v < 4; ++v) qp[v] = qm[v];
     if (in.bc == 0) {
@@ -1215,11 +1218,12 @@ AW_HD void edge_fwd(const Tab& T, const EdgeIn<M>& in, double* G) {
     }
 }
 
-// reverse of the Gauss point (gx, gt) of edge_fwd: adds to Pb[4][2] and the
+// reverse of the Gauss point (gx, gt) of edge_fwd: adds to Pb[4][2], the
 // two traces' adjoints (row gx of the left trace, row Nt-1-gx of the right)
+// and, on a transmissive edge, the outer state's adjoint qgb[4]
 template <int M>
 AW_HD void edge_point_rev(const Tab& T, const EdgeIn<M>& in, int gx, int gt, const double* Gb, double (*Pb)[2],
-                          double (*trLb)[Sz<M>::Nt][4], double (*trRb)[Sz<M>::Nt][4]) {
+                          double (*trLb)[Sz<M>::Nt][4], double (*trRb)[Sz<M>::Nt][4], double* qgb) {
   constexpr int Nt = Sz<M>::Nt;
   const double g = T.gamma;
   double qm[4], qp[4], n[3], dchi[3], dtau[3], tl, tr;
@@ -1248,6 +1252,8 @@ AW_HD void edge_point_rev(const Tab& T, const EdgeIn<M>& in, int gx, int gt, con
       for (int v = 0; v < 4; ++v) trRb[Nt - 1 - gx][p][v] += qpb[v] * tp_;
       tp_ *= tr;
     }
+  } else if (in.bc == 1) {
+    for (int v = 0; v < 4; ++v) qgb[v] += qpb[v];
   } else {
     for (int v = 0; v < 4; ++v) qmb[v] += (v == 1 || v == 2) ? 0.0 : qpb[v];
     const double nn = n[0] * n[0] + n[1] * n[1];
@@ -1297,10 +1303,10 @@ AW_HD void edge_point_rev(const Tab& T, const EdgeIn<M>& in, int gx, int gt, con
 // reverse of edge_fwd: adds to Pb[4][2] and the two traces' adjoints
 template <int M>
 AW_HD void edge_rev(const Tab& T, const EdgeIn<M>& in, const double* Gb, double (*Pb)[2], double (*trLb)[Sz<M>::Nt][4],
-                    double (*trRb)[Sz<M>::Nt][4]) {
+                    double (*trRb)[Sz<M>::Nt][4], double* qgb) {
   constexpr int Nt = Sz<M>::Nt;
   for (int gx = 0; gx < Nt; ++gx)
-    for (int gt = 0; gt < Nt; ++gt) edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb);
+    for (int gt = 0; gt < Nt; ++gt) edge_point_rev<M>(T, in, gx, gt, Gb, Pb, trLb, trRb, qgb);
 }
 
 // ---------------------------------------------------------------------------

@@ -389,6 +389,12 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
           for (int p = Nt - 2; p >= 0; --p) acc = acc * tr + c0[p * 4 + v];
           qp[v] = acc;
         }
+      } else if (d.edge_bc[ed] == 1) {
+        // transmissive: the boundary element's sweep-start average (phase A
+        // updates Q after this kernel), not the inner trace value, with
+        // which a gas at rest beside the boundary grows from roundoff
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qp[v] = d.Q[4 * (size_t)L + v];
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = qm[v];

@@ -94,3 +94,22 @@ def test_period_components_are_validated():
     bad["period"] = np.array([-1.0, 0.1])
     with pytest.raises(Exception):
         o.load_mesh(bad)
+
+
+def test_gas_at_rest_beside_transmissive_ends_stays_at_rest():
+    """Reading R15: the outer state of a transmissive edge is the boundary
+    element's average.  Taking the inner trace value instead makes the flux
+    through the edge the bare physical flux of an extrapolated state; an
+    incoming characteristic then sees downwind differencing and a gas at rest
+    grows from roundoff (about 4 % per step at P1 on this mesh: 1e-15 to 1e-10
+    in 300 steps)."""
+    mesh = W.tube_mesh_periodic_y(40, 4)
+    Q = np.tile(W.prim_to_cons(1.0, 0.0, 0.0, 1.0, 1.4), (mesh["tri"].shape[0], 1))
+    o = Oracle(order_M=1, t_end=10.0, gts=True)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    for _ in range(300):
+        o.sweep()
+    q = o.get_elem()["Q"]
+    assert np.abs(q[:, 1:3]).max() < 1e-13
+    assert np.abs(q[:, 0] - 1.0).max() < 1e-13
