@@ -311,15 +311,16 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2.load_state(Qh)
-        ups = 0
-        for _ in range(args.e2e_sweeps):
-            ups += s2.sweep()
+        s2.sync()
+        s2.enqueue(args.e2e_sweeps)
+        ups = s2.sync()
         s2.get_state(out)
         el = time.perf_counter() - t0
         nst = args.e2e_sweeps
         e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": Qh.nbytes / nst,
-               "d2h_bytes_per_step": (out.nbytes + 8 * nst) / nst,
-               "note": "aw_load_state(host Q) + sweeps via aw_lts_sweep + aw_get_state(host Q); mesh pre-processing "
+               "d2h_bytes_per_step": (out.nbytes + 16) / nst,
+               "note": "aw_load_state(host Q, with the pre-processing phase of the state) + aw_enqueue_sweeps + "
+                       "aw_sync (update count) + aw_get_state(host Q); mesh pre-processing "
                        f"({t_mesh:.1f} s, once per mesh) excluded"}
         s2.close()
 
