@@ -407,12 +407,12 @@ EXPLOSION_PROBLEMS = {
 }
 
 
-def riemann_problem(case="RP1", nx=211, ny=21, seed=SEED_BASE + 4, gamma=1.4):
+def riemann_problem(case="RP1", nx=211, ny=21, seed=SEED_BASE + 4, gamma=1.4, jitter=0.1):
     """The shock tubes of Sec. 3.2 as the paper sets them up: [-0.5, 0.5] x
     [-0.05, 0.05], periodic in y, transmissive in x, discontinuity at x = 0;
     returns (mesh, Q, t_end)."""
     left, right, t_end = RIEMANN_PROBLEMS[case]
-    mesh = tube_mesh_periodic_y(nx, ny, seed=seed)
+    mesh = tube_mesh_periodic_y(nx, ny, seed=seed, jitter=jitter)
     q = cell_average(mesh, lambda x, y: riemann_state(x, y, left, right, 0.0, gamma), _subtriangle_rule(16))
     return mesh, q, t_end
 
