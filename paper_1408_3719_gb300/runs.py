@@ -114,7 +114,7 @@ def explosion(order=2, hc=0.00114, gts=False, flux="rusanov"):
     return info
 
 
-def riemann(case="RP1", order=2, gts=False, flux="osher", jitter=0.1):
+def riemann(case="RP1", order=2, gts=False, flux="osher", jitter=0.0):
     """A shock tube of Sec. 3.2 as the paper sets it up; density L1 error of
     the averages against the exact solution, weighted by area."""
     mesh, Q, t_end = W.riemann_problem(case, jitter=jitter)

@@ -53,7 +53,7 @@ CASES = {
     "disc_p3": (lambda: W.explosion(0.04), dict(order_M=3, t_end=0.25)),
     "vortex_p2_gts": (lambda: W.vortex(10), dict(order_M=2, t_end=1.0, gts=True)),
     "tube_p1_eulerian": (lambda: W.sod_tube(40, 6), dict(order_M=1, t_end=0.2, eulerian=True)),
-    "rp1_periodic_y_p2": (lambda: W.riemann_problem("RP1", 40, 6)[:2], dict(order_M=2, t_end=0.2)),
+    "rp1_periodic_y_p2": (lambda: W.riemann_problem("RP1", 40, 6, jitter=0.1)[:2], dict(order_M=2, t_end=0.2)),
 }
 
 
