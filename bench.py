@@ -562,7 +562,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--e2e-sweeps", type=int, default=2000)
+    ap.add_argument("--e2e-sweeps", type=int, default=500)
     ap.add_argument("--workload", default="explosion", choices=["explosion", "batched", "adjoint"])
     ap.add_argument("--vortex-n", type=int, default=158)
     ap.add_argument("--tune-sweeps", type=int, default=20)
