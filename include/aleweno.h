@@ -60,6 +60,14 @@ typedef struct {
   void* cuda_stream;      /* cudaStream_t to run on, or NULL for a stream the context creates */
   int flux;               /* 0: Rusanov-type ALE flux (eq. rusanov); 1: Osher-type ALE flux (eq. osher)
                              on the straight path (eq. path), path integral by 3-point Gauss-Legendre */
+  double wall_u, wall_v;  /* velocity of the moving slip walls (boundary tag 2), the piston of Sec. 3.5:
+                             their nodes move with it, the outer state mirrors the momentum normal to
+                             the wall relative to it, and an element with such an edge counts the wall's
+                             speed in its local step */
+  double t_switch;        /* > 0: until t_switch every element takes the global minimum of the local
+                             steps computed with CFL cfl_start, clipped at t_switch; local steps after
+                             (the start of the Saltzman run, Sec. 3.5); 0: none */
+  double cfl_start;
 } aw_config;
 
 /* Create a context (Sec. 2.1 set-up).  INVALID_ARG on an unsupported config. */
@@ -72,7 +80,7 @@ const char* aw_last_error(const aw_ctx* ctx);
  * reconstruction stencils per element and the symmetric total stencil S^W
  * (eq. WENOstencil).  tri: [n_tris][3] counter-clockwise node indices;
  * bc: [n_tris][3] tag of local edge e = (v_e, v_{e+1 mod 3}): -1 interior,
- * 0 slip wall, 1 transmissive; shift: [n_tris][3][2] int8 periodic image of
+ * 0 slip wall, 1 transmissive, 2 slip wall moving with (wall_u, wall_v); shift: [n_tris][3][2] int8 periodic image of
  * each corner (corner = xy[node] + shift * period) or NULL, with period [2]
  * or NULL (both or neither); a zero period component means the mesh is not
  * periodic in that direction (the shock tubes of Sec. 3.2 are periodic in y

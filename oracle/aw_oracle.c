@@ -54,6 +54,10 @@
  *     base run's schedule (used by the central differences of the adjoint).
  *  R14 Osher-type flux: the path integral of |A_n^V| (eq. osher) by 3-point
  *     Gauss-Legendre quadrature on [0, 1] along the straight path (eq. path).
+ *  R16 moving slip wall and start-up: a bc-2 edge mirrors the momentum normal
+ *     to it relative to the wall velocity; its nodes move with the wall.
+ *     Until t_switch every element takes the global minimum of the local
+ *     steps computed with CFL cfl_start, clipped at t_switch (Sec. 3.5).
  *  R15 transmissive boundary state: the outer state of a transmissive edge is
  *     the boundary element's cell average at the start of the sweep (not the
  *     inner state at the quadrature point, with which a gas at rest next to
@@ -104,6 +108,8 @@ struct oc_ctx {
   int8_t* shift;  /* [ne][3][2] */
   int periodic;
   double period[2];
+  int64_t Tsw;         /* ticks of the global-step start-up, 0 if none */
+  double wall_speed;   /* |(wall_u, wall_v)| */
   int64_t nedges;
   int32_t* edge_nodes; /* [nedges][2] a,b in the owner's orientation */
   int32_t* edge_elem;  /* [nedges][2] owner (left), right or -1 */
@@ -115,7 +121,7 @@ struct oc_ctx {
   int64_t* v2e_ptr;    /* node -> elements CSR */
   int32_t* v2e;
   int8_t* v2e_loc;
-  int8_t* node_type;   /* 0 free, 1 slide, 2 fixed */
+  int8_t* node_type;   /* 0 free, 1 slide, 2 fixed, 3 moves with the wall */
   double* node_n;      /* [nn][2] wall normal */
   int32_t* sten;       /* [ne][7][ne_max] members, -1 dropped */
   int8_t* sten_shift;  /* [ne][7][ne_max][2] */
@@ -700,6 +706,10 @@ static int build_mesh(oc_ctx* c, const double* xy) {
       }
     }
   }
+  /* nodes of moving walls move with the wall (R16) */
+  for (int64_t ed = 0; ed < ned; ++ed)
+    if (c->edge_bc[ed] == 2)
+      for (int q = 0; q < 2; ++q) c->node_type[c->edge_nodes[2 * ed + q]] = 3;
   /* stencils */
   int ne_s = c->ne;
   c->sten = (int32_t*)malloc(sizeof(int32_t) * ne * NSTEN * ne_s);
@@ -1001,14 +1011,19 @@ static void num_flux(const oc_ctx* c, const double* qm, const double* qp, const 
   else rusanov(c, qm, qp, n, F);
 }
 
-static void boundary_state(int bc, const double* q, const double* n, double* qb) {
+static void boundary_state(const oc_ctx* c, int bc, const double* q, const double* n, double* qb) {
   for (int v = 0; v < 4; ++v) qb[v] = q[v];
-  if (bc == 0) {
+  if (bc == 0 || bc == 2) {
+    /* mirror the momentum normal to the wall, relative to the wall's velocity */
+    double wu = bc == 2 ? c->cfg.wall_u : 0.0, wv = bc == 2 ? c->cfg.wall_v : 0.0;
     double nn = n[0] * n[0] + n[1] * n[1];
     if (nn > 0.0) {
-      double mn = (q[1] * n[0] + q[2] * n[1]) / nn;
+      double mn = ((q[1] - q[0] * wu) * n[0] + (q[2] - q[0] * wv) * n[1]) / nn;
       qb[1] = q[1] - 2.0 * mn * n[0];
       qb[2] = q[2] - 2.0 * mn * n[1];
+      /* same internal energy: the mirrored momentum of a moving wall has
+         another kinetic energy */
+      if (bc == 2) qb[3] = q[3] + 0.5 * (qb[1] * qb[1] + qb[2] * qb[2] - q[1] * q[1] - q[2] * q[2]) / q[0];
     }
   }
 }
@@ -1184,7 +1199,7 @@ static void reconstruct(const oc_ctx* c, int64_t i, double* w) {
 
 /* local time step of element i from its own and its edge neighbours' virtual
    data (eq. timestep, R9), in seconds */
-static double local_dt(const oc_ctx* c, int64_t i) {
+static double local_dt(const oc_ctx* c, int64_t i, double cfl) {
   double best = HUGE_VAL;
   for (int e = -1; e < 3; ++e) {
     int64_t j = e < 0 ? i : c->nbr[i * 3 + e];
@@ -1199,8 +1214,12 @@ static double local_dt(const oc_ctx* c, int64_t i) {
     }
     double d = 4.0 * area / per;
     double u = Qv[1] / Qv[0], v = Qv[2] / Qv[0];
-    double lam = sqrt(u * u + v * v) + sqrt(c->cfg.gamma * pressure(c, Qv) / Qv[0]);
-    double dtj = c->cfg.cfl * d / lam;
+    double vel = sqrt(u * u + v * v);
+    if (e < 0) /* an element on a moving wall counts the wall's speed (R16) */
+      for (int k = 0; k < 3; ++k)
+        if (c->edge_bc[c->elem_edge[i * 3 + k]] == 2) vel = fmax(vel, c->wall_speed);
+    double lam = vel + sqrt(c->cfg.gamma * pressure(c, Qv) / Qv[0]);
+    double dtj = cfl * d / lam;
     if (dtj < best) best = dtj;
   }
   return best;
@@ -1376,14 +1395,16 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
     int64_t i = list[q];
     reconstruct(c, i, W + q * c->Mc * 4);
     int64_t ticks = 0;
+    const int start = c->t[i] < c->Tsw;  /* global-step start-up (R16) */
     if (c->t[i] < c->T) {
-      double dts = local_dt(c, i);
+      double dts = local_dt(c, i, start ? c->cfg.cfl_start : c->cfg.cfl);
       if (!(dts > 0.0)) {
         rc = fail(c, OC_NONPHYSICAL, "element %lld: non-positive time step", (long long)i);
         break;
       }
       double r = floor(dts / c->tick);
-      ticks = r > (double)(c->T - c->t[i]) ? c->T - c->t[i] : (int64_t)r;
+      int64_t end = start ? c->Tsw : c->T;
+      ticks = r > (double)(end - c->t[i]) ? end - c->t[i] : (int64_t)r;
       if (ticks < 1) ticks = 1;
     }
     if (c->sched_mode != 0) {
@@ -1397,11 +1418,11 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
       else ticks = *slot;
     }
     c->dt[i] = ticks;
-    if (ticks > 0 && ticks < gmin) gmin = ticks;
+    if (ticks > 0 && ticks < gmin && (c->cfg.gts || start)) gmin = ticks;
   }
-  if (rc == OC_OK && c->cfg.gts && gmin != INT64_MAX)
+  if (rc == OC_OK && gmin != INT64_MAX)
     for (int64_t q = 0; q < n; ++q)
-      if (c->dt[list[q]] > 0) c->dt[list[q]] = gmin;
+      if (c->dt[list[q]] > 0 && (c->cfg.gts || c->t[list[q]] < c->Tsw)) c->dt[list[q]] = gmin;
   if (rc == OC_OK)
     for (int64_t q = 0; q < n; ++q) element_predictor(c, list[q], W + q * c->Mc * 4);
   free(W);
@@ -1414,7 +1435,8 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
 
 int oc_create(const oc_config* cfg, oc_ctx** out) {
   if (!cfg || !out || cfg->order_M < 1 || cfg->order_M > MAXM || !(cfg->t_end > 0) || cfg->time_quantum_log2 < 1 ||
-      cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->flux < 0 || cfg->flux > 1)
+      cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->flux < 0 || cfg->flux > 1 ||
+      (cfg->t_switch > 0.0 && !(cfg->cfl_start > 0)))
     return OC_INVALID;
   oc_ctx* c = (oc_ctx*)calloc(1, sizeof(oc_ctx));
   c->cfg = *cfg;
@@ -1426,6 +1448,12 @@ int oc_create(const oc_config* cfg, oc_ctx** out) {
   c->nit = cfg->predictor_iters > 0 ? cfg->predictor_iters : c->M + 1;
   c->T = (int64_t)1 << cfg->time_quantum_log2;
   c->tick = ldexp(cfg->t_end, -cfg->time_quantum_log2);
+  c->wall_speed = sqrt(cfg->wall_u * cfg->wall_u + cfg->wall_v * cfg->wall_v);
+  c->Tsw = 0;
+  if (cfg->t_switch > 0.0) {
+    double r = floor(cfg->t_switch / c->tick);
+    c->Tsw = r >= (double)c->T ? c->T : (int64_t)r;
+  }
   if (build_tables(c)) {
     free(c);
     return OC_INVALID;
@@ -1470,8 +1498,10 @@ int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
   free_mesh(c);
   c->nn = n_nodes;
   c->ne_ = n_tris;
-  for (int64_t q = 0; q < 3 * n_tris; ++q)
+  for (int64_t q = 0; q < 3 * n_tris; ++q) {
     if (tri[q] < 0 || tri[q] >= n_nodes) return fail(c, OC_BAD_MESH, "node index out of range");
+    if (bc[q] < -1 || bc[q] > 2) return fail(c, OC_BAD_MESH, "boundary tag out of range");
+  }
   c->tri = (int32_t*)malloc(sizeof(int32_t) * 3 * n_tris);
   memcpy(c->tri, tri, sizeof(int32_t) * 3 * n_tris);
   c->bc = (int8_t*)malloc(3 * n_tris);
@@ -1541,7 +1571,8 @@ int oc_load_state_xy(oc_ctx* c, const double* Q, const double* xy) {
 
 int oc_schedule(oc_ctx* c, int mode, int64_t k) {
   if (!c || !c->tri || mode < 0 || mode > 2) return OC_INVALID;
-  if (mode != 0 && c->cfg.gts) return fail(c, OC_INVALID, "the schedule log is for local time stepping");
+  if (mode != 0 && (c->cfg.gts || c->Tsw > 0))
+    return fail(c, OC_INVALID, "the schedule log is for local time stepping");
   if (mode == 1) {
     if (k < 1) return OC_INVALID;
     free(c->sched_log);
@@ -1631,6 +1662,10 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
       D[1] -= dn * c->node_n[2 * n + 1];
     } else if (c->node_type[n] == 2) {
       D[0] = D[1] = 0.0;
+    } else if (c->node_type[n] == 3) {
+      double span = (double)(tnew[n] - c->nt[n]) * c->tick;
+      D[0] = c->cfg.wall_u * span;
+      D[1] = c->cfg.wall_v * span;
     }
     Xnew[2 * n] = c->nX[2 * n] + D[0];
     Xnew[2 * n + 1] = c->nX[2 * n + 1] + D[1];
@@ -1690,7 +1725,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
           /* transmissive: the boundary element's sweep-start average (R15) */
           for (int v = 0; v < 4; ++v) qp[v] = c->Q[4 * L + v];
         } else {
-          boundary_state(c->edge_bc[ed], qm, n, qp);
+          boundary_state(c, c->edge_bc[ed], qm, n, qp);
         }
         double F[4];
         num_flux(c, qm, qp, n, F);
@@ -1869,7 +1904,7 @@ int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const dou
   if (qR)
     memcpy(qp, qR, sizeof qp);
   else
-    boundary_state(bc, qL, n3, qp);
+    boundary_state(c, bc, qL, n3, qp);
   num_flux(c, qL, qp, n3, out);
   return OC_OK;
 }

@@ -36,6 +36,10 @@ typedef struct {
   int predictor_iters;  /* Picard iterations of eq. CGfinal; <=0 means M+1 */
   int mesh_velocity;    /* 0: V = v (Lagrangian-type), 1: V = 0 (Eulerian) */
   int flux;             /* 0: Rusanov-type (eq. rusanov), 1: Osher-type (eq. osher) */
+  double wall_u, wall_v; /* velocity of the moving slip walls (bc 2), Sec. 3.5 piston */
+  double t_switch;      /* > 0: global steps with CFL cfl_start until t_switch, then
+                           local steps (the start of the Saltzman run, Sec. 3.5) */
+  double cfl_start;
 } oc_config;
 
 int oc_create(const oc_config* cfg, oc_ctx** out);
@@ -74,8 +78,9 @@ int oc_reconstruct_eval(oc_ctx* c, int64_t i, int64_t npts, const double* xy, do
 int oc_predict_debug(oc_ctx* c, const double* X6, double dt_sec, const double* w_nodal,
                      double* qhat_out);
 /* the configuration's numerical flux; qR NULL: boundary state of type bc built
-   from qL (a wall mirrors the normal momentum; transmissive copies qL: in a
-   sweep the transmissive outer state is the element average instead, R15) */
+   from qL (a wall mirrors the normal momentum, a moving wall the normal
+   momentum relative to the wall; transmissive copies qL: in a sweep the
+   transmissive outer state is the element average instead, R15) */
 int oc_flux_debug(const oc_ctx* c, const double* qL, const double* qR, const double* n3,
                   int bc, double* out);
 int oc_eval_qh(const oc_ctx* c, const double* qhat, int64_t npts, const double* pts, double* out);

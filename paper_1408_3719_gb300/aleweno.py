@@ -37,7 +37,8 @@ class AwConfig(C.Structure):
     _fields_ = [("order_M", C.c_int), ("gamma", C.c_double), ("cfl", C.c_double),
                 ("time_quantum_log2", C.c_int), ("t_end", C.c_double), ("gts", C.c_int),
                 ("predictor_iters", C.c_int), ("mesh_velocity", C.c_int), ("cuda_stream", C.c_void_p),
-                ("flux", C.c_int)]
+                ("flux", C.c_int), ("wall_u", C.c_double), ("wall_v", C.c_double),
+                ("t_switch", C.c_double), ("cfl_start", C.c_double)]
 
 
 class AwError(RuntimeError):
@@ -135,10 +136,12 @@ class Solver:
     """One GPU context: mesh, LTS state and configuration."""
 
     def __init__(self, order_M=1, gamma=1.4, cfl=0.5, t_end=0.2, time_quantum_log2=20, gts=False,
-                 predictor_iters=0, eulerian=False, stream=None, flux="rusanov"):
+                 predictor_iters=0, eulerian=False, stream=None, flux="rusanov", wall_velocity=(0.0, 0.0),
+                 t_switch=0.0, cfl_start=0.0):
         self.lib = load()
         cfg = AwConfig(order_M, gamma, cfl, time_quantum_log2, t_end, int(gts), predictor_iters, int(eulerian),
-                       stream, {"rusanov": 0, "osher": 1}[flux])
+                       stream, {"rusanov": 0, "osher": 1}[flux], float(wall_velocity[0]), float(wall_velocity[1]),
+                       float(t_switch), float(cfl_start))
         h = C.c_void_p()
         rc = self.lib.aw_create(C.byref(cfg), C.byref(h))
         if rc:

@@ -24,6 +24,7 @@ struct aw_ctx {
   bool own_stream = false;
   int nsm = 0;
   bool have_mesh = false, have_state = false, failed = false;
+  bool moving_wall = false;  // the mesh has a moving slip wall (tag 2)
   std::vector<void*> allocs;
   Counters* hcnt = nullptr;  // pinned mirror of the device counters
   bool prof = false;         // per-kernel CUDA-event timing of sweeps
@@ -167,6 +168,15 @@ int build_tab(aw_ctx* c) {
   T.gts = c->cfg.gts ? 1 : 0;
   T.nit = c->cfg.predictor_iters > 0 ? c->cfg.predictor_iters : M + 1;
   T.flux = c->cfg.flux;
+  T.wall_u = c->cfg.wall_u;
+  T.wall_v = c->cfg.wall_v;
+  T.wall_speed = std::sqrt(c->cfg.wall_u * c->cfg.wall_u + c->cfg.wall_v * c->cfg.wall_v);
+  T.cfl_start = c->cfg.cfl_start;
+  T.Tsw = 0;
+  if (c->cfg.t_switch > 0.0) {
+    const double r = std::floor(c->cfg.t_switch / T.tick);
+    T.Tsw = r >= (double)T.T ? T.T : (long long)r;
+  }
   const int Mc = T.Mc, Nt = T.Nt;
   // lattice nodes: rows of constant eta, xi fastest
   int s = 0;
@@ -473,6 +483,10 @@ int preprocess(aw_ctx* c, HostMesh& m, const double* xy, int ne_s, int M) {
       }
     }
   }
+  // nodes of moving walls move with the wall
+  for (int ed = 0; ed < m.ned; ++ed)
+    if (m.edge_bc[ed] == 2)
+      for (int q = 0; q < 2; ++q) m.node_type[m.edge_nodes[2 * ed + q]] = 3;
   // stencils: candidates within vertex-neighbour layers, ordered by centroid distance then index
   m.sten.assign((size_t)ne * kNSten * ne_s, 0);
   m.sten_ok.assign((size_t)ne * kNSten, 0);
@@ -793,7 +807,7 @@ int aw_create(const aw_config* cfg, aw_ctx** out) {
   *out = nullptr;
   if (cfg->order_M < 1 || cfg->order_M > kMaxM || !(cfg->t_end > 0) || cfg->time_quantum_log2 < 1 ||
       cfg->time_quantum_log2 > 50 || !(cfg->cfl > 0) || !(cfg->gamma > 1) || cfg->mesh_velocity < 0 ||
-      cfg->mesh_velocity > 1 || cfg->flux < 0 || cfg->flux > 1)
+      cfg->mesh_velocity > 1 || cfg->flux < 0 || cfg->flux > 1 || (cfg->t_switch > 0.0 && !(cfg->cfl_start > 0)))
     return AW_ERR_INVALID_ARG;
   aw_ctx* c = new aw_ctx();
   c->cfg = *cfg;
@@ -849,6 +863,11 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
     return set_err(c, AW_ERR_CUDA, "copying the mesh arrays failed");
   for (int v : m.tri)
     if (v < 0 || v >= n_nodes) return set_err(c, AW_ERR_BAD_MESH, "node index out of range");
+  c->moving_wall = false;
+  for (signed char b : m.bc) {
+    if (b < -1 || b > 2) return set_err(c, AW_ERR_BAD_MESH, "boundary tag out of range");
+    c->moving_wall |= b == 2;
+  }
   if (period) {
     m.periodic = true;
     m.shift.resize(6 * n_tris);
@@ -927,6 +946,7 @@ int aw_load_batch(aw_ctx* c, int n_inst, const int64_t* node_offsets, const int6
   if (!c) return AW_ERR_INVALID_ARG;
   if (n_inst < 1 || !node_offsets || !tri_offsets || !t_end || !xy || !tri || !bc)
     return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: null arrays or no instance");
+  if (c->tab.Tsw > 0) return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: no global-step start-up in a batch");
   std::vector<int64_t> no(node_offsets, node_offsets + n_inst + 1), to(tri_offsets, tri_offsets + n_inst + 1);
   if (no[0] != 0 || to[0] != 0) return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: offsets must start at 0");
   for (int k = 0; k < n_inst; ++k)
@@ -1322,6 +1342,8 @@ int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
   if (!c->fresh) return set_err(c, AW_ERR_STATE, "aw_adjoint_forward starts from a state just loaded");
   if (c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint is for local time stepping");
   if (c->cfg.flux != 0) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers the Rusanov-type flux");
+  if (c->tab.Tsw > 0 || c->moving_wall)
+    return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers neither moving walls nor the global-step start-up");
   CK(cudaStreamSynchronize(c->stream));
   for (void* p : c->adj_allocs) cudaFree(p);
   c->adj_allocs.clear();

@@ -25,6 +25,9 @@ struct Tab {
   int gts;              // global time step
   int nit;              // Picard iterations
   int flux;             // 0 Rusanov-type, 1 Osher-type ALE flux
+  double wall_u, wall_v, wall_speed;  // moving slip walls (boundary tag 2)
+  long long Tsw;        // ticks of the global-step start-up (0: none)
+  double cfl_start;     // its CFL number
   double lat[kMaxMc][2];
   int vnode[3];
   double Dxi[kMaxMc][kMaxMc], Deta[kMaxMc][kMaxMc];

@@ -204,6 +204,10 @@ __global__ void k_nodes_grp(Tab T, Dev d) {
         D1 -= dn * ny;
       } else if (ty == 2) {
         D0 = D1 = 0.0;
+      } else if (ty == 3) {  // moves with the wall
+        const double span = (double)(d.ntn[n] - d.nt[n]) * d.etick[d.v2e[d.v2e_ptr[n]]];
+        D0 = T.wall_u * span;
+        D1 = T.wall_v * span;
       }
       d.nXn[2 * n] = d.nX[2 * n] + D0;
       d.nXn[2 * n + 1] = d.nX[2 * n + 1] + D1;
@@ -398,12 +402,17 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = qm[v];
-        if (d.edge_bc[ed] == 0) {
+        const int bc = d.edge_bc[ed];
+        if (bc == 0 || bc == 2) {  // mirror the normal momentum relative to the wall
+          const double wu = bc == 2 ? T.wall_u : 0.0, wv = bc == 2 ? T.wall_v : 0.0;
           const double nn = n[0] * n[0] + n[1] * n[1];
           if (nn > 0.0) {
-            const double mn = (qm[1] * n[0] + qm[2] * n[1]) / nn;
+            const double mn = ((qm[1] - qm[0] * wu) * n[0] + (qm[2] - qm[0] * wv) * n[1]) / nn;
             qp[1] = qm[1] - 2.0 * mn * n[0];
             qp[2] = qm[2] - 2.0 * mn * n[1];
+            // same internal energy: a moving wall's mirror changes the kinetic energy
+            if (bc == 2)
+              qp[3] = qm[3] + 0.5 * (qp[1] * qp[1] + qp[2] * qp[2] - qm[1] * qm[1] - qm[2] * qm[2]) / qm[0];
           }
         }
       }
@@ -665,7 +674,7 @@ __global__ void __launch_bounds__(TH) k_predict_coop(Tab T, Dev d, int initial, 
     if (live && l == 0) {
       const int i = initial ? pos : d.ready_list[pos];
       long long dtk = d.dt[i];
-      if (gts && dtk > 0) {
+      if ((gts || d.t[i] < T.Tsw) && dtk > 0) {
         dtk = gmin;
         d.dt[i] = dtk;
       }
@@ -1004,8 +1013,12 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
           }
           const double dd = 4.0 * area6(Xv) / per;
           const double uu = Qv[1] / Qv[0], vv = Qv[2] / Qv[0];
-          const double lam = sqrt(uu * uu + vv * vv) + sqrt(T.gamma * pressure(T, Qv) / Qv[0]);
-          dtc = T.cfl * dd / lam;
+          double vel = sqrt(uu * uu + vv * vv);
+          if (k == 0)  // an element on a moving wall counts the wall's speed
+            for (int e2 = 0; e2 < 3; ++e2)
+              if (d.edge_bc[d.elem_edge[3 * (size_t)i + e2]] == 2) vel = fmax(vel, T.wall_speed);
+          const double lam = vel + sqrt(T.gamma * pressure(T, Qv) / Qv[0]);
+          dtc = (ti < T.Tsw ? T.cfl_start : T.cfl) * dd / lam;
           if (!(dtc > 0.0)) dtc = -1.0;
         }
         sDt[e * 4 + k] = dtc;
@@ -1213,9 +1226,11 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
             best = d.etick[i];
           }
           const double rt = floor(best / d.etick[i]);
-          tks = rt > (double)(T.T - ti) ? T.T - ti : (long long)rt;
+          const bool start = ti < T.Tsw;  // global-step start-up
+          const long long end = start ? T.Tsw : T.T;
+          tks = rt > (double)(end - ti) ? end - ti : (long long)rt;
           if (tks < 1) tks = 1;
-          atomicMin(&d.cnt->gts_min, tks);
+          if (T.gts || start) atomicMin(&d.cnt->gts_min, tks);
         }
         if (d.sched_mode) {  // frozen schedule: record or replay this update's step
           const long long ci = d.count[i];

@@ -12,6 +12,7 @@ The paper's own set-ups (third order = P2, Osher-type flux, LTS and GTS):
     python -m paper_1408_3719_gb300.runs rp --problem RP1|RP2 [--gts]
     python -m paper_1408_3719_gb300.runs ep --problem EP1|EP2 [--gts] [--t-end 0.2]
     python -m paper_1408_3719_gb300.runs table
+    python -m paper_1408_3719_gb300.runs saltzman [--gts]   (Rusanov-type flux, Sec. 3.5)
 
 ``table`` runs RP1, RP2, EP1 and EP2 with both time-stepping modes and prints
 the update counts beside those of Tables tab.RPdata and tab.EPdata.
@@ -163,6 +164,26 @@ def explosion_paper(case="EP1", order=2, gts=False, flux="osher", t_end=None, n_
     return info
 
 
+def saltzman(order=2, gts=False, flux="rusanov", t_end=0.6):
+    """The Saltzman piston of Sec. 3.5: third order, Rusanov-type flux, global
+    steps with CFL 0.1 until t = 0.01, then local (or global) steps with CFL
+    0.5; density and velocity L1 errors against the exact piston shock."""
+    mesh, Q = W.saltzman()
+    g = 5.0 / 3.0
+    e, info = _run(mesh, Q, order_M=order, gamma=g, t_end=t_end, gts=gts, flux=flux, wall_velocity=(1.0, 0.0),
+                   t_switch=0.01, cfl_start=0.1)
+    A = _areas(e["X"])
+    cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
+    s, rho1, _ = W.piston_shock()
+    behind = cx < s * t_end
+    rho_ex = np.where(behind, rho1, 1.0)
+    u_ex = np.where(behind, 1.0, 0.0)
+    q = e["Q"]
+    info.update(config="Saltzman", t_end=t_end, l1_rho=float(np.sum(np.abs(q[:, 0] - rho_ex) * A) / A.sum()),
+                l1_u=float(np.sum(np.abs(q[:, 1] / q[:, 0] - u_ex) * A) / A.sum()), shock_x=float(s * t_end))
+    return info
+
+
 def table(order=2, flux="osher"):
     """GTS and LTS update counts of RP1, RP2, EP1, EP2 beside the paper's."""
     out = []
@@ -189,7 +210,7 @@ def table(order=2, flux="osher"):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sod", "vortex", "explosion", "rp", "ep", "table"])
+    ap.add_argument("case", choices=["sod", "vortex", "explosion", "rp", "ep", "table", "saltzman"])
     ap.add_argument("--problem", default=None, help="RP1 | RP2 (rp), EP1 | EP2 (ep)")
     ap.add_argument("--t-end", type=float, default=None)
     ap.add_argument("--order", type=int, default=None)
@@ -202,7 +223,12 @@ def main():
     aleweno.load()
     paper = a.case in ("rp", "ep", "table")
     flux = a.flux or ("osher" if paper else "rusanov")
-    if a.case == "rp":
+    if a.case == "saltzman":
+        try:
+            print(json.dumps(saltzman(a.order or 2, a.gts, a.flux or "rusanov", a.t_end or 0.6)), flush=True)
+        except RuntimeError as err:
+            print(json.dumps(dict(config="Saltzman", gts=a.gts, failed=str(err)[:600])), flush=True)
+    elif a.case == "rp":
         print(json.dumps(riemann(a.problem or "RP1", a.order or 2, a.gts, flux)), flush=True)
     elif a.case == "ep":
         print(json.dumps(explosion_paper(a.problem or "EP1", a.order or 2, a.gts, flux, a.t_end)), flush=True)

@@ -436,6 +436,41 @@ def explosion_problem(case="EP1", scale=0.86, seed=SEED_BASE + 5, gamma=1.4):
     return mesh, q, t_end
 
 
+BC_MOVING_WALL = 2
+
+
+def saltzman(nx=100, ny=10, gamma=5.0 / 3.0, e0=1e-4):
+    """The Saltzman piston problem of Sec. 3.5: 100 x 10 squares on
+    [0, 1] x [0, 0.1], each split into two right triangles, skewed by
+    x' = x + (0.1 - y) sin(pi x); gas at rest with rho = 1 and internal
+    energy e0; the left side is a slip wall moving with velocity (1, 0)
+    (tag 2), the other sides fixed slip walls.  Returns (mesh, Q)."""
+    mesh = shock_tube_mesh(nx, ny, 1.0, 0.1, jitter=0.0, seed=SEED_BASE + 6)
+    xy = mesh["xy"]
+    xy[:, 0] = xy[:, 0] + (0.1 - xy[:, 1]) * np.sin(np.pi * xy[:, 0])
+    P = _corner_coords(mesh)
+    bc = mesh["bc"].copy()
+    for i, e in zip(*np.nonzero(bc == BC_WALL)):
+        a, b = P[i, e], P[i, (e + 1) % 3]
+        if abs(a[0]) < 1e-12 and abs(b[0]) < 1e-12:
+            bc[i, e] = BC_MOVING_WALL
+    assert np.all(_signed_areas(xy, mesh["tri"]) > 0)
+    mesh = dict(mesh, xy=xy, bc=bc, name=f"saltzman_{nx}x{ny}")
+    q = np.tile(prim_to_cons(1.0, 0.0, 0.0, (gamma - 1.0) * e0, gamma), (mesh["tri"].shape[0], 1))
+    return mesh, q
+
+
+def piston_shock(u_p=1.0, rho0=1.0, p0=(5.0 / 3.0 - 1.0) * 1e-4, gamma=5.0 / 3.0):
+    """Exact state behind the shock driven by a piston of speed u_p into gas
+    at rest (Rankine-Hugoniot): returns (shock speed, rho1, p1)."""
+    c0 = math.sqrt(gamma * p0 / rho0)
+    a = 0.25 * (gamma + 1.0) * u_p
+    s = a + math.sqrt(a * a + c0 * c0)
+    rho1 = rho0 * s / (s - u_p)
+    p1 = p0 + rho0 * s * u_p
+    return s, rho1, p1
+
+
 def batched_instances(n_inst=256, lo=2000, hi=60000, seed=SEED_BASE + 3, gamma=1.4, size_scale=1.0):
     """Independent explosion / shock-tube instances with log-uniform sizes,
     density ratio U[2,10], pressure ratio U[2,20], interface U[0.3,0.6]."""

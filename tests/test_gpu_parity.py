@@ -54,6 +54,12 @@ CASES = {
     "vortex_p2_gts": (lambda: W.vortex(10), dict(order_M=2, t_end=1.0, gts=True)),
     "tube_p1_eulerian": (lambda: W.sod_tube(40, 6), dict(order_M=1, t_end=0.2, eulerian=True)),
     "rp1_periodic_y_p2": (lambda: W.riemann_problem("RP1", 40, 6, jitter=0.1)[:2], dict(order_M=2, t_end=0.2)),
+    # the Saltzman piston (Sec. 3.5), coarse: a moving slip wall and the
+    # global-step start-up with CFL 0.1 until t = 0.01, local steps after
+    "saltzman_p1": (lambda: W.saltzman(20, 4), dict(order_M=1, gamma=5.0 / 3.0, t_end=0.6, wall_velocity=(1.0, 0.0),
+                                                    t_switch=0.01, cfl_start=0.1)),
+    "saltzman_p2": (lambda: W.saltzman(20, 4), dict(order_M=2, gamma=5.0 / 3.0, t_end=0.6, wall_velocity=(1.0, 0.0),
+                                                    t_switch=0.01, cfl_start=0.1)),
 }
 
 
@@ -183,3 +189,22 @@ def test_device_pointers(aw):
     g.get_state(out)
     host = g.get_state()
     assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_moving_wall_and_start_up_guards(aw):
+    mesh, Q = W.saltzman(20, 4)
+    bad = dict(mesh)
+    bad["bc"] = mesh["bc"].copy()
+    bad["bc"][bad["bc"] == 2] = 3
+    g = aw.Solver(order_M=1, gamma=5.0 / 3.0)
+    with pytest.raises(aw.AwError) as e:
+        g.load_mesh(bad)
+    assert e.value.code == -2
+    with pytest.raises(aw.AwError):
+        aw.Solver(order_M=1, t_switch=0.01, cfl_start=0.0)
+    s = aw.Solver(order_M=2, gamma=5.0 / 3.0, t_end=0.6, wall_velocity=(1.0, 0.0))
+    s.load_mesh(mesh)
+    s.load_state(Q)
+    with pytest.raises(aw.AwError) as e:
+        s.adjoint_forward(2, 1)
+    assert e.value.code == -1
