@@ -68,6 +68,9 @@ typedef struct {
                              steps computed with CFL cfl_start, clipped at t_switch; local steps after
                              (the start of the Saltzman run, Sec. 3.5); 0: none */
   double cfl_start;
+  double kidder[5];       /* r_i0, r_e0, rho_i0, rho_e0, s0 of the isentropic compression of Sec. 3.4
+                             (eqs. KidderIC, KidderEx): edges tagged 3 take its exact state at each
+                             quadrature point's position and time as outer state */
 } aw_config;
 
 /* Create a context (Sec. 2.1 set-up).  INVALID_ARG on an unsupported config. */
@@ -80,7 +83,8 @@ const char* aw_last_error(const aw_ctx* ctx);
  * reconstruction stencils per element and the symmetric total stencil S^W
  * (eq. WENOstencil).  tri: [n_tris][3] counter-clockwise node indices;
  * bc: [n_tris][3] tag of local edge e = (v_e, v_{e+1 mod 3}): -1 interior,
- * 0 slip wall, 1 transmissive, 2 slip wall moving with (wall_u, wall_v); shift: [n_tris][3][2] int8 periodic image of
+ * 0 slip wall, 1 transmissive, 2 slip wall moving with (wall_u, wall_v),
+ * 3 the exact state of the Kidder compression (cfg.kidder); shift: [n_tris][3][2] int8 periodic image of
  * each corner (corner = xy[node] + shift * period) or NULL, with period [2]
  * or NULL (both or neither); a zero period component means the mesh is not
  * periodic in that direction (the shock tubes of Sec. 3.2 are periodic in y

@@ -58,6 +58,9 @@
  *     to it relative to the wall velocity; its nodes move with the wall.
  *     Until t_switch every element takes the global minimum of the local
  *     steps computed with CFL cfl_start, clipped at t_switch (Sec. 3.5).
+ *  R17 Kidder boundary state: the outer state of a bc-3 edge is the exact
+ *     solution of Sec. 3.4 (eqs. KidderIC, KidderEx, gamma = 2) at the
+ *     quadrature point's position and time; the edges are chords of the arcs.
  *  R15 transmissive boundary state: the outer state of a transmissive edge is
  *     the boundary element's cell average at the start of the sweep (not the
  *     inner state at the quadrature point, with which a gas at rest next to
@@ -1011,6 +1014,30 @@ static void num_flux(const oc_ctx* c, const double* qm, const double* qp, const 
   else rusanov(c, qm, qp, n, F);
 }
 
+/* Exact state of the Kidder compression (Sec. 3.4) at (x, y, t): a particle
+   that starts at radius r is at h(t) r with h = sqrt(1 - t^2/tau^2); the
+   density is rho0(r)/h^2 with rho0^(gamma-1) linear in r^2 between
+   rho_i0^(gamma-1) at r_i0 and rho_e0^(gamma-1) at r_e0 (eq. KidderIC), the
+   velocity h'(t) r along the radius, the pressure s0 rho^gamma.  tau is the
+   focalisation time sqrt((gamma-1)/2 (r_e0^2 - r_i0^2)/(c_e0^2 - c_i0^2)). */
+static void kidder_state(const oc_ctx* c, double x, double y, double t, double* q) {
+  const double* k = c->cfg.kidder;
+  double g = c->cfg.gamma, ri = k[0], re = k[1], s0 = k[4];
+  double ai = pow(k[2], g - 1.0), ae = pow(k[3], g - 1.0);
+  double ci2 = g * s0 * ai, ce2 = g * s0 * ae;
+  double tau2 = 0.5 * (g - 1.0) * (re * re - ri * ri) / (ce2 - ci2);
+  double h = sqrt(1.0 - t * t / tau2), dh = -t / (tau2 * h);
+  double R = sqrt(x * x + y * y), r = R / h;
+  double w = (r * r - ri * ri) / (re * re - ri * ri);
+  double rho = pow((1.0 - w) * ai + w * ae, 1.0 / (g - 1.0)) / (h * h);
+  double u = dh / h * x, v = dh / h * y;
+  double p = s0 * pow(rho, g);
+  q[0] = rho;
+  q[1] = rho * u;
+  q[2] = rho * v;
+  q[3] = p / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
 static void boundary_state(const oc_ctx* c, int bc, const double* q, const double* n, double* qb) {
   for (int v = 0; v < 4; ++v) qb[v] = q[v];
   if (bc == 0 || bc == 2) {
@@ -1500,7 +1527,7 @@ int oc_load_mesh(oc_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, c
   c->ne_ = n_tris;
   for (int64_t q = 0; q < 3 * n_tris; ++q) {
     if (tri[q] < 0 || tri[q] >= n_nodes) return fail(c, OC_BAD_MESH, "node index out of range");
-    if (bc[q] < -1 || bc[q] > 2) return fail(c, OC_BAD_MESH, "boundary tag out of range");
+    if (bc[q] < -1 || bc[q] > 3) return fail(c, OC_BAD_MESH, "boundary tag out of range");
   }
   c->tri = (int32_t*)malloc(sizeof(int32_t) * 3 * n_tris);
   memcpy(c->tri, tri, sizeof(int32_t) * 3 * n_tris);
@@ -1724,6 +1751,11 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
         } else if (c->edge_bc[ed] == 1) {
           /* transmissive: the boundary element's sweep-start average (R15) */
           for (int v = 0; v < 4; ++v) qp[v] = c->Q[4 * L + v];
+        } else if (c->edge_bc[ed] == 3) {
+          /* the exact Kidder state at the quadrature point (R17) */
+          double px = (1 - chi) * (1 - tau) * P[0][0] + chi * (1 - tau) * P[1][0] + chi * tau * P[2][0] + (1 - chi) * tau * P[3][0];
+          double py = (1 - chi) * (1 - tau) * P[0][1] + chi * (1 - tau) * P[1][1] + chi * tau * P[2][1] + (1 - chi) * tau * P[3][1];
+          kidder_state(c, px, py, tt * c->tick, qp);
         } else {
           boundary_state(c, c->edge_bc[ed], qm, n, qp);
         }

@@ -40,6 +40,8 @@ typedef struct {
   double t_switch;      /* > 0: global steps with CFL cfl_start until t_switch, then
                            local steps (the start of the Saltzman run, Sec. 3.5) */
   double cfl_start;
+  double kidder[5];     /* r_i0, r_e0, rho_i0, rho_e0, s0: the exact isentropic
+                           compression (Sec. 3.4) whose state bc-3 edges take */
 } oc_config;
 
 int oc_create(const oc_config* cfg, oc_ctx** out);

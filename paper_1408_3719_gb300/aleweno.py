@@ -38,7 +38,7 @@ class AwConfig(C.Structure):
                 ("time_quantum_log2", C.c_int), ("t_end", C.c_double), ("gts", C.c_int),
                 ("predictor_iters", C.c_int), ("mesh_velocity", C.c_int), ("cuda_stream", C.c_void_p),
                 ("flux", C.c_int), ("wall_u", C.c_double), ("wall_v", C.c_double),
-                ("t_switch", C.c_double), ("cfl_start", C.c_double)]
+                ("t_switch", C.c_double), ("cfl_start", C.c_double), ("kidder", C.c_double * 5)]
 
 
 class AwError(RuntimeError):
@@ -137,11 +137,11 @@ class Solver:
 
     def __init__(self, order_M=1, gamma=1.4, cfl=0.5, t_end=0.2, time_quantum_log2=20, gts=False,
                  predictor_iters=0, eulerian=False, stream=None, flux="rusanov", wall_velocity=(0.0, 0.0),
-                 t_switch=0.0, cfl_start=0.0):
+                 t_switch=0.0, cfl_start=0.0, kidder=(0.9, 1.0, 1.0, 2.0, 1.0)):
         self.lib = load()
         cfg = AwConfig(order_M, gamma, cfl, time_quantum_log2, t_end, int(gts), predictor_iters, int(eulerian),
                        stream, {"rusanov": 0, "osher": 1}[flux], float(wall_velocity[0]), float(wall_velocity[1]),
-                       float(t_switch), float(cfl_start))
+                       float(t_switch), float(cfl_start), (C.c_double * 5)(*[float(v) for v in kidder]))
         h = C.c_void_p()
         rc = self.lib.aw_create(C.byref(cfg), C.byref(h))
         if rc:

@@ -24,7 +24,7 @@ struct aw_ctx {
   bool own_stream = false;
   int nsm = 0;
   bool have_mesh = false, have_state = false, failed = false;
-  bool moving_wall = false;  // the mesh has a moving slip wall (tag 2)
+  bool moving_wall = false;  // the mesh has a moving slip wall or a Kidder boundary (tags 2, 3)
   std::vector<void*> allocs;
   Counters* hcnt = nullptr;  // pinned mirror of the device counters
   bool prof = false;         // per-kernel CUDA-event timing of sweeps
@@ -172,6 +172,7 @@ int build_tab(aw_ctx* c) {
   T.wall_v = c->cfg.wall_v;
   T.wall_speed = std::sqrt(c->cfg.wall_u * c->cfg.wall_u + c->cfg.wall_v * c->cfg.wall_v);
   T.cfl_start = c->cfg.cfl_start;
+  for (int k = 0; k < 5; ++k) T.kidder[k] = c->cfg.kidder[k];
   T.Tsw = 0;
   if (c->cfg.t_switch > 0.0) {
     const double r = std::floor(c->cfg.t_switch / T.tick);
@@ -865,8 +866,8 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
     if (v < 0 || v >= n_nodes) return set_err(c, AW_ERR_BAD_MESH, "node index out of range");
   c->moving_wall = false;
   for (signed char b : m.bc) {
-    if (b < -1 || b > 2) return set_err(c, AW_ERR_BAD_MESH, "boundary tag out of range");
-    c->moving_wall |= b == 2;
+    if (b < -1 || b > 3) return set_err(c, AW_ERR_BAD_MESH, "boundary tag out of range");
+    c->moving_wall |= b == 2 || b == 3;
   }
   if (period) {
     m.periodic = true;
@@ -1343,7 +1344,7 @@ int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
   if (c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint is for local time stepping");
   if (c->cfg.flux != 0) return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers the Rusanov-type flux");
   if (c->tab.Tsw > 0 || c->moving_wall)
-    return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers neither moving walls nor the global-step start-up");
+    return set_err(c, AW_ERR_INVALID_ARG, "the adjoint covers neither moving walls, Kidder boundaries nor the global-step start-up");
   CK(cudaStreamSynchronize(c->stream));
   for (void* p : c->adj_allocs) cudaFree(p);
   c->adj_allocs.clear();

@@ -28,6 +28,7 @@ struct Tab {
   double wall_u, wall_v, wall_speed;  // moving slip walls (boundary tag 2)
   long long Tsw;        // ticks of the global-step start-up (0: none)
   double cfl_start;     // its CFL number
+  double kidder[5];     // r_i0, r_e0, rho_i0, rho_e0, s0 of the Kidder state (boundary tag 3)
   double lat[kMaxMc][2];
   int vnode[3];
   double Dxi[kMaxMc][kMaxMc], Deta[kMaxMc][kMaxMc];

@@ -238,6 +238,28 @@ __global__ void k_edges(Dev d) {
   }
 }
 
+// Exact state of the Kidder compression (Sec. 3.4, eqs. KidderIC, KidderEx)
+// at (x, y, t): a particle starting at radius r sits at h(t) r with
+// h = sqrt(1 - t^2/tau^2); density rho0(r)/h^2 with rho0^(gamma-1) linear in
+// r^2 between the two frontiers, radial velocity h' r, pressure s0 rho^gamma;
+// tau = sqrt((gamma-1)/2 (r_e0^2 - r_i0^2)/(c_e0^2 - c_i0^2)).
+__device__ void kidder_state(const Tab& T, double x, double y, double t, double* q) {
+  const double g = T.gamma, ri = T.kidder[0], re = T.kidder[1], s0 = T.kidder[4];
+  const double ai = pow(T.kidder[2], g - 1.0), ae = pow(T.kidder[3], g - 1.0);
+  const double ci2 = g * s0 * ai, ce2 = g * s0 * ae;
+  const double tau2 = 0.5 * (g - 1.0) * (re * re - ri * ri) / (ce2 - ci2);
+  const double h = sqrt(1.0 - t * t / tau2), dh = -t / (tau2 * h);
+  const double R = sqrt(x * x + y * y), r = R / h;
+  const double w = (r * r - ri * ri) / (re * re - ri * ri);
+  const double rho = pow((1.0 - w) * ai + w * ae, 1.0 / (g - 1.0)) / (h * h);
+  const double u = dh / h * x, v = dh / h * y;
+  const double p = s0 * pow(rho, g);
+  q[0] = rho;
+  q[1] = rho * u;
+  q[2] = rho * v;
+  q[3] = p / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
 // Rusanov-type ALE flux through the area-weighted space-time normal n
 // (eq. rusanov): the largest |eigenvalue| of A_n^V times |n_xy| is
 // |v.n_xy + n_t| + c |n_xy|.
@@ -399,6 +421,13 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
         // which a gas at rest beside the boundary grows from roundoff
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = d.Q[4 * (size_t)L + v];
+      } else if (d.edge_bc[ed] == 3) {
+        // the exact Kidder state at the quadrature point
+        const double px = (1 - chi) * (1 - tau) * P[0][0] + chi * (1 - tau) * P[1][0] + chi * tau * P[2][0] +
+                          (1 - chi) * tau * P[3][0];
+        const double py = (1 - chi) * (1 - tau) * P[0][1] + chi * (1 - tau) * P[1][1] + chi * tau * P[2][1] +
+                          (1 - chi) * tau * P[3][1];
+        kidder_state(T, px, py, tt * d.etick[L], qp);
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = qm[v];

@@ -13,6 +13,7 @@ The paper's own set-ups (third order = P2, Osher-type flux, LTS and GTS):
     python -m paper_1408_3719_gb300.runs ep --problem EP1|EP2 [--gts] [--t-end 0.2]
     python -m paper_1408_3719_gb300.runs table
     python -m paper_1408_3719_gb300.runs saltzman [--gts]   (Rusanov-type flux, Sec. 3.5)
+    python -m paper_1408_3719_gb300.runs kidder [--gts]     (fourth order, Sec. 3.4)
 
 ``table`` runs RP1, RP2, EP1 and EP2 with both time-stepping modes and prints
 the update counts beside those of Tables tab.RPdata and tab.EPdata.
@@ -184,6 +185,37 @@ def saltzman(order=2, gts=False, flux="rusanov", t_end=0.6):
     return info
 
 
+# Table tab.Kidder: frontier radii at t_f (fourth order, Osher-type flux)
+PAPER_KIDDER = {"inner": (0.45, 0.44996063, 3.94e-05), "outer": (0.5, 0.49930053, 6.99e-04)}
+
+
+def kidder(order=3, gts=False, flux="osher", nr=10, nth=120):
+    """The Kidder compression of Sec. 3.4 to t_f = sqrt(3)/2 tau: the radii of
+    the inner and outer frontier (mean over their nodes) against the exact
+    0.45 and 0.5, and the density's L1 error against the exact solution."""
+    mesh, Q, tf = W.kidder(nr, nth)
+    s = aleweno.Solver(order_M=order, gamma=2.0, t_end=tf, gts=gts, flux=flux)
+    s.load_mesh(mesh)
+    s.load_state(Q)
+    t0 = time.perf_counter()
+    sweeps, updates = s.advance()
+    run_s = time.perf_counter() - t0
+    X, _ = s.get_nodes()
+    e = s.get_elem()
+    s.close()
+    r0 = np.hypot(*mesh["xy"].T)
+    rn = np.hypot(*X.T)
+    r_in, r_out = float(rn[np.abs(r0 - 0.9) < 1e-12].mean()), float(rn[np.abs(r0 - 1.0) < 1e-12].mean())
+    A = _areas(e["X"])
+    c = e["X"].reshape(-1, 3, 2).mean(1)
+    rho_ex = W.kidder_prim(c[:, 0], c[:, 1], tf)[0]
+    return dict(config="Kidder", n_tris=int(mesh["tri"].shape[0]), order_M=order, gts=gts, flux=flux, t_end=tf,
+                sweeps=sweeps, updates=updates, run_s=run_s, r_inner=r_in, r_outer=r_out,
+                err_inner=abs(r_in - 0.45), err_outer=abs(r_out - 0.5),
+                l1_rho_rel=float(np.sum(np.abs(e["Q"][:, 0] - rho_ex) * A) / np.sum(rho_ex * A)),
+                paper=PAPER_KIDDER)
+
+
 def table(order=2, flux="osher"):
     """GTS and LTS update counts of RP1, RP2, EP1, EP2 beside the paper's."""
     out = []
@@ -210,7 +242,7 @@ def table(order=2, flux="osher"):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sod", "vortex", "explosion", "rp", "ep", "table", "saltzman"])
+    ap.add_argument("case", choices=["sod", "vortex", "explosion", "rp", "ep", "table", "saltzman", "kidder"])
     ap.add_argument("--problem", default=None, help="RP1 | RP2 (rp), EP1 | EP2 (ep)")
     ap.add_argument("--t-end", type=float, default=None)
     ap.add_argument("--order", type=int, default=None)
@@ -223,7 +255,9 @@ def main():
     aleweno.load()
     paper = a.case in ("rp", "ep", "table")
     flux = a.flux or ("osher" if paper else "rusanov")
-    if a.case == "saltzman":
+    if a.case == "kidder":
+        print(json.dumps(kidder(a.order or 3, a.gts, a.flux or "osher")), flush=True)
+    elif a.case == "saltzman":
         try:
             print(json.dumps(saltzman(a.order or 2, a.gts, a.flux or "rusanov", a.t_end or 0.6)), flush=True)
         except RuntimeError as err:

@@ -471,6 +471,67 @@ def piston_shock(u_p=1.0, rho0=1.0, p0=(5.0 / 3.0 - 1.0) * 1e-4, gamma=5.0 / 3.0
     return s, rho1, p1
 
 
+BC_KIDDER = 3
+KIDDER = (0.9, 1.0, 1.0, 2.0, 1.0)  # r_i0, r_e0, rho_i0, rho_e0, s0 (Sec. 3.4), gamma = 2
+
+
+def kidder_tau(kidder=KIDDER, gamma=2.0):
+    """Focalisation time of the Kidder compression (Sec. 3.4)."""
+    ri, re, rhoi, rhoe, s0 = kidder
+    ci2, ce2 = gamma * s0 * rhoi ** (gamma - 1.0), gamma * s0 * rhoe ** (gamma - 1.0)
+    return math.sqrt(0.5 * (gamma - 1.0) * (re * re - ri * ri) / (ce2 - ci2))
+
+
+def kidder_prim(x, y, t, kidder=KIDDER, gamma=2.0):
+    """Exact primitive state (rho, u, v, p) of the Kidder compression at
+    (x, y, t) (eqs. KidderIC, KidderEx): homothety h(t) = sqrt(1 - t^2/tau^2),
+    density rho0(R/h)/h^2, radial velocity h' R/h, pressure s0 rho^gamma."""
+    ri, re, rhoi, rhoe, s0 = kidder
+    tau = kidder_tau(kidder, gamma)
+    h = math.sqrt(1.0 - t * t / (tau * tau))
+    dh = -t / (tau * tau * h)
+    r = np.hypot(x, y) / h
+    w = (r * r - ri * ri) / (re * re - ri * ri)
+    rho = ((1.0 - w) * rhoi ** (gamma - 1.0) + w * rhoe ** (gamma - 1.0)) ** (1.0 / (gamma - 1.0)) / (h * h)
+    return rho, dh / h * x, dh / h * y, s0 * rho ** gamma
+
+
+def kidder(nr=10, nth=120, kidder=KIDDER, gamma=2.0):
+    """The Kidder problem of Sec. 3.4: the quarter shell r_i0 <= r <= r_e0,
+    0 <= theta <= pi/2 on an nr x nth polar grid (each cell split along its
+    shorter diagonal), slip walls on the two straight sides, the exact state
+    (tag 3) on the two arcs; cell averages of the exact state at t = 0.
+    Returns (mesh, Q, t_f) with t_f = sqrt(3)/2 tau, where h(t_f) = 1/2."""
+    ri, re = kidder[0], kidder[1]
+    rr = np.linspace(ri, re, nr + 1)
+    th = np.linspace(0.0, 0.5 * math.pi, nth + 1)
+    R, TH = np.meshgrid(rr, th, indexing="ij")
+    xy = np.stack([R * np.cos(TH), R * np.sin(TH)], axis=-1).reshape(-1, 2)
+    xy[np.abs(xy) < 1e-15] = 0.0
+    node = lambda i, j: i * (nth + 1) + j
+    tris = []
+    for i in range(nr):
+        for j in range(nth):
+            a, b, c, d = node(i, j), node(i + 1, j), node(i + 1, j + 1), node(i, j + 1)
+            if np.sum((xy[a] - xy[c]) ** 2) <= np.sum((xy[b] - xy[d]) ** 2):
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    tri = np.asarray(tris, dtype=np.int32)
+    assert np.all(_signed_areas(xy, tri) > 0)
+    bnd = _boundary_edges(tri)
+    bc = np.full(tri.shape, BC_INTERIOR, dtype=np.int8)
+    P = xy[tri]
+    for i, e in zip(*np.nonzero(bnd)):
+        a, b = P[i, e], P[i, (e + 1) % 3]
+        ra, rb = np.hypot(*a), np.hypot(*b)
+        arc = (abs(ra - ri) < 1e-12 and abs(rb - ri) < 1e-12) or (abs(ra - re) < 1e-12 and abs(rb - re) < 1e-12)
+        bc[i, e] = BC_KIDDER if arc else BC_WALL
+    mesh = dict(xy=xy, tri=tri, bc=bc, shift=None, period=None, name=f"kidder_{nr}x{nth}")
+    q = cell_average(mesh, lambda x, y: prim_to_cons(*kidder_prim(x, y, 0.0, kidder, gamma), gamma), _duffy_rule(8))
+    return mesh, q, 0.5 * math.sqrt(3.0) * kidder_tau(kidder, gamma)
+
+
 def batched_instances(n_inst=256, lo=2000, hi=60000, seed=SEED_BASE + 3, gamma=1.4, size_scale=1.0):
     """Independent explosion / shock-tube instances with log-uniform sizes,
     density ratio U[2,10], pressure ratio U[2,20], interface U[0.3,0.6]."""

@@ -38,6 +38,8 @@ CASES = {
     "rp2_periodic_y_p2": (lambda: W.riemann_problem("RP2", 40, 6, jitter=0.1)[:2], dict(order_M=2, t_end=0.1)),
     "ep2_p2": (lambda: W.explosion(0.04, inner=(1, 0, 0, 1000), outer=(1, 0, 0, 0.01)),
                dict(order_M=2, t_end=0.012)),
+    # the Kidder compression at the paper's fourth order (Sec. 3.4)
+    "kidder_p3": (lambda: W.kidder(5, 40)[:2], dict(order_M=3, gamma=2.0, t_end=0.5 * 3 ** 0.5 * W.kidder_tau())),
 }
 
 

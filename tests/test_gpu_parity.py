@@ -60,6 +60,8 @@ CASES = {
                                                     t_switch=0.01, cfl_start=0.1)),
     "saltzman_p2": (lambda: W.saltzman(20, 4), dict(order_M=2, gamma=5.0 / 3.0, t_end=0.6, wall_velocity=(1.0, 0.0),
                                                     t_switch=0.01, cfl_start=0.1)),
+    # the Kidder compression (Sec. 3.4): exact state on the two arcs
+    "kidder_p2": (lambda: W.kidder(5, 40)[:2], dict(order_M=2, gamma=2.0, t_end=0.5 * 3 ** 0.5 * W.kidder_tau())),
 }
 
 
