@@ -197,7 +197,7 @@ def test_moving_wall_and_start_up_guards(aw):
     mesh, Q = W.saltzman(20, 4)
     bad = dict(mesh)
     bad["bc"] = mesh["bc"].copy()
-    bad["bc"][bad["bc"] == 2] = 3
+    bad["bc"][bad["bc"] == 2] = 4
     g = aw.Solver(order_M=1, gamma=5.0 / 3.0)
     with pytest.raises(aw.AwError) as e:
         g.load_mesh(bad)
