@@ -27,7 +27,7 @@ def _need_gpu():
     return aleweno
 
 
-class GpuRun:
+class GpuCase:
     """One GPU context with a recorded base run and its adjoint gradient."""
 
     def __init__(self, aleweno, mesh, Q0, order, n_sweeps, ckpt=10, mask=None):
@@ -66,7 +66,7 @@ class GpuRun:
 def test_adjoint_matches_gpu_central_differences(order, n_sweeps, kind):
     aleweno = _need_gpu()
     mesh, Q0 = wavy_vortex(14)
-    run = GpuRun(aleweno, mesh, Q0, order, n_sweeps)
+    run = GpuCase(aleweno, mesh, Q0, order, n_sweeps)
     rng = np.random.default_rng(100 + 10 * order + n_sweeps)
     for _ in range(3):
         vQ, vxy = _direction(rng, Q0, run.xy0, kind)
@@ -99,7 +99,7 @@ def test_adjoint_through_transmissive_boundaries(order):
     average: its adjoint goes to that average."""
     aleweno = _need_gpu()
     mesh, Q0 = _wavy_tube()
-    run = GpuRun(aleweno, mesh, Q0, order, 12, 5, mask=np.ones(mesh["tri"].shape[0]))
+    run = GpuCase(aleweno, mesh, Q0, order, 12, 5, mask=np.ones(mesh["tri"].shape[0]))
     rng = np.random.default_rng(300 + order)
     for kind in ("Q", "xy", "both"):
         vQ, vxy = _direction(rng, Q0, run.xy0, kind)
@@ -167,7 +167,7 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     mesh, Q0 = W.vortex(12)
     ref = None
     for ck in (1, 4, 25):
-        run = GpuRun(aleweno, mesh, Q0, 2, 25, ck)
+        run = GpuCase(aleweno, mesh, Q0, 2, 25, ck)
         g = np.concatenate([run.gQ0.ravel(), run.gxy0.ravel()])
         if ref is None:
             ref = g
@@ -187,7 +187,7 @@ def test_autograd_function_gives_the_adjoint_gradient():
     Q, X = LtsRun.apply(Qt, xyt, s, 10, 5)
     J = kinetic_energy(Q, X, mask)
     J.backward()
-    run = GpuRun(aleweno, mesh, Q0, 2, 10, 5)
+    run = GpuCase(aleweno, mesh, Q0, 2, 10, 5)
     assert abs(J.item() - run.J0) <= 1e-14 * abs(run.J0)
     assert np.abs(Qt.grad.cpu().numpy() - run.gQ0).max() <= 1e-12 * np.abs(run.gQ0).max()
     assert np.abs(xyt.grad.cpu().numpy() - run.gxy0).max() <= 1e-12 * np.abs(run.gxy0).max()
@@ -196,7 +196,7 @@ def test_autograd_function_gives_the_adjoint_gradient():
 def _against_oracle(mesh, Q0, n_sweeps, n_dirs, workers):
     aleweno = _need_gpu()
     n_vortex = mesh["tri"].shape[0]
-    run = GpuRun(aleweno, mesh, Q0, 2, n_sweeps, 10)
+    run = GpuCase(aleweno, mesh, Q0, 2, n_sweeps, 10)
     rng = np.random.default_rng(2024 + n_vortex)
     dirs = [_direction(rng, Q0, run.xy0, ("Q", "xy", "both")[k % 3]) for k in range(n_dirs)]
     ctx = mp.get_context("spawn")

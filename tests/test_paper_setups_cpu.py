@@ -18,7 +18,7 @@ def test_riemann_problem_mesh_matches_the_paper_set_up():
     mesh, Q, t_end = W.riemann_problem("RP2")
     assert mesh["tri"].shape[0] == 8862 and t_end == 0.1
     P = W._corner_coords(mesh)
-    assert abs(_areas(P).sum() - 0.1) < 1e-12  # the box, tiled exactly
+    assert abs(_areas(P).sum() - 0.1) < 1e-12  # the rectangle, tiled exactly
     assert np.all(mesh["shift"][..., 0] == 0) and mesh["period"][0] == 0.0
     # transmissive edges only at the two x ends, one per row of quads
     tx = np.nonzero(mesh["bc"] == W.BC_TRANSMISSIVE)
