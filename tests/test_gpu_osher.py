@@ -126,3 +126,16 @@ def test_adjoint_refuses_the_osher_flux(aw):
 def test_bad_flux_name_raises(aw):
     with pytest.raises((ValueError, KeyError)):
         aw.Solver(order_M=1, flux="roe")
+
+
+def test_paper_shock_tube_full_size(aw):
+    """RP1 as the paper sets it up (8862 triangles, P2, Osher-type flux, LTS):
+    60 sweeps against the oracle."""
+    mesh, Q, t_end = W.riemann_problem("RP1")
+    g, o = make_pair(aw, mesh, Q, order_M=2, t_end=t_end)
+    for _ in range(60):
+        assert g.sweep() == o.sweep()
+    eg, eo = g.get_elem(), o.get_elem()
+    for k in ("t", "dt", "count"):
+        assert np.array_equal(eg[k], eo[k]), k
+    assert rel(eg["Q"], eo["Q"]) < 1e-9
