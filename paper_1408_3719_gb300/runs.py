@@ -3,6 +3,7 @@
     python -m paper_1408_3719_gb300.runs sod [--gts] [--order 1]
     python -m paper_1408_3719_gb300.runs vortex --n 45 90 179 [--order 3]
     python -m paper_1408_3719_gb300.runs explosion [--order 2] [--hc 0.00114] [--gts]
+                                                   [--cfl 0.5] [--t-switch T --cfl-start C]
 
 ``--flux osher`` selects the Osher-type ALE flux instead of the Rusanov-type
 one for any case.
@@ -108,11 +109,16 @@ def vortex(n, order=3, gts=False, flux="rusanov"):
     return info
 
 
-def explosion(order=2, hc=0.00114, gts=False, flux="rusanov"):
+def explosion(order=2, hc=0.00114, gts=False, flux="rusanov", cfl=0.5, t_switch=0.0, cfl_start=0.0):
+    """The cylindrical explosion on the graded disc.  ``t_switch`` > 0 starts
+    the run with global steps of CFL ``cfl_start`` up to that time, then local
+    steps (the start-up the paper gives its piston problem, Sec. 3.5)."""
     mesh, Q = W.explosion(hc)
-    e, info = _run(mesh, Q, order_M=order, t_end=0.25, gts=gts, flux=flux)
+    e, info = _run(mesh, Q, order_M=order, t_end=0.25, gts=gts, flux=flux, cfl=cfl,
+                   t_switch=t_switch, cfl_start=cfl_start)
     r = np.linalg.norm(e["X"].reshape(-1, 3, 2).mean(1), axis=1)
-    info.update(config="explosion EP1", rho_max=float(e["Q"][:, 0].max()), r_max=float(r.max()))
+    info.update(config="explosion EP1", cfl=cfl, t_switch=t_switch, cfl_start=cfl_start,
+                rho_max=float(e["Q"][:, 0].max()), r_max=float(r.max()))
     return info
 
 
@@ -249,6 +255,10 @@ def main():
     ap.add_argument("--gts", action="store_true")
     ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
     ap.add_argument("--hc", type=float, default=0.00114)
+    ap.add_argument("--cfl", type=float, default=0.5, help="explosion: CFL number of eq. timestep")
+    ap.add_argument("--t-switch", type=float, default=0.0,
+                    help="explosion: global steps until this time, then local steps")
+    ap.add_argument("--cfl-start", type=float, default=0.0, help="explosion: CFL of the start-up steps")
     ap.add_argument("--flux", default=None, choices=["rusanov", "osher"],
                     help="default: rusanov for sod/vortex/explosion, osher (the paper's) for rp/ep/table")
     a = ap.parse_args()
@@ -280,7 +290,8 @@ def main():
             print(json.dumps(r), flush=True)
             prev = r
     else:
-        print(json.dumps(explosion(a.order or 2, a.hc, a.gts, flux)), flush=True)
+        print(json.dumps(explosion(a.order or 2, a.hc, a.gts, flux, a.cfl, a.t_switch, a.cfl_start or a.cfl)),
+              flush=True)
 
 
 if __name__ == "__main__":
