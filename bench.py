@@ -96,8 +96,16 @@ def host_info():
 
 
 def flux_flops(M: int) -> float:
+    """FP64 operations of one space-time edge surface (Rusanov-type flux,
+    (M+1)^2 Gauss points)."""
     Nt = M + 1
-    per_point = 30 + 2 * 4 * 2 * (Nt - 1) + 6 + 2 * 25 + 25 + 4 * 4
+    per_point = (4                      # corner times (ticks x tick length)
+                 + 33 + 9               # bilinear surface derivatives, normal = cross product
+                 + 11                   # time of the point
+                 + 2 * (2 + 8 * (Nt - 1))  # each side's local tau and trace (4 variables, Horner)
+                 + 2 * 53               # each side's velocity, pressure, sound speed, f, g and F.n
+                 + 15 + 16              # |n_xy|, mesh normal speed, s_max; the Rusanov combination
+                 + 8 + 7)               # weights of the flux and GCL vector; sum over the points
     return Nt * Nt * per_point
 
 
@@ -266,10 +274,12 @@ def run_ours(args, rank, world):
     # with events between the launches (the timed pass above runs each sweep
     # as one captured CUDA graph)
     s.profile(True)
+    surf0 = s.diag()["surfaces"]
     for k in range(args.steps):
         flush.fill_(float(k))
         s.enqueue(1)
     prof_updates = s.sync()
+    prof_surfaces = s.diag()["surfaces"] - surf0
     kms, ksweeps = s.profile_read()
     s.profile(False)
     ms_max, updates_all = aggregate(ms, updates, dist, "cuda")
@@ -278,15 +288,20 @@ def run_ours(args, rank, world):
     # dominant kernel and its roofline (FP64 pipe: this path is ALU-bound)
     dom = max(kms, key=kms.get)
     members = sizes["u_entries"] / max(sizes["n_tris"], 1)
-    model = {"k_predict": predictor_flops(args.order), "k_recon": recon_flops(args.order, members)}
+    # FP64 operations of the profiled pass: per update (predictor,
+    # reconstruction) or per space-time edge surface (fluxes)
+    model = {"k_predict": (predictor_flops(args.order), prof_updates, "update"),
+             "k_recon": (recon_flops(args.order, members), prof_updates, "update"),
+             "k_flux": (flux_flops(args.order), prof_surfaces, "surface")}
     roof = None
     if dom in model and kms[dom] > 0:
-        achieved = model[dom] * prof_updates / (kms[dom] * 1e-3) / 1e12
+        per_unit, units, unit_name = model[dom]
+        achieved = per_unit * units / (kms[dom] * 1e-3) / 1e12
         peak = peak_gflops / 1e3
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured FP64 DFMA throughput (aw_measure_fp64_peak, this run)",
-                "flops_per_update": model[dom]}
+                f"flops_per_{unit_name}": per_unit, f"{unit_name}s_profiled": units}
     # the HBM roofline this FP64-bound path is far from: compulsory bytes per
     # update x update rate, against the measured copy bandwidth
     bpu = hbm_bytes_per_update(args.order, sizes["sw_entries"] / n_tris)

@@ -157,7 +157,9 @@ int aw_get_node_arrays(aw_ctx* ctx, double* X, int64_t* t);
 int aw_set_node_arrays(aw_ctx* ctx, const double* X, const int64_t* t);
 
 /* out[0] = largest GCL residual |sum of int n dS| / |T| seen in an update
- * (eq. gcl); out[1] = number of element updates; out[2] = sweeps run. */
+ * (eq. gcl); out[1] = number of element updates; out[2] = sweeps run;
+ * out[3] = space-time edge surfaces integrated (Sec. 2.5, eq. spacetimenodes).
+ * out holds 4 doubles. */
 int aw_diagnostics(aw_ctx* ctx, double* out);
 /* Sizes (out has 6 entries): out[0] n_tris, out[1] n_nodes, out[2] n_edges,
  * out[3] N_st, out[4] total S^W entries, out[5] total distinct members of

@@ -316,7 +316,7 @@ class Solver:
     def diag(self):
         out = np.zeros(4)
         self._check(self.lib.aw_diagnostics(self.h, _ptr(out)))
-        return dict(gcl_max=out[0], updates=out[1], sweeps=out[2])
+        return dict(gcl_max=out[0], updates=out[1], sweeps=out[2], surfaces=out[3])
 
     def profile(self, on=True):
         self._check(self.lib.aw_profile_enable(self.h, int(on)))

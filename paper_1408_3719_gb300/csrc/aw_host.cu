@@ -1267,6 +1267,7 @@ int aw_diagnostics(aw_ctx* c, double* out) {
   out[0] = g;
   out[1] = (double)c->hcnt->updates;
   out[2] = (double)c->hcnt->sweeps;
+  out[3] = (double)c->hcnt->surfaces;
   return AW_OK;
 }
 

@@ -145,6 +145,7 @@ struct Counters {
   int last_ready;                 // ready elements of the last completed sweep
   int finish_blocks;
   long long updates_since_sync;
+  long long surfaces;            // space-time edge surfaces integrated (all sweeps)
 };
 
 // Tile shapes of a sweep's kernels (they change no arithmetic): recon_half

@@ -135,6 +135,7 @@ __global__ void k_finish(Tab T, Dev d) {
     c->n_cand[epoch & 1] = 0;  // consumed by this sweep; refilled by the next one's finish
     c->n_ready = 0;
     c->n_moved = 0;
+    c->surfaces += c->n_active;
     c->n_active = 0;
     c->n_touched = 0;
     c->sweeps += 1;
@@ -347,16 +348,18 @@ __device__ __forceinline__ void osher(const Tab& T, const double* qm, const doub
 // shuffle tree within each edge's lanes.
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
-  constexpr int Nt = M + 1, NP = Nt * Nt, EPW = 32 / NP;
+  // one thread per Gauss point, the block's EPB edges packed back to back
+  // (an edge's points may span two warps: every lane of a warp FP64
+  // instruction costs the pipe the same, used or not), the point sums
+  // through shared memory in point order
+  constexpr int Nt = M + 1, NP = Nt * Nt, EPB = kBlock / NP;
+  __shared__ double sGN[kBlock][7];
   const int epoch = d.cnt->epoch;
   const int n_active = d.cnt->n_active;
-  const int n_items = (n_active + EPW - 1) / EPW * 32;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < n_items; base += stride) {
-    const int item = base + threadIdx.x;
-    const int lane = item & 31, slot = lane / NP, pt = lane % NP;
-    const int q = (item >> 5) * EPW + slot;
-    const bool valid = item < n_items && slot < EPW && q < n_active;
+  const int slot = threadIdx.x / NP, pt = threadIdx.x % NP;
+  for (int first = blockIdx.x * EPB; first < n_active; first += gridDim.x * EPB) {
+    const int q = first + slot;
+    const bool valid = slot < EPB && q < n_active;
     double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
     int ed = -1;
     if (valid) {
@@ -454,26 +457,22 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       for (int c = 0; c < 3; ++c) Nn[c] = wq * n[c];
     }
 #pragma unroll
-    for (int off = 1; off < NP; off <<= 1) {
-      const bool in = pt + off < NP;
+    for (int v = 0; v < 4; ++v) sGN[threadIdx.x][v] = G[v];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const double o = __shfl_down_sync(0xffffffffu, G[v], off);
-        if (in) G[v] += o;
-      }
+    for (int c = 0; c < 3; ++c) sGN[threadIdx.x][4 + c] = Nn[c];
+    __syncthreads();
+    // one thread per (edge, component): the flux G (4) and the GCL vector (3)
+    for (int it = threadIdx.x; it < EPB * 7; it += kBlock) {
+      const int le = it / 7, k = it % 7, qq = first + le;
+      if (qq >= n_active) continue;
+      double acc = sGN[le * NP][k];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double o = __shfl_down_sync(0xffffffffu, Nn[c], off);
-        if (in) Nn[c] += o;
-      }
+      for (int p2 = 1; p2 < NP; ++p2) acc += sGN[le * NP + p2][k];
+      const int e2 = d.active_list[qq];
+      if (k < 4) d.G[4 * (size_t)e2 + k] = acc;
+      else d.N[4 * (size_t)e2 + k - 4] = acc;
     }
-    if (pt == 0 && valid) {
-      ed = d.active_list[q];
-      double* g = d.G + 4 * (size_t)ed;
-      double* nn = d.N + 4 * (size_t)ed;
-      g[0] = G[0]; g[1] = G[1]; g[2] = G[2]; g[3] = G[3];
-      nn[0] = Nn[0]; nn[1] = Nn[1]; nn[2] = Nn[2];
-    }
+    __syncthreads();
   }
 }
 
@@ -670,7 +669,7 @@ struct PredShape {
 };
 
 template <int M, int TH>
-__global__ void __launch_bounds__(TH) k_predict_coop(Tab T, Dev d, int initial, int gts) {
+__global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, Dev d, int initial, int gts) {
   using S = PredShape<M, TH>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst, G = S::G;
   __shared__ double sq[G][Nst][4], sf[G][Nst][4], sg[G][Nst][4], sP[G][Nst][4];
@@ -690,12 +689,28 @@ __global__ void __launch_bounds__(TH) k_predict_coop(Tab T, Dev d, int initial, 
   for (int k = threadIdx.x; k < 3 * Nt * Mc; k += blockDim.x) sTr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc] = T.Tr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc];
   const int n_ready = initial ? d.ne : d.cnt->n_ready;
   const long long gmin = d.cnt->gts_min;
-  // thread -> (time slice t, element e, lattice node s): the tau = 0 nodes of
-  // all G elements are the first threads, so the warps that only hold them go
-  // quiet where the tau = 0 work is cheap or already done
-  const int t = threadIdx.x / (G * Mc), rr = threadIdx.x % (G * Mc);
+  // thread -> (time slice t, element e, lattice node s).  A warp-wide FP64
+  // instruction costs the FP64 pipe the same whatever number of its lanes is
+  // active, so the tau = 0 nodes (full work in the first iteration only) and
+  // the tau > 0 nodes (full work in the later ones) sit in separate warps:
+  // the tau = 0 nodes of all G elements first, padded to a whole warp, when
+  // that fits the block, otherwise after the tau > 0 nodes.
+  constexpr int nBot = G * Mc, nTop = G * Mc * (Nt - 1), nBotPad = (nBot + 31) / 32 * 32;
+  constexpr bool padBot = nBotPad + nTop <= TH;
+  int t, rr;
+  if (padBot) {
+    const int x = threadIdx.x;
+    if (x < nBot) { t = 0; rr = x; }
+    else if (x >= nBotPad && x < nBotPad + nTop) { t = 1 + (x - nBotPad) / nBot; rr = (x - nBotPad) % nBot; }
+    else { t = Nt; rr = 0; }
+  } else {
+    const int x = threadIdx.x;
+    if (x < nTop) { t = 1 + x / nBot; rr = x % nBot; }
+    else if (x < nTop + nBot) { t = 0; rr = x - nTop; }
+    else { t = Nt; rr = 0; }
+  }
   const int e = t < Nt ? rr / Mc : G;
-  const int s = rr % Mc, l = t * Mc + s;
+  const int s = rr % Mc, l = (t < Nt ? t : 0) * Mc + s;
   const double gm1 = T.gamma - 1.0;
   for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
     const int pos = base + e;
@@ -743,7 +758,45 @@ __global__ void __launch_bounds__(TH) k_predict_coop(Tab T, Dev d, int initial, 
         sV[e][l][1] = T.eulerian ? 0.0 : v;
       }
       __syncthreads();
-      if (full) {  // P at the own node (eq. pdef) with the isoparametric metric (eq. Jac)
+      if (full && t > 0) {
+        // tau > 0 node (later iterations): P at the own node (eq. pdef) with
+        // the isoparametric metric (eq. Jac) first, then one contraction with
+        // the combined weights D_xi xi_x + D_eta eta_x (and the y, t ones)
+        double xx = 0, xe = 0, yx = 0, ye = 0;
+#pragma unroll
+        for (int r = 0; r < Mc; ++r) {
+          const double a = sDxi[s][r], b = sDeta[s][r];
+          const int lr = t * Mc + r;
+          xx += a * sx[e][lr][0]; xe += b * sx[e][lr][0];
+          yx += a * sx[e][lr][1]; ye += b * sx[e][lr][1];
+        }
+        double xt = 0.0, yt = 0.0;
+#pragma unroll
+        for (int u = 0; u < Nt; ++u) {
+          xt += sDtau[t][u] * sx[e][u * Mc + s][0];
+          yt += sDtau[t][u] * sx[e][u * Mc + s][1];
+        }
+        xt *= idt;
+        yt *= idt;
+        const double idet = 1.0 / (xx * ye - xe * yx);
+        const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+        const double xit = -(xix * xt + xiy * yt), ett = -(etx * xt + ety * yt);
+        double Pv[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int r = 0; r < Mc; ++r) {
+          const double a = sDxi[s][r], b = sDeta[s][r];
+          const double wx = a * xix + b * etx, wy = a * xiy + b * ety, wt = a * xit + b * ett;
+          const int lr = t * Mc + r;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            Pv[v] += wx * sf[e][lr][v];
+            Pv[v] += wy * sg[e][lr][v];
+            Pv[v] += wt * sq[e][lr][v];
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sP[e][l][v] = -Pv[v];
+      } else if (full) {  // tau = 0 node, first iteration: P (eq. pdef, eq. Jac) keeping its parts
         double Qx[4] = {0, 0, 0, 0}, Qe[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fe[4] = {0, 0, 0, 0};
         double gx[4] = {0, 0, 0, 0}, ge[4] = {0, 0, 0, 0};
         double xx = 0, xe = 0, yx = 0, ye = 0;
@@ -982,7 +1035,7 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
     __syncthreads();
     if (tid == 0) {
       sPre[0] = 0;
-      for (int e = 0; e < G; ++e) sPre[e + 1] = sPre[e] + (sVal[e] ? sNU[e] + 4 : 0);
+      for (int e = 0; e < G; ++e) sPre[e + 1] = sPre[e] + (sVal[e] ? sNU[e] : 0);
     }
     for (int k = tid; k < G * kNSten * NE; k += nth) {
       const int e = k / (kNSten * NE);
@@ -990,16 +1043,18 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
     }
     __syncthreads();
     // P1: rows of the least-squares systems (virtual data, eqs. virtGeom,
-    // virtCellaverage, intConsRec) and the time-step candidates (eq. timestep)
+    // virtCellaverage, intConsRec), then the time-step candidates
+    // (eq. timestep) on the last threads of the block, so that the warps
+    // holding rows do not also run the time-step code with a few lanes
+    constexpr int NQ = M == 1 ? 1 : (M == 2 ? 3 : 4);  // points of the exact degree-M rule
     for (int item = tid; item < sPre[G]; item += nth) {
       int e = 0;
       while (item >= sPre[e + 1]) ++e;
       const int u = item - sPre[e];
       const double* el = sEl + e * 16;
-      const int i = sI[e];
-      const long long ti = d.t[i];
+      const long long ti = d.t[sI[e]];
       double Xv[6], Qv[4];
-      if (u < sNU[e]) {
+      {
         const int q = sU0[e] + u;
         const int j = d.u_elem[q];
         virtual_data<M>(T, d, j, ti, Xv, Qv);
@@ -1014,7 +1069,8 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
         double row[NU];
 #pragma unroll
         for (int a = 0; a < NU; ++a) row[a] = 0.0;
-        for (int qq = 0; qq < T.nq; ++qq) {
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
           const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
           const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
           double m[kMaxNU];
@@ -1027,8 +1083,15 @@ __global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial
         for (int a = 0; a < NU; ++a) dst[a] = row[a] - T.mbar[a];
 #pragma unroll
         for (int v = 0; v < 4; ++v) dst[NU + v] = Qv[v] - el[6 + v];
-      } else {
-        const int k = u - sNU[e];
+      }
+    }
+    for (int item = nth - 1 - tid; item < G * 4; item += nth) {
+      const int e = item / 4, k = item % 4;
+      if (!sVal[e]) continue;
+      const int i = sI[e];
+      const long long ti = d.t[i];
+      double Xv[6], Qv[4];
+      {
         const int j = k == 0 ? i : d.nbr[3 * (size_t)i + k - 1];
         double dtc = DBL_MAX;
         if (j >= 0 && ti < T.T) {
