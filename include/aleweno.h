@@ -239,8 +239,8 @@ int aw_adjoint(aw_ctx* ctx, const double* dJdQ, const double* dJdX, const double
 
 /* Tile shapes of the sweep kernels; they change no result, only speed.
  * tiles[0] = 1 halves the reconstruction's elements per block (16/8/4 for
- * P1/P2/P3 by default), tiles[1] = 1 runs the predictor on 256-thread blocks
- * (default 128), tiles[2] = blocks per SM of the kernels that loop over a
+ * P1/P2/P3 by default on 256 threads; half of them on 128 threads),
+ * tiles[1] = 1 runs the predictor on 256-thread blocks (default 128), tiles[2] = blocks per SM of the kernels that loop over a
  * sweep's lists (default 8, range 1..64).  Setting them re-captures the sweep
  * graph.  No counterpart in the paper. */
 int aw_set_tiles(aw_ctx* ctx, const int32_t* tiles);

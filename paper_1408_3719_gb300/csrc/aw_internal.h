@@ -149,7 +149,7 @@ struct Counters {
 };
 
 // Tile shapes of a sweep's kernels (they change no arithmetic): recon_half
-// halves the reconstruction's elements per block, pred_wide runs the
+// halves the reconstruction's elements and threads per block, pred_wide runs the
 // predictor on 256-thread blocks instead of 128, bpsm = blocks per SM of the
 // persistent kernels that loop over the sweep's lists.
 struct Tiles {

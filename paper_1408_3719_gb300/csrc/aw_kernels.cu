@@ -964,7 +964,9 @@ struct ReconShape {
   static constexpr int Mc = (M + 1) * (M + 2) / 2, NU = Mc - 1, NE = 2 * Mc;
   static constexpr int MaxU = kNSten * (NE - 1);
   static constexpr int G = GG;
-  static constexpr int kThreads = 256;
+  // the default shape on 256 threads; half the elements on 128 threads (the
+  // same threads per element, twice the blocks and barrier domains per SM)
+  static constexpr int kThreads = GG < recon_g_default<M>() ? 128 : 256;
   static constexpr int NL = NU * (NU + 1) / 2;      // lower triangle of the normal matrix
   static constexpr int NN = NL + 4 * NU;           // + right-hand sides
   static constexpr int RW = NU + 4;                 // row: basis averages, then Q~ - Q_i
@@ -985,7 +987,8 @@ struct ReconShape {
 };
 
 template <int M, int GG>
-__global__ void __launch_bounds__(256, 2) k_recon_coop(Tab T, Dev d, int initial) {
+__global__ void __launch_bounds__(ReconShape<M, GG>::kThreads, 512 / ReconShape<M, GG>::kThreads)
+k_recon_coop(Tab T, Dev d, int initial) {
   using S = ReconShape<M, GG>;
   constexpr int Mc = S::Mc, NU = S::NU, NE = S::NE, MaxU = S::MaxU, G = S::G, NL = S::NL, NN = S::NN, RW = S::RW;
   extern __shared__ double smem[];
