@@ -47,42 +47,52 @@ __device__ __forceinline__ double pressure(const Tab& T, const double* q) {
 // afterwards the total stencils of the previous sweep's ready elements (the
 // criterion of any other element reads only unchanged times).
 __global__ void k_ready(Tab T, Dev d) {
-  // one warp per candidate element, lanes over its total stencil
+  // eight lanes per candidate element, four candidates per warp; each lane
+  // loads its UN total-stencil entries of a chunk (and their ticks) before
+  // any of them is tested, and a chunk that finds a violation ends the test
+  constexpr int GL = 8, UN = 4;
   const int epoch = d.cnt->epoch;
   const int par = epoch & 1;
   const bool listed = d.cnt->cand_valid != 0 && !T.gts;
   const int n_items = listed ? d.cnt->n_cand[par] : d.ne;
   const int* clist = d.cand_list + (size_t)par * d.ne;
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, gl = lane & (GL - 1);
+  const unsigned gmask = 0xFFu << (lane & ~(GL - 1));
+  const int ngroups = (gridDim.x * blockDim.x) / GL;
   if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->gts_min = LLONG_MAX;
-  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n_items; q += nwarps) {
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / GL; q < n_items; q += ngroups) {
     const int i = listed ? clist[q] : q;
     const long long ti = d.t[i];
     if (ti >= T.T) continue;
     const long long tn = ti + d.dt[i];
     bool ready = true;
-    for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += 32) {
-      const int p = base + lane;
-      bool bad = false;
-      if (p < pe) {
-        const int j = d.sw[p];
-        const long long tj = d.t[j];
-        bad = tj > tn || tn > tj + d.dt[j];
+    for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += GL * UN) {
+      int jj[UN];
+#pragma unroll
+      for (int u = 0; u < UN; ++u) {
+        const int p = base + u * GL + gl;
+        jj[u] = p < pe ? d.sw[p] : -1;
       }
-      if (__any_sync(0xffffffffu, bad)) {
+      bool bad = false;
+#pragma unroll
+      for (int u = 0; u < UN; ++u)
+        if (jj[u] >= 0) {
+          const long long tj = d.t[jj[u]];
+          bad |= tj > tn || tn > tj + d.dt[jj[u]];
+        }
+      if (__any_sync(gmask, bad)) {
         ready = false;
         break;
       }
     }
     if (!ready) continue;
-    if (lane == 0) {
+    if (gl == 0) {
       const int slot = atomicAdd(&d.cnt->n_ready, 1);
       d.ready_list[slot] = i;
       d.elem_ready[i] = epoch;
     }
-    if (lane < 3) {
-      const int n = d.tri[3 * i + lane];
+    if (gl < 3) {
+      const int n = d.tri[3 * i + gl];
       d.ntn[n] = tn;
       if (atomicExch(&d.node_moved[n], epoch) != epoch) {
         const int s2 = atomicAdd(&d.cnt->n_moved, 1);

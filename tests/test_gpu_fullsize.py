@@ -1,5 +1,6 @@
-"""Full-size checks on the 498,681-triangle explosion at P3 (the benchmark's
-workload and launch configuration): one sweep from a GPU snapshot, recomputed
+"""Full-size checks on the 498,681-triangle explosion at P3 and P2 (the benchmark's
+workload and launch configuration, autotuned tiles and the captured sweep
+graph): one sweep from a GPU snapshot, recomputed
 by the oracle for every element it updates, must agree to the single-update
 tolerance; conservation and the geometric conservation law must hold over
 the whole mesh."""
@@ -17,16 +18,21 @@ def _areas(X):
     return 0.5 * ((X[:, 2] - X[:, 0]) * (X[:, 5] - X[:, 1]) - (X[:, 3] - X[:, 1]) * (X[:, 4] - X[:, 0]))
 
 
-def test_fullsize_explosion_p3_sweep_against_oracle():
+@pytest.mark.parametrize("order", [3, 2])
+def test_fullsize_explosion_sweep_against_oracle(order):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1408_3719_gb300 import aleweno
 
     mesh, Q = W.explosion(0.00114)
-    g = aleweno.Solver(order_M=3, t_end=0.25)
+    g = aleweno.Solver(order_M=order, t_end=0.25)
     g.load_mesh(mesh)
     g.load_state(Q)
     tot0 = (_areas(g.get_elem()["X"])[:, None] * Q).sum(0)
+    # the benchmark's launch configuration: the autotuner picks the tile
+    # shapes on the loaded state (and restores it), then the captured graph
+    tiles, _ = g.autotune(20)
+    assert g.get_tiles() == tiles
     g.enqueue(12)  # the captured-graph path the benchmark times
     g.sync()
     snap = g.get_elem()
@@ -37,7 +43,7 @@ def test_fullsize_explosion_p3_sweep_against_oracle():
     # local time, so the momentum total is not fixed between common times)
     assert np.abs(tot[[0, 3]] - tot0[[0, 3]]).max() < 1e-12 * np.abs(tot0).max()
     assert g.diag()["gcl_max"] < 1e-12
-    o = Oracle(order_M=3, t_end=0.25)
+    o = Oracle(order_M=order, t_end=0.25)
     o.load_mesh(mesh)
     o.set_elem(snap)
     o.set_nodes(nX, nt)
