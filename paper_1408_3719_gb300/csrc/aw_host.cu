@@ -30,6 +30,10 @@ struct aw_ctx {
   bool prof = false;         // per-kernel CUDA-event timing of sweeps
   cudaGraphExec_t prof_graph = nullptr;  // the sweep with an event before and after every kernel
   cudaEvent_t prof_ev[kNumKernels + 1] = {};
+  // side stream of the sweep graph: the node solver runs beside the edge
+  // marking (they read the moved-node list and write disjoint arrays)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   double prof_ms[kNumKernels] = {0};
   long long prof_sweeps = 0;
   long long ne = 0, nn = 0, ned = 0, sw_total = 0, u_total = 0;
@@ -835,6 +839,9 @@ void aw_destroy(aw_ctx* c) {
   free_all(c);
   for (cudaEvent_t e : c->prof_ev)
     if (e) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->hcnt) cudaFreeHost(c->hcnt);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1051,9 +1058,14 @@ static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
   // kernels: each profiled sweep waits for its last event and adds the
   // kernel times (the kernels run as in the plain graph).
   if (!c->prof && !c->graph_exec) {
+    if (!c->side) {
+      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    launch_sweep(c->tab, c->d, c->nsm, c->stream, nullptr, c->tiles);
+    launch_sweep(c->tab, c->d, c->nsm, c->stream, nullptr, c->tiles, c->side, c->fork_ev, c->join_ev);
     CK(cudaStreamEndCapture(c->stream, &g));
     CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
     cudaGraphDestroy(g);

@@ -161,7 +161,10 @@ struct Tiles {
 // kernel launchers (aw_kernels.cu)
 constexpr int kNumKernels = 8;  // launches per sweep
 const char* kernel_name(int k);
-void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl);
+// side, fork, join (optional, plain launches only): the node solver on the
+// side stream, beside the edge marking on s
+void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl,
+                  cudaStream_t side = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, const Tiles& tl);
 void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
 double measure_fp64_peak();

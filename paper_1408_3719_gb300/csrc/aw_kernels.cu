@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       double qm[4], qp[4];
       {
         const long long tL = d.t[L], dtL = d.dt[L];
-        const double tl = dtL > 0 ? (tt - (double)tL) / (double)dtL : 0.0;
+        const double tl = dtL > 0 ? (tt - (double)tL) * (1.0 / (double)dtL) : 0.0;  // a reciprocal costs the FP64 pipe half a divide
         const double* c0 = d.trace + ((((size_t)L * 3 + le) * Nt + gx) * Nt) * 4;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       }
       if (R >= 0) {
         const long long tR = d.t[R], dtR = d.dt[R];
-        const double tr = dtR > 0 ? (tt - (double)tR) / (double)dtR : 0.0;
+        const double tr = dtR > 0 ? (tt - (double)tR) * (1.0 / (double)dtR) : 0.0;
         const double* c0 = d.trace + ((((size_t)R * 3 + lr) * Nt + (Nt - 1 - gx)) * Nt) * 4;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -493,6 +493,7 @@ __global__ void k_update(Tab T, Dev d) {
   for (int base = blockIdx.x * blockDim.x; base < n_touched; base += stride) {
     int q = base + threadIdx.x;
     bool upd = false;
+    double gcl = 0.0;  // GCL residual of this thread's update (non-negative)
     if (q < n_touched) {
       int i = d.touch_list[q];
       bool ready = d.elem_ready[i] == epoch;
@@ -533,8 +534,7 @@ __global__ void k_update(Tab T, Dev d) {
           d.HM[4 * i + c] = 0.0;
         }
         res[2] += Anew - Aold;
-        double r = fmax(fabs(res[0]), fmax(fabs(res[1]), fabs(res[2]))) / Aold;
-        atomicMax(&d.cnt->gcl_bits, (unsigned long long)__double_as_longlong(r));
+        gcl = fmax(fabs(res[0]), fmax(fabs(res[1]), fabs(res[2]))) / Aold;
         for (int k = 0; k < 6; ++k) d.X[6 * i + k] = Xn[k];
         d.t[i] += d.dt[i];
         if (d.t[i] >= T.T) atomicSub(&d.cnt->n_unfinished, 1);
@@ -549,6 +549,15 @@ __global__ void k_update(Tab T, Dev d) {
       }
     }
     unsigned um = __ballot_sync(0xffffffffu, upd);
+    // the warp's largest residual (non-negative doubles order like their
+    // bit patterns), one atomic per warp
+    unsigned long long gb = (unsigned long long)__double_as_longlong(gcl);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, gb, off);
+      gb = o > gb ? o : gb;
+    }
+    if ((threadIdx.x & 31) == 0 && um) atomicMax(&d.cnt->gcl_bits, gb);
     if ((threadIdx.x & 31) == 0 && um) {
       atomicAdd((unsigned long long*)&d.cnt->updates, (unsigned long long)__popc(um));
       atomicAdd((unsigned long long*)&d.cnt->updates_since_sync, (unsigned long long)__popc(um));
@@ -569,7 +578,7 @@ __device__ __forceinline__ void virtual_data(const Tab& T, const Dev& d, int j, 
     for (int v = 0; v < 4; ++v) Qv[v] = d.Q[4 * j + v];
     return;
   }
-  const double tau = (double)(ti - tj) / (double)dtj;
+  const double tau = (double)(ti - tj) * (1.0 / (double)dtj);  // a reciprocal costs half a divide
   const double dts = (double)dtj * d.etick[j];
   const double* vd = d.vdisp + (size_t)j * 6 * Nt;
 #pragma unroll
@@ -1444,7 +1453,8 @@ void launch_predict(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int ini
 // ev (optional): kNumKernels + 1 events recorded on s around the launches,
 // for per-kernel CUDA-event timing on the launching stream.
 template <int M>
-void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl) {
+void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl,
+                cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
   const int grid_w = nsm * tl.bpsm;
   int k = 0;
@@ -1452,8 +1462,19 @@ void sweep_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t
   // order the capture)
   auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[k++], s, cudaEventRecordExternal); };
   mark(); k_ready<<<std::min(grid_all_e * 8, nsm * 64), 256, 0, s>>>(T, d);
-  mark(); k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
-  mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
+  if (!ev && side && fork && join) {
+    // the node solver and the edge marking both read only the moved-node
+    // list and write disjoint arrays: two branches of the graph
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
+    k_nodes_grp<M><<<grid_w * 2, kBlock, 0, side>>>(T, d);
+    cudaEventRecord(join, side);
+    k_edges<<<grid_w, kBlock, 0, s>>>(d);
+    cudaStreamWaitEvent(s, join, 0);
+  } else {
+    mark(); k_nodes_grp<M><<<grid_w * 2, kBlock, 0, s>>>(T, d);
+    mark(); k_edges<<<grid_w, kBlock, 0, s>>>(d);
+  }
   mark(); k_flux_grp<M><<<grid_w * 4, kBlock, 0, s>>>(T, d);
   mark(); k_update<<<grid_w, kBlock, 0, s>>>(T, d);
   mark(); launch_recon<M>(T, d, nsm, s, 0, tl);
@@ -1500,11 +1521,12 @@ const char* kernel_name(int k) {
   return (k >= 0 && k < kNumKernels) ? names[k] : nullptr;
 }
 
-void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl) {
+void launch_sweep(const Tab& T, const Dev& d, int nsm, cudaStream_t s, cudaEvent_t* ev, const Tiles& tl,
+                  cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
   switch (T.M) {
-    case 1: sweep_impl<1>(T, d, nsm, s, ev, tl); break;
-    case 2: sweep_impl<2>(T, d, nsm, s, ev, tl); break;
-    default: sweep_impl<3>(T, d, nsm, s, ev, tl); break;
+    case 1: sweep_impl<1>(T, d, nsm, s, ev, tl, side, fork, join); break;
+    case 2: sweep_impl<2>(T, d, nsm, s, ev, tl, side, fork, join); break;
+    default: sweep_impl<3>(T, d, nsm, s, ev, tl, side, fork, join); break;
   }
 }
 
