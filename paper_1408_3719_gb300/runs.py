@@ -149,13 +149,16 @@ def _radial_reference(case, t_end, n):
     return _REFERENCE[key]
 
 
-def explosion_paper(case="EP1", order=2, gts=False, flux="osher", t_end=None, n_ref=15000):
+def explosion_paper(case="EP1", order=2, gts=False, flux="osher", t_end=None, n_ref=15000, cfl=0.5,
+                    t_switch=0.0, cfl_start=0.0):
     """An explosion of Sec. 3.3 on the stand-in for mesh m1; density and
     pressure L1 differences (area-weighted) against the 1D radial reference
-    solution of eqs. inhomEuler on n_ref points, sampled at the centroids."""
+    solution of eqs. inhomEuler on n_ref points, sampled at the centroids.
+    ``t_switch`` > 0: global steps of CFL ``cfl_start`` until then."""
     mesh, Q, t_def = W.explosion_problem(case)
     t_end = t_def if t_end is None else t_end
-    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux)
+    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux, cfl=cfl, t_switch=t_switch,
+                   cfl_start=cfl_start)
     A = _areas(e["X"])
     rc = np.linalg.norm(e["X"].reshape(-1, 3, 2).mean(1), axis=1)
     r, rho, u, p = _radial_reference(case, t_end, n_ref)
@@ -171,14 +174,14 @@ def explosion_paper(case="EP1", order=2, gts=False, flux="osher", t_end=None, n_
     return info
 
 
-def saltzman(order=2, gts=False, flux="rusanov", t_end=0.6):
+def saltzman(order=2, gts=False, flux="rusanov", t_end=0.6, cfl=0.5):
     """The Saltzman piston of Sec. 3.5: third order, Rusanov-type flux, global
     steps with CFL 0.1 until t = 0.01, then local (or global) steps with CFL
-    0.5; density and velocity L1 errors against the exact piston shock."""
+    ``cfl``; density and velocity L1 errors against the exact piston shock."""
     mesh, Q = W.saltzman()
     g = 5.0 / 3.0
     e, info = _run(mesh, Q, order_M=order, gamma=g, t_end=t_end, gts=gts, flux=flux, wall_velocity=(1.0, 0.0),
-                   t_switch=0.01, cfl_start=0.1)
+                   t_switch=0.01, cfl_start=0.1, cfl=cfl)
     A = _areas(e["X"])
     cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
     s, rho1, _ = W.piston_shock()
@@ -255,10 +258,11 @@ def main():
     ap.add_argument("--gts", action="store_true")
     ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
     ap.add_argument("--hc", type=float, default=0.00114)
-    ap.add_argument("--cfl", type=float, default=0.5, help="explosion: CFL number of eq. timestep")
+    ap.add_argument("--cfl", type=float, default=0.5,
+                    help="explosion, ep, saltzman: CFL number of eq. timestep (saltzman: after its start-up)")
     ap.add_argument("--t-switch", type=float, default=0.0,
-                    help="explosion: global steps until this time, then local steps")
-    ap.add_argument("--cfl-start", type=float, default=0.0, help="explosion: CFL of the start-up steps")
+                    help="explosion, ep: global steps until this time, then local steps")
+    ap.add_argument("--cfl-start", type=float, default=0.0, help="explosion, ep: CFL of the start-up steps")
     ap.add_argument("--flux", default=None, choices=["rusanov", "osher"],
                     help="default: rusanov for sod/vortex/explosion, osher (the paper's) for rp/ep/table")
     a = ap.parse_args()
@@ -269,13 +273,14 @@ def main():
         print(json.dumps(kidder(a.order or 3, a.gts, a.flux or "osher")), flush=True)
     elif a.case == "saltzman":
         try:
-            print(json.dumps(saltzman(a.order or 2, a.gts, a.flux or "rusanov", a.t_end or 0.6)), flush=True)
+            print(json.dumps(saltzman(a.order or 2, a.gts, a.flux or "rusanov", a.t_end or 0.6, a.cfl)), flush=True)
         except RuntimeError as err:
             print(json.dumps(dict(config="Saltzman", gts=a.gts, failed=str(err)[:600])), flush=True)
     elif a.case == "rp":
         print(json.dumps(riemann(a.problem or "RP1", a.order or 2, a.gts, flux)), flush=True)
     elif a.case == "ep":
-        print(json.dumps(explosion_paper(a.problem or "EP1", a.order or 2, a.gts, flux, a.t_end)), flush=True)
+        print(json.dumps(explosion_paper(a.problem or "EP1", a.order or 2, a.gts, flux, a.t_end, cfl=a.cfl,
+                                         t_switch=a.t_switch, cfl_start=a.cfl_start or a.cfl)), flush=True)
     elif a.case == "table":
         table(a.order or 2, flux)
     elif a.case == "sod":
