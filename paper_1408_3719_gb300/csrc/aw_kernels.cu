@@ -49,7 +49,10 @@ __device__ __forceinline__ double pressure(const Tab& T, const double* q) {
 __global__ void k_ready(Tab T, Dev d) {
   // eight lanes per candidate element, four candidates per warp; each lane
   // loads its UN total-stencil entries of a chunk (and their ticks) before
-  // any of them is tested, and a chunk that finds a violation ends the test
+  // any of them is tested, and a chunk that finds a violation ends the test.
+  // Compaction: a warp ballot of its ready candidates and of their new
+  // vertices, one atomic per warp for each list, slots from the ballot's
+  // prefix counts.
   constexpr int GL = 8, UN = 4;
   const int epoch = d.cnt->epoch;
   const int par = epoch & 1;
@@ -58,47 +61,64 @@ __global__ void k_ready(Tab T, Dev d) {
   const int* clist = d.cand_list + (size_t)par * d.ne;
   const int lane = threadIdx.x & 31, gl = lane & (GL - 1);
   const unsigned gmask = 0xFFu << (lane & ~(GL - 1));
-  const int ngroups = (gridDim.x * blockDim.x) / GL;
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->gts_min = LLONG_MAX;
-  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / GL; q < n_items; q += ngroups) {
-    const int i = listed ? clist[q] : q;
-    const long long ti = d.t[i];
-    if (ti >= T.T) continue;
-    const long long tn = ti + d.dt[i];
-    bool ready = true;
-    for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += GL * UN) {
-      int jj[UN];
+  for (int qb = warp * (32 / GL); qb < n_items; qb += nwarps * (32 / GL)) {  // warp-uniform
+    const int q = qb + lane / GL;
+    int i = -1;
+    long long tn = 0;
+    bool ready = false;
+    if (q < n_items) {
+      i = listed ? clist[q] : q;
+      const long long ti = d.t[i];
+      if (ti < T.T) {
+        tn = ti + d.dt[i];
+        ready = true;
+        for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += GL * UN) {
+          int jj[UN];
 #pragma unroll
-      for (int u = 0; u < UN; ++u) {
-        const int p = base + u * GL + gl;
-        jj[u] = p < pe ? d.sw[p] : -1;
-      }
-      bool bad = false;
+          for (int u = 0; u < UN; ++u) {
+            const int p = base + u * GL + gl;
+            jj[u] = p < pe ? d.sw[p] : -1;
+          }
+          bool bad = false;
 #pragma unroll
-      for (int u = 0; u < UN; ++u)
-        if (jj[u] >= 0) {
-          const long long tj = d.t[jj[u]];
-          bad |= tj > tn || tn > tj + d.dt[jj[u]];
+          for (int u = 0; u < UN; ++u)
+            if (jj[u] >= 0) {
+              const long long tj = d.t[jj[u]];
+              bad |= tj > tn || tn > tj + d.dt[jj[u]];
+            }
+          if (__any_sync(gmask, bad)) {
+            ready = false;
+            break;
+          }
         }
-      if (__any_sync(gmask, bad)) {
-        ready = false;
-        break;
       }
     }
-    if (!ready) continue;
-    if (gl == 0) {
-      const int slot = atomicAdd(&d.cnt->n_ready, 1);
-      d.ready_list[slot] = i;
+    // ready list: one slot per ready candidate (its group's lane 0)
+    const unsigned br = __ballot_sync(0xffffffffu, ready && gl == 0);
+    int base_r = 0;
+    if (lane == 0 && br) base_r = atomicAdd(&d.cnt->n_ready, __popc(br));
+    base_r = __shfl_sync(0xffffffffu, base_r, 0);
+    if (ready && gl == 0) {
+      d.ready_list[base_r + __popc(br & lt)] = i;
       d.elem_ready[i] = epoch;
     }
-    if (gl < 3) {
-      const int n = d.tri[3 * i + gl];
+    // its three vertices move to tn; the first to claim a node lists it
+    bool claim = false;
+    int n = -1;
+    if (ready && gl < 3) {
+      n = d.tri[3 * i + gl];
       d.ntn[n] = tn;
-      if (atomicExch(&d.node_moved[n], epoch) != epoch) {
-        const int s2 = atomicAdd(&d.cnt->n_moved, 1);
-        d.moved_list[s2] = n;
-      }
+      claim = atomicExch(&d.node_moved[n], epoch) != epoch;
     }
+    const unsigned bm = __ballot_sync(0xffffffffu, claim);
+    int base_m = 0;
+    if (lane == 0 && bm) base_m = atomicAdd(&d.cnt->n_moved, __popc(bm));
+    base_m = __shfl_sync(0xffffffffu, base_m, 0);
+    if (claim) d.moved_list[base_m + __popc(bm & lt)] = n;
   }
 }
 
