@@ -633,7 +633,7 @@ int dalloc(aw_ctx* c, T** p, size_t n) {
 
 template <class T>
 int dupload(aw_ctx* c, const T** out, const std::vector<T>& v) {
-  T* p;
+  T* p = nullptr;
   int rc = dalloc(c, &p, v.size());
   if (rc) return rc;
   if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
