@@ -25,7 +25,8 @@
  *     vertices' Voronoi sets, closed under symmetry (Sec. 2.2).
  *  R4 constrained least squares: exact on T_i (w_0 = Q_i), least squares on
  *     the other members; Dubiner basis in T_i's reference frame; sigma sums
- *     1 <= alpha+beta <= M; weights per conserved variable (eq. weno).
+ *     1 <= alpha+beta <= M; the fields the weights act on are those of R10
+ *     (eq. weno).
  *  R5 virtual geometry X~ = X^n + dt_j * int_0^tau* V_h(vertex) dtau and
  *     virtual average = reference-triangle average of q_h at tau*; a stencil
  *     element already at t_i uses its real data (eqs. virtGeom,
