@@ -1,5 +1,6 @@
 // Kernels of one LTS sweep (Sec. 2.6) on sm_103a, all FP64, launched in this
-// order (one captured CUDA graph per sweep):
+// order (one captured CUDA graph per sweep; k_nodes_grp and k_edges are two
+// parallel branches of it):
 //   k_ready        update criterion on S^W (eq. WENOupdate) for the candidate
 //                  elements; compaction of the ready elements and their nodes
 //   k_nodes_grp    node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
@@ -14,7 +15,8 @@
 //                  vertex displacement polynomials)
 //   k_finish       commit the moved nodes, list the next sweep's candidates,
 //                  reset the per-sweep counters
-// Work lists are compacted with atomics on warp-aggregated slots; every
+// Work lists are compacted with atomics on warp-aggregated slots (the ready
+// list and the moved nodes by warp ballot); every
 // per-element and per-node sum runs in a fixed order, so results do not
 // depend on the order of the lists.
 #include <algorithm>
