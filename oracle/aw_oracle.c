@@ -15,7 +15,11 @@
  *     at least 1, clipped so that t + dt <= t_end (Sec. 2.1, eq. updateFV).
  *  R2 Jacobi sweep: the ready set and phase A (node motion, space-time fluxes,
  *     FV update) use the sweep-start state; phase B (projection, WENO, dt,
- *     predictor) runs on the post-update state (Sec. 2.6).
+ *     predictor) runs on the post-update state (Sec. 2.6).  The paper fixes
+ *     no order between ready neighbours, so the rule itself is parity
+ *     unpinned; the sweep is pinned through what it must keep (GCL,
+ *     conservation, free stream, LTS with equal steps = GTS, exact update
+ *     counts, the exact Sod solution and the designed order).
  *  R3 stencil rule: central = n_e nearest centroids within M+1 vertex-
  *     neighbour layers; sector s = i plus the n_e-1 nearest elements whose
  *     centroid lies in the closed cone (primary: spanned by the rays from
