@@ -1623,6 +1623,17 @@ int oc_get_schedule(const oc_ctx* c, int64_t* out) {
   return OC_OK;
 }
 
+int oc_set_schedule(oc_ctx* c, int64_t k, const int64_t* log) {
+  if (!c || !c->tri || k < 1 || !log) return OC_INVALID;
+  if (c->cfg.gts || c->Tsw > 0) return fail(c, OC_INVALID, "the schedule log is for local time stepping");
+  free(c->sched_log);
+  c->sched_log = (int64_t*)malloc(sizeof(int64_t) * (size_t)c->ne_ * (size_t)k);
+  if (!c->sched_log) return fail(c, OC_INVALID, "out of memory");
+  memcpy(c->sched_log, log, sizeof(int64_t) * (size_t)c->ne_ * (size_t)k);
+  c->sched_k = k;
+  return OC_OK;
+}
+
 /* one cycle of the LTS algorithm under the Jacobi reading R2 (Sec. 2.6) */
 int oc_sweep(oc_ctx* c, int64_t* n_updated) {
   if (!c || !c->have_state) return OC_STATE;

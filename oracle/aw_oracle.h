@@ -60,6 +60,9 @@ int oc_load_state_xy(oc_ctx* c, const double* Q, const double* xy);
    log survives oc_load_state so that perturbed runs replay a base run */
 int oc_schedule(oc_ctx* c, int mode, int64_t k);
 int oc_get_schedule(const oc_ctx* c, int64_t* out); /* [n_tris][k] */
+/* load a schedule log [n_tris][k] (the layout oc_get_schedule returns);
+   oc_schedule(c, 2, 0) then replays it */
+int oc_set_schedule(oc_ctx* c, int64_t k, const int64_t* log);
 int oc_sweep(oc_ctx* c, int64_t* n_updated);
 int oc_get_elem(const oc_ctx* c, double* Q, double* QM, double* HM, int64_t* t,
                 int64_t* dt, double* X, int64_t* count, double* qhat);

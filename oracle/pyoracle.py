@@ -59,6 +59,7 @@ def _load():
             lib.oc_load_state_xy.argtypes = [P, P, P]
             lib.oc_schedule.argtypes = [P, C.c_int, C.c_int64]
             lib.oc_get_schedule.argtypes = [P, P]
+            lib.oc_set_schedule.argtypes = [P, C.c_int64, P]
             lib.oc_sweep.argtypes = [P, C.POINTER(C.c_int64)]
             lib.oc_get_elem.argtypes = [P] + [P] * 8
             lib.oc_set_elem.argtypes = [P] + [P] * 8
@@ -162,6 +163,12 @@ class Oracle:
         out = np.empty((self.n_tris, self._sched_k), np.int64)
         self._check(self.lib.oc_get_schedule(self.h, _ptr(out)))
         return out
+
+    def set_schedule(self, log):
+        """Load a schedule log [n_tris][k]; schedule(2) then replays it."""
+        log = np.ascontiguousarray(log, dtype=np.int64)
+        self._check(self.lib.oc_set_schedule(self.h, log.shape[1], _ptr(log)))
+        self._sched_k = log.shape[1]
 
     def sweep(self):
         n = C.c_int64(0)

@@ -291,6 +291,42 @@ def test_lts_invariant_and_counts():
     assert total < gtotal
 
 
+@pytest.mark.parametrize("case,M", [("vortex", 1), ("vortex", 2), ("sod", 2)])
+def test_local_steps_forced_to_the_global_step_reproduce_gts(case, M):
+    """The Jacobi sweep (reading R2) reduces to global time stepping when every
+    element takes the same step: a local-step run that replays the global
+    step of each step of a GTS run for every element (eq. WENOupdate then
+    marks every element ready in every sweep, Sec. 2.6) reproduces the GTS
+    run's states, predictors, nodes and counts bit for bit."""
+    mesh, Q = W.vortex(8) if case == "vortex" else W.sod_tube(20, 4)
+    t_end = 5.0 if case == "vortex" else 0.2  # several global steps before t_end
+    ne = mesh["tri"].shape[0]
+    n_steps = 6
+    g = Oracle(order_M=M, t_end=t_end, gts=True)
+    g.load_mesh(mesh)
+    g.load_state(Q)
+    e = g.get_elem()
+    assert np.all(e["dt"] == e["dt"][0])
+    steps = [int(e["dt"][0])]
+    for _ in range(n_steps):
+        assert g.sweep() == ne
+        e = g.get_elem()
+        assert np.all(e["dt"] == e["dt"][0])
+        steps.append(int(e["dt"][0]))
+    o = Oracle(order_M=M, t_end=t_end)
+    o.load_mesh(mesh)
+    o.set_schedule(np.tile(np.asarray(steps, np.int64), (ne, 1)))
+    o.schedule("replay")
+    o.load_state(Q)
+    for _ in range(n_steps):
+        assert o.sweep() == ne
+    eg, eo = g.get_elem(), o.get_elem()
+    for k in ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat"):
+        assert np.array_equal(eg[k], eo[k]), k
+    for a, b in zip(g.get_nodes(), o.get_nodes()):
+        assert np.array_equal(a, b)
+
+
 def test_sod_star_state_golden():
     vals = np.loadtxt(os.path.join(GOLDEN, "sod_star_state.txt"))
     p, u, rl, rr = riemann_exact.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
