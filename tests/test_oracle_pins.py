@@ -236,8 +236,14 @@ def test_free_stream_on_moving_periodic_mesh(M):
     QM_expected = HM[:, :1] * f + HM[:, 1:2] * gg + HM[:, 2:3] * q0
     assert np.abs(e["QM"] - QM_expected).max() < 1e-12
     assert np.abs(e["QM"]).max() > 1e-3
-    X, _ = o.get_nodes()
+    X, tn = o.get_nodes()
     assert np.abs(X - mesh["xy"]).max() > 1e-3  # the mesh did move
+    # node solver (eqs. NScs.weights, NodesVel, newVertex, reading R7): in a
+    # uniform flow every node has moved by v times its own time, whatever its
+    # Voronoi elements' times and masses
+    shift = np.outer(tn * o.tick, [u, v])
+    assert np.abs(X - mesh["xy"] - shift).max() < 1e-12
+    assert len(np.unique(tn)) > 1  # the nodes are at different times (LTS)
     assert o.diag()["gcl_max"] < 1e-13
 
 
