@@ -247,6 +247,50 @@ def test_free_stream_on_moving_periodic_mesh(M):
     assert o.diag()["gcl_max"] < 1e-13
 
 
+@pytest.mark.parametrize("M,n_sweeps", [(1, 30), (2, 40)])
+def test_translating_linear_density_is_exact_under_lts(M, n_sweeps):
+    """An entropy wave rho = 1 + 0.2 x + 0.1 y carried by a uniform flow
+    (u, v, p constant) is an exact solution of the Euler equations (Sec. 3,
+    eq. eulerTerms) that every part of the scheme represents exactly for
+    M >= 1: the linear data are reproduced by each stencil's constrained least
+    squares (eq. intConsRec) whatever the nonlinear weights, the predictor
+    carries them exactly, the two traces at an edge agree, and the nodes move
+    with the flow.  With local time steps the stencil members sit at other
+    times, so the reconstruction sees them only through the virtual projection
+    (eqs. virtGeom, virtCellaverage): away from the transmissive boundary,
+    whose zeroth-order outer state (reading R15) is not exact, every average
+    must equal the exact one at the element's own time on its moved cell."""
+    g = 1.4
+    mesh = W.shock_tube_mesh(30, 30, 1.0, 1.0, jitter=0.2, seed=W.SEED_BASE + 50)
+    mesh["bc"] = np.where(mesh["bc"] == W.BC_WALL, W.BC_TRANSMISSIVE, mesh["bc"]).astype(np.int8)
+    u, v, p = 0.5, 0.3, 1.0
+
+    def rho(x, y):
+        return 1.0 + 0.2 * x + 0.1 * y
+
+    def cons(x, y):  # the average of a linear field over a triangle is its centroid value
+        r = rho(x, y)
+        return np.stack([r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)], 1)
+
+    c0 = mesh["xy"][mesh["tri"]].mean(1)
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(cons(c0[:, 0], c0[:, 1]))
+    for _ in range(n_sweeps):
+        o.sweep()
+    e = o.get_elem()
+    t = e["t"] * o.tick
+    c = e["X"].reshape(-1, 3, 2).mean(1)
+    exact = cons(c[:, 0] - u * t, c[:, 1] - v * t)
+    inner = np.minimum.reduce([c0[:, 0], 1 - c0[:, 0], c0[:, 1], 1 - c0[:, 1]]) > 0.25
+    assert len(np.unique(t[inner])) > 3 and e["count"][inner].max() >= 2  # local steps at work
+    assert np.abs(e["Q"][inner] - exact[inner]).max() < 1e-13 * np.abs(exact).max()
+    # the moved cells are the initial ones translated by the flow: node motion
+    X0 = mesh["xy"][mesh["tri"]].reshape(-1, 6)
+    shift = np.tile(np.stack([u * t, v * t], 1), (1, 3))
+    assert np.abs(e["X"][inner] - X0[inner] - shift[inner]).max() < 1e-14
+
+
 @pytest.mark.parametrize("M,gts", [(1, False), (2, False), (2, True)])
 def test_conservation_and_gcl_vortex(M, gts):
     mesh, Q = W.vortex(10)
