@@ -247,6 +247,45 @@ def test_free_stream_on_moving_periodic_mesh(M):
     assert o.diag()["gcl_max"] < 1e-13
 
 
+@pytest.mark.parametrize("cfl", [0.5, 0.3])
+def test_initial_local_time_step_closed_form(cfl):
+    """Eq. timestep with readings R9 and R1 on a uniform state: the step of
+    element i is CFL min_j d_j / (|v| + c) over i and its edge neighbours,
+    d_j = 4 |T_j| / perimeter_j (the incircle diameter), floored to whole
+    ticks; the global step is the minimum over the mesh."""
+    g = 1.4
+    mesh = W.shock_tube_mesh(20, 20, 1.0, 1.0, jitter=0.2, seed=W.SEED_BASE + 51)
+    ne = mesh["tri"].shape[0]
+    q0 = W.prim_to_cons(1.3, 0.3, -0.2, 0.8, g)
+    o = Oracle(order_M=2, cfl=cfl, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(np.tile(q0, (ne, 1)))
+    P = mesh["xy"][mesh["tri"]]
+    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                        - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
+    per = sum(np.linalg.norm(P[:, (k + 1) % 3] - P[:, k], axis=1) for k in range(3))
+    d = 4.0 * area / per
+    lam = math.hypot(0.3, -0.2) + math.sqrt(g * 0.8 / 1.3)
+    edges = {}
+    for i, t in enumerate(mesh["tri"]):
+        for k in range(3):
+            edges.setdefault(tuple(sorted((t[k], t[(k + 1) % 3]))), []).append(i)
+    dmin = d.copy()
+    for owners in edges.values():
+        if len(owners) == 2:
+            a, b = owners
+            dmin[a] = min(dmin[a], d[b])
+            dmin[b] = min(dmin[b], d[a])
+    expect = np.floor(cfl * dmin / lam / o.tick).astype(np.int64)
+    got = o.get_elem()["dt"]
+    assert np.abs(got - expect).max() <= 1  # a tick boundary may round either way
+    assert np.mean(got == expect) > 0.99
+    gts = Oracle(order_M=2, cfl=cfl, t_end=1.0, gts=True)
+    gts.load_mesh(mesh)
+    gts.load_state(np.tile(q0, (ne, 1)))
+    assert np.all(gts.get_elem()["dt"] == got.min())
+
+
 @pytest.mark.parametrize("M,n_sweeps", [(1, 30), (2, 40)])
 def test_translating_linear_density_is_exact_under_lts(M, n_sweeps):
     """An entropy wave rho = 1 + 0.2 x + 0.1 y carried by a uniform flow
