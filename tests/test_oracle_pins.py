@@ -247,6 +247,47 @@ def test_free_stream_on_moving_periodic_mesh(M):
     assert o.diag()["gcl_max"] < 1e-13
 
 
+@pytest.mark.parametrize("M", [1, 2])
+def test_node_solver_mass_weighted_time_averaged_velocity(M):
+    """The node solver NS_cs (eqs. eqnNScs, NScs.weights, dtau, NodesVel,
+    newVertex; reading R7) recomputed here from the predictor: a moved node k
+    of the first sweep moves by sum_j mu_j D_j / sum_j mu_j over its Voronoi
+    elements j, mu_j = rho_j |T_j|, D_j = dt_j times the integral over
+    [tau0, tau1] of the time interpolant (Gauss-Lobatto nodes) of the nodal
+    velocities (rho u, rho v) / rho at the vertex."""
+    mesh, Q = W.vortex(8)
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    e0 = o.get_elem()
+    X0, t0 = o.get_nodes()
+    assert np.all(t0 == 0) and np.all(e0["t"] == 0)
+    o.sweep()
+    X1, t1 = o.get_nodes()
+    moved = np.nonzero(t1 != t0)[0]
+    assert len(moved) > 3
+    Mc = (M + 1) * (M + 2) // 2
+    vnode = (0, M, Mc - 1)
+    gll = {1: [0.0, 1.0], 2: [0.0, 0.5, 1.0]}[M]
+    P = e0["X"].reshape(-1, 3, 2)
+    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                        - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
+    for n in moved:
+        num, den = np.zeros(2), 0.0
+        for j, k in zip(*np.nonzero(mesh["tri"] == n)):
+            tau1 = t1[n] / e0["dt"][j]
+            assert 0.0 < tau1 <= 1.0
+            qs = e0["qhat"][j].reshape(M + 1, Mc, 4)[:, vnode[k]]  # the vertex at every time node
+            D = np.empty(2)
+            for c in range(2):
+                poly = np.polynomial.Polynomial.fit(gll, qs[:, 1 + c] / qs[:, 0], M).convert().integ()
+                D[c] = e0["dt"][j] * o.tick * (poly(tau1) - poly(0.0))
+            mu = e0["Q"][j, 0] * area[j]
+            num += mu * D
+            den += mu
+        assert np.abs(X1[n] - X0[n] - num / den).max() < 1e-13
+
+
 @pytest.mark.parametrize("cfl", [0.5, 0.3])
 def test_initial_local_time_step_closed_form(cfl):
     """Eq. timestep with readings R9 and R1 on a uniform state: the step of
