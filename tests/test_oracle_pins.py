@@ -113,6 +113,22 @@ def test_rusanov_consistency_and_wall():
     assert abs(F[0]) < 1e-15 and abs(F[3]) < 1e-15
     smax = abs(v * nw[1]) + math.sqrt(g * p / rho) * 0.3
     assert abs(F[2] - ((rho * v * v + p) * nw[1] + smax * q[2])) < 1e-13
+    # two states through a moving surface (eq. rusanov): the dissipation speed
+    # is the largest |lambda| of the ALE Jacobian, |v . n_xy + n_t| + c |n_xy|
+    # (V . n = -n_t / |n_xy|), on either side
+    qr = np.array([0.9, -0.2, 0.1, 2.2])
+
+    def phys(qq):
+        r, uu, vv = qq[0], qq[1] / qq[0], qq[2] / qq[0]
+        pp = (g - 1) * (qq[3] - 0.5 * r * (uu * uu + vv * vv))
+        ff = np.array([r * uu, r * uu * uu + pp, r * uu * vv, uu * (qq[3] + pp)])
+        gq = np.array([r * vv, r * uu * vv, r * vv * vv + pp, vv * (qq[3] + pp)])
+        lam = abs(uu * n[0] + vv * n[1] + n[2]) + math.sqrt(g * pp / r) * math.hypot(n[0], n[1])
+        return ff * n[0] + gq * n[1] + qq * n[2], lam
+
+    (fl, ll), (fr, lr) = phys(q), phys(qr)
+    expect = 0.5 * (fl + fr) - 0.5 * max(ll, lr) * (qr - q)
+    assert np.allclose(o.flux(q, qr, n), expect, rtol=1e-13, atol=1e-14)
 
 
 # ---------------------------------------------------------------- reconstruction
