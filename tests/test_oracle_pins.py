@@ -133,6 +133,106 @@ def test_rusanov_consistency_and_wall():
 
 # ---------------------------------------------------------------- reconstruction
 
+@pytest.mark.parametrize("M", [2, 3])
+def test_weno_reconstruction_rebuilt_from_its_definition(M):
+    """The WENO reconstruction of an interior element rebuilt in numpy from
+    the definitions, independently of the oracle's Dubiner basis, Duffy rows,
+    Householder solves and smoothness matrix: per stencil the least-squares
+    polynomial exact on T_i (eq. intConsRec, reading R4) in centred monomials
+    of T_i's reference coordinates (numpy lstsq); oscillation indicators
+    sum_{1 <= a+b <= M} int_Te (d^{a+b} w / dxi^a deta^b)^2 per characteristic
+    field of dF/dQ.n at Q_i, n along the central stencil's density gradient at
+    the centroid (reading R10); weights lambda_s / (sigma + 1e-14)^8 with
+    lambda = 1e5 for the central stencil and 1 for the others (eq. weno)."""
+    g = 1.4
+
+    def prim(x, y):
+        r = 1.5 + 0.4 * np.sin(5 * x + 1) * np.cos(4 * y)
+        u = 0.3 * np.cos(3 * y)
+        v = -0.2 * np.sin(4 * x)
+        p = 1.0 + 0.3 * np.cos(5 * x - 2 * y)
+        return np.stack([r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)], -1)
+
+    mesh = W.shock_tube_mesh(12, 12, 1.0, 1.0, jitter=0.2, seed=W.SEED_BASE + 52)
+    Q = W.cell_average(mesh, prim, W._duffy_rule(6))
+    o = Oracle(order_M=M, t_end=1.0)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    P = mesh["xy"][mesh["tri"]]
+    mono = [(a - b, b) for a in range(1, M + 1) for b in range(a + 1)]  # xi^p eta^q, 1 <= p+q <= M
+    qs, qt, qw = duffy(6)  # reference-triangle rule, weights sum to 1/2
+    ref_mean = np.array([np.sum(qw * qs ** p * qt ** q) * 2.0 for p, q in mono])
+
+    def basis(xi, eta):  # centred monomials: zero mean over the reference triangle
+        return np.stack([xi ** p * eta ** q for p, q in mono], -1) - ref_mean
+
+    def dbasis(xi, eta, a, b):  # d^{a+b} / dxi^a deta^b of the monomials
+        out = []
+        for p, q in mono:
+            if a > p or b > q:
+                out.append(np.zeros_like(xi))
+            else:
+                cp = math.factorial(p) / math.factorial(p - a)
+                cq = math.factorial(q) / math.factorial(q - b)
+                out.append(cp * cq * xi ** (p - a) * eta ** (q - b))
+        return np.stack(out, -1)
+
+    sig_mat = np.zeros((len(mono), len(mono)))
+    for a in range(M + 1):
+        for b in range(M + 1 - a):
+            if a + b == 0:
+                continue
+            D = dbasis(qs, qt, a, b)
+            sig_mat += np.einsum("q,qa,qb->ab", qw, D, D)
+    checked = 0
+    for i in range(mesh["tri"].shape[0]):
+        members, _ = o.stencils(i)
+        if np.any(members < 0) or checked >= 6:
+            continue
+        X0, J = P[i, 0], np.column_stack([P[i, 1] - P[i, 0], P[i, 2] - P[i, 0]])
+        Ji = np.linalg.inv(J)
+
+        def to_ref(pts):
+            return (pts - X0) @ Ji.T
+
+        coef = []
+        for st in members:
+            assert st[0] == i
+            rows = []
+            for j in st[1:]:
+                pts = P[j, 0] + np.outer(qs, P[j, 1] - P[j, 0]) + np.outer(qt, P[j, 2] - P[j, 0])
+                r = to_ref(pts)
+                rows.append(2.0 * qw @ basis(r[:, 0], r[:, 1]))
+            c, *_ = np.linalg.lstsq(np.array(rows), Q[st[1:]] - Q[i], rcond=None)
+            coef.append(c)  # [n_basis][4]
+        # characteristic fields (reading R10)
+        c3 = np.array(1.0 / 3.0)
+        grad_ref = np.array([dbasis(c3, c3, 1, 0) @ coef[0][:, 0], dbasis(c3, c3, 0, 1) @ coef[0][:, 0]])
+        gx, gy = Ji.T @ grad_ref
+        nx, ny = gx / math.hypot(gx, gy), gy / math.hypot(gx, gy)
+        rho, u, v = Q[i, 0], Q[i, 1] / Q[i, 0], Q[i, 2] / Q[i, 0]
+        p = (g - 1) * (Q[i, 3] - 0.5 * rho * (u * u + v * v))
+        cs, H, un, ut = math.sqrt(g * p / rho), (Q[i, 3] + p) / rho, u * nx + v * ny, -u * ny + v * nx
+        R = np.array([[1, 1, 0, 1], [u - cs * nx, u, -ny, u + cs * nx], [v - cs * ny, v, nx, v + cs * ny],
+                      [H - cs * un, 0.5 * (u * u + v * v), ut, H + cs * un]])
+        L = np.linalg.inv(R)
+        chars = [c @ L.T for c in coef]  # [n_basis][field]
+        sig = np.array([[ch[:, r] @ sig_mat @ ch[:, r] for r in range(4)] for ch in chars])
+        lam = np.array([1e5] + [1.0] * 6)[:, None]
+        om = lam / (sig + 1e-14) ** 8
+        om /= om.sum(0)
+        wchar = sum(om[s_][None, :] * chars[s_] for s_ in range(7))
+        w = wchar @ R.T  # back to conserved variables, [n_basis][4]
+        pts = np.array([[0.2, 0.3], [0.6, 0.1], [0.1, 0.7]]) @ J.T + X0
+        r = to_ref(pts)
+        expect = Q[i] + basis(r[:, 0], r[:, 1]) @ w
+        got = o.reconstruct_eval(i, pts)
+        assert np.abs(got - expect).max() < 1e-13 * np.abs(Q[i]).max(), (i, got, expect)
+        assert sig.min() > 1e-8  # the weights are not at their epsilon floor
+        checked += 1
+    assert checked == 6
+
+
 @pytest.mark.parametrize("M", [1, 2, 3])
 def test_weno_reproduces_polynomials(M):
     """Cell averages of any polynomial of degree <= M are reproduced exactly
