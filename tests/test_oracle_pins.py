@@ -299,6 +299,78 @@ def test_predictor_constant_state_is_exact(M):
 
 
 @pytest.mark.parametrize("M", [1, 2, 3])
+def test_predictor_rebuilt_from_its_definition(M):
+    """The space-time Galerkin predictor with the isoparametric geometry
+    (eqs. PDECG, pdef, Jac, thetaSol, Ktau, CGfinal, ODEmesh, Vdof, newVertPos;
+    reading R6) rebuilt in numpy: nodal basis = lattice (i/M, j/M) x
+    Gauss-Lobatto times; per lattice node and variable the tau > 0 dofs solve
+    K_t^{11} q_{>0} = dt (M_t P)_{>0} - K_t^{10} q_0 with K_t = int phi_k phi_l',
+    M_t = int phi_k phi_l over [0, 1]; P = -(Q_xi xi_t + Q_eta eta_t + f_xi xi_x
+    + f_eta eta_x + g_xi xi_y + g_eta eta_y) with the metric of the node's
+    current space-time geometry, x updated the same way with V = (u, v);
+    initial guess w_h on every slice and a static geometry; M+1 Picard
+    iterations.  Lagrange bases come from numpy polynomial fits."""
+    g = 1.4
+    o = Oracle(order_M=M)
+    Mc, Nt = o.Mc, M + 1
+    lat = np.array([(i / M, j / M) for j in range(M + 1) for i in range(M + 1 - j)])
+    gll = {1: [0.0, 1.0], 2: [0.0, 0.5, 1.0],
+           3: [0.0, 0.5 - 0.5 / math.sqrt(5.0), 0.5 + 0.5 / math.sqrt(5.0), 1.0]}[M]
+    # spatial nodal derivative matrices from the monomial Vandermonde matrix
+    mono = [(a - b, b) for a in range(M + 1) for b in range(a + 1)]
+    V = np.array([[x ** p * y ** q for p, q in mono] for x, y in lat])
+    Vx = np.array([[p * x ** max(p - 1, 0) * y ** q if p else 0.0 for p, q in mono] for x, y in lat])
+    Vy = np.array([[q * x ** p * y ** max(q - 1, 0) if q else 0.0 for p, q in mono] for x, y in lat])
+    Dxi, Deta = Vx @ np.linalg.inv(V), Vy @ np.linalg.inv(V)  # [node s][node r]
+    # time Lagrange basis on the Gauss-Lobatto nodes
+    phi = [np.polynomial.Polynomial.fit(gll, np.eye(Nt)[k], M).convert() for k in range(Nt)]
+    Dtau = np.array([[phi[l].deriv()(gll[k]) for l in range(Nt)] for k in range(Nt)])
+    Kt = np.array([[(phi[k] * phi[l].deriv()).integ()(1.0) - (phi[k] * phi[l].deriv()).integ()(0.0)
+                    for l in range(Nt)] for k in range(Nt)])
+    Mt = np.array([[(phi[k] * phi[l]).integ()(1.0) - (phi[k] * phi[l]).integ()(0.0)
+                    for l in range(Nt)] for k in range(Nt)])
+    K11inv, K10 = np.linalg.inv(Kt[1:, 1:]), Kt[1:, :1]
+
+    X6 = np.array([0.1, 0.2, 0.35, 0.18, 0.2, 0.41])
+    P3 = X6.reshape(3, 2)
+    xs = P3[0] + lat[:, :1] * (P3[1] - P3[0]) + lat[:, 1:] * (P3[2] - P3[0])
+    rho = 1.2 + 0.3 * np.sin(4 * xs[:, 0]) + 0.2 * xs[:, 1]
+    u, v = 0.4 + 0.5 * xs[:, 1], -0.3 + 0.6 * xs[:, 0] ** 2
+    p = 1.0 + 0.5 * np.cos(3 * xs[:, 0] + 2 * xs[:, 1])
+    w0 = np.stack([rho, rho * u, rho * v, p / (g - 1) + 0.5 * rho * (u * u + v * v)], 1)
+    dt = 0.03
+    q = np.tile(w0, (Nt, 1, 1))  # [time][space][var]
+    x = np.tile(xs, (Nt, 1, 1))  # [time][space][2]
+    for _ in range(M + 1):
+        r_, uu, vv = q[..., 0], q[..., 1] / q[..., 0], q[..., 2] / q[..., 0]
+        pp = (g - 1) * (q[..., 3] - 0.5 * r_ * (uu * uu + vv * vv))
+        f = np.stack([q[..., 1], q[..., 1] * uu + pp, q[..., 1] * vv, uu * (q[..., 3] + pp)], -1)
+        gq = np.stack([q[..., 2], q[..., 2] * uu, q[..., 2] * vv + pp, vv * (q[..., 3] + pp)], -1)
+        Pn = np.empty_like(q)
+        for t in range(Nt):
+            xx, xe = Dxi @ x[t, :, 0], Deta @ x[t, :, 0]
+            yx, ye = Dxi @ x[t, :, 1], Deta @ x[t, :, 1]
+            xt = np.einsum("u,us->s", Dtau[t], x[:, :, 0]) / dt
+            yt = np.einsum("u,us->s", Dtau[t], x[:, :, 1]) / dt
+            det = xx * ye - xe * yx
+            xix, xiy, etx, ety = ye / det, -xe / det, -yx / det, xx / det
+            xit, ett = -(xix * xt + xiy * yt), -(etx * xt + ety * yt)
+            Pn[t] = -((Dxi @ q[t]) * xit[:, None] + (Deta @ q[t]) * ett[:, None]
+                      + (Dxi @ f[t]) * xix[:, None] + (Deta @ f[t]) * etx[:, None]
+                      + (Dxi @ gq[t]) * xiy[:, None] + (Deta @ gq[t]) * ety[:, None])
+        Vn = np.stack([uu, vv], -1)
+        q_new, x_new = q.copy(), x.copy()
+        q_new[1:] = np.einsum("ab,bsv->asv", K11inv, dt * np.einsum("bc,csv->bsv", Mt[1:], Pn)
+                              - np.einsum("bc,csv->bsv", K10, q[:1]))
+        x_new[1:] = np.einsum("ab,bsv->asv", K11inv, dt * np.einsum("bc,csv->bsv", Mt[1:], Vn)
+                              - np.einsum("bc,csv->bsv", K10, x[:1]))
+        q, x = q_new, x_new
+    got = o.predict(X6, dt, w0).reshape(Nt, Mc, 4)
+    assert np.abs(got - q).max() < 1e-12 * np.abs(q).max()
+    assert np.abs(q[-1] - q[0]).max() > 1e-3 * np.abs(q).max()  # the data did evolve
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
 def test_predictor_order_on_smooth_flow(M):
     """Eulerian mode (V = 0): starting from the exact data, the predictor at
     tau = 1 differs from the convected vortex by O(h^(M+1)) with dt = h/2."""
