@@ -582,6 +582,35 @@ def test_conservation_and_gcl_vortex(M, gts):
     assert inv_ok
 
 
+@pytest.mark.parametrize("M", [1, 2])
+def test_ready_set_is_the_update_criterion(M):
+    """Eq. WENOupdate on the total stencil S^W (Sec. 2.2), in integer ticks
+    (reading R1), recomputed in numpy before every sweep: the elements a sweep
+    updates are exactly those with t_i < t_end and
+    max_{j in S^W_i} t_j <= t_i + dt_i <= min_{j in S^W_i} (t_j + dt_j)."""
+    mesh, Q = W.explosion(0.04)
+    o = Oracle(order_M=M, t_end=0.05)
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    ne = mesh["tri"].shape[0]
+    sw = [o.stencils(i)[1] for i in range(ne)]
+    T = 2 ** 20
+    sweeps = 0
+    while True:
+        e = o.get_elem()
+        t, dt = e["t"], e["dt"]
+        tn = t + dt
+        expect = np.array([t[i] < T and t[sw[i]].max() <= tn[i] <= tn[sw[i]].min() for i in range(ne)])
+        n = o.sweep()
+        upd = o.get_elem()["count"] != e["count"]
+        assert np.array_equal(upd, expect), sweeps
+        assert n == expect.sum()
+        sweeps += 1
+        if n == 0:
+            break
+    assert sweeps > 20 and np.all(o.get_elem()["t"] == T)
+
+
 def test_lts_invariant_and_counts():
     mesh, Q = W.explosion(0.05)
     o = Oracle(order_M=1, t_end=0.05)
