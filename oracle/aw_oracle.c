@@ -117,6 +117,9 @@ struct oc_ctx {
   int periodic;
   double period[2];
   int64_t Tsw;         /* ticks of the global-step start-up, 0 if none */
+  int64_t Ts;          /* sync time in ticks (reading R18): every step is clipped
+                          at it and elements stop there; T unless oc_advance_to
+                          set an earlier time */
   double wall_speed;   /* |(wall_u, wall_v)| */
   int64_t nedges;
   int32_t* edge_nodes; /* [nedges][2] a,b in the owner's orientation */
@@ -1371,6 +1374,7 @@ static void predictor(const oc_ctx* c, const double* X, double dtsec, const doub
    (b) If the predictor ends with a non-positive density or pressure at a
    space-time node, the element keeps w_h at every time slice instead. */
 static int physical(const oc_ctx* c, const double* q) { return q[0] > 0.0 && pressure(c, q) > 0.0; }
+static void nodal_predictor(const oc_ctx* c, int64_t i, const double* w0);
 
 static void element_predictor(const oc_ctx* c, int64_t i, const double* w) {
   double w0[MAXMC * 4];
@@ -1405,6 +1409,12 @@ static void element_predictor(const oc_ctx* c, int64_t i, const double* w) {
       for (int s = 0; s < c->Mc; ++s)
         for (int v = 0; v < 4; ++v) w0[s * 4 + v] = Qi[v] + theta * (w0[s * 4 + v] - Qi[v]);
   }
+  nodal_predictor(c, i, w0);
+}
+
+/* the predictor of element i over its step dt[i] from the nodal values w0 of
+   its (scaled) WENO polynomial, with safeguard (b) */
+static void nodal_predictor(const oc_ctx* c, int64_t i, const double* w0) {
   double* qh = c->qhat + (size_t)i * c->Nst * 4;
   predictor(c, c->X + 6 * i, (double)c->dt[i] * c->tick, w0, qh);
   int ok = 1;
@@ -1428,7 +1438,7 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
     reconstruct(c, i, W + q * c->Mc * 4);
     int64_t ticks = 0;
     const int start = c->t[i] < c->Tsw;  /* global-step start-up (R16) */
-    if (c->t[i] < c->T) {
+    if (c->t[i] < c->Ts) {
       double dts = local_dt(c, i, start ? c->cfg.cfl_start : c->cfg.cfl);
       if (!(dts > 0.0)) {
         rc = fail(c, OC_NONPHYSICAL, "element %lld: non-positive time step", (long long)i);
@@ -1436,6 +1446,7 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
       }
       double r = floor(dts / c->tick);
       int64_t end = start ? c->Tsw : c->T;
+      if (end > c->Ts) end = c->Ts;
       ticks = r > (double)(end - c->t[i]) ? end - c->t[i] : (int64_t)r;
       if (ticks < 1) ticks = 1;
     }
@@ -1479,6 +1490,7 @@ int oc_create(const oc_config* cfg, oc_ctx** out) {
   c->ne = 2 * c->Mc;
   c->nit = cfg->predictor_iters > 0 ? cfg->predictor_iters : c->M + 1;
   c->T = (int64_t)1 << cfg->time_quantum_log2;
+  c->Ts = c->T;
   c->tick = ldexp(cfg->t_end, -cfg->time_quantum_log2);
   c->wall_speed = sqrt(cfg->wall_u * cfg->wall_u + cfg->wall_v * cfg->wall_v);
   c->Tsw = 0;
@@ -1582,6 +1594,7 @@ static int load_state(oc_ctx* c, const double* Q, const double* xy) {
     for (int k = 0; k < 3; ++k) corner(c, i, k, c->nX, c->X + 6 * i + 2 * k);
   }
   for (int64_t n = 0; n < c->nn; ++n) c->nt[n] = 0;
+  c->Ts = c->T;
   int64_t* all = (int64_t*)malloc(sizeof(int64_t) * ne);
   for (int64_t i = 0; i < ne; ++i) all[i] = i;
   int rc = phase_b(c, all, ne);
@@ -1637,7 +1650,7 @@ int oc_set_schedule(oc_ctx* c, int64_t k, const int64_t* log) {
 /* one cycle of the LTS algorithm under the Jacobi reading R2 (Sec. 2.6) */
 int oc_sweep(oc_ctx* c, int64_t* n_updated) {
   if (!c || !c->have_state) return OC_STATE;
-  int64_t ne = c->ne_, nn = c->nn, T = c->T;
+  int64_t ne = c->ne_, nn = c->nn, T = c->Ts;
   int Mc = c->Mc, Nt = c->Nt, Nst = c->Nst;
   /* update criterion on the total stencil (eq. WENOupdate) */
   char* ready = (char*)calloc(ne, 1);
@@ -1857,6 +1870,61 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
   if (rc != OC_OK) c->have_state = 0;
   (void)Mc;
   return rc;
+}
+
+/* Run sweeps until every element reached the sync time t (reading R18: t is
+   t_end or a whole number of ticks, not behind any element's time) or
+   max_sweeps sweeps ran.  Moving the sync time back cuts every step that
+   crosses it back to it and re-solves that element's predictor over the
+   shorter step from its own tau = 0 dofs (the scaled WENO values); moving
+   it forward gives each element stopped at the old sync time its phase B
+   (reconstruction, step, predictor) at that time. */
+int oc_advance_to(oc_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done, int64_t* updates_done) {
+  if (!c || !c->have_state) return OC_STATE;
+  int64_t ne = c->ne_, Tn = c->T;
+  if (t < c->cfg.t_end) {
+    double r = t / c->tick;
+    if (!(r >= 0.0) || r != floor(r)) return fail(c, OC_INVALID, "the sync time is not a whole number of ticks");
+    Tn = (int64_t)r;
+  }
+  for (int64_t i = 0; i < ne; ++i)
+    if (c->t[i] > Tn) return fail(c, OC_INVALID, "element %lld is beyond the sync time", (long long)i);
+  if (Tn != c->Ts && c->sched_mode != 0) return fail(c, OC_INVALID, "a sync time before t_end with a frozen schedule");
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (ne > 0 ? ne : 1));
+  int64_t n = 0;
+  int rc = OC_OK;
+  if (Tn < c->Ts) {
+    for (int64_t i = 0; i < ne; ++i)
+      if (c->t[i] < Tn && c->t[i] + c->dt[i] > Tn) {
+        c->dt[i] = Tn - c->t[i];
+        double w0[MAXMC * 4];
+        memcpy(w0, c->qhat + (size_t)i * c->Nst * 4, sizeof(double) * c->Mc * 4);
+        nodal_predictor(c, i, w0);
+      }
+    c->Ts = Tn;
+  } else if (Tn > c->Ts) {
+    for (int64_t i = 0; i < ne; ++i)
+      if (c->t[i] == c->Ts) list[n++] = i;
+    c->Ts = Tn;
+    rc = phase_b(c, list, n);
+  }
+  free(list);
+  if (rc != OC_OK) {
+    c->have_state = 0;
+    return rc;
+  }
+  int64_t sweeps = 0, updates = 0;
+  while (sweeps < max_sweeps) {
+    int64_t u = 0;
+    rc = oc_sweep(c, &u);
+    if (rc != OC_OK) return rc;
+    if (u == 0) break;
+    updates += u;
+    ++sweeps;
+  }
+  if (sweeps_done) *sweeps_done = sweeps;
+  if (updates_done) *updates_done = updates;
+  return OC_OK;
 }
 
 int oc_get_elem(const oc_ctx* c, double* Q, double* QM, double* HM, int64_t* t, int64_t* dt, double* X,

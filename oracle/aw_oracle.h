@@ -64,6 +64,9 @@ int oc_get_schedule(const oc_ctx* c, int64_t* out); /* [n_tris][k] */
    oc_schedule(c, 2, 0) then replays it */
 int oc_set_schedule(oc_ctx* c, int64_t k, const int64_t* log);
 int oc_sweep(oc_ctx* c, int64_t* n_updated);
+/* sweeps until every element reached the sync time t (t_end, or a whole
+   number of ticks not behind any element: reading R18) or max_sweeps ran */
+int oc_advance_to(oc_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done, int64_t* updates_done);
 int oc_get_elem(const oc_ctx* c, double* Q, double* QM, double* HM, int64_t* t,
                 int64_t* dt, double* X, int64_t* count, double* qhat);
 int oc_set_elem(oc_ctx* c, const double* Q, const double* QM, const double* HM,

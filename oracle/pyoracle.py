@@ -61,6 +61,7 @@ def _load():
             lib.oc_get_schedule.argtypes = [P, P]
             lib.oc_set_schedule.argtypes = [P, C.c_int64, P]
             lib.oc_sweep.argtypes = [P, C.POINTER(C.c_int64)]
+            lib.oc_advance_to.argtypes = [P, C.c_double, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             lib.oc_get_elem.argtypes = [P] + [P] * 8
             lib.oc_set_elem.argtypes = [P] + [P] * 8
             lib.oc_get_nodes.argtypes = [P, P, P]
@@ -184,6 +185,13 @@ class Oracle:
             total += n
             sweeps += 1
         return sweeps, total
+
+    def advance_to(self, t, max_sweeps=10 ** 9):
+        """Sweeps until every element reached the sync time t (t_end or a
+        whole number of ticks; reading R18); returns (sweeps, updates)."""
+        ns, nu = C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.oc_advance_to(self.h, float(t), int(max_sweeps), C.byref(ns), C.byref(nu)))
+        return ns.value, nu.value
 
     def get_elem(self):
         n, Nst = self.n_tris, self.Nst
