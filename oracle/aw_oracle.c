@@ -79,6 +79,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Phase marks of the operation-counting build (aw_oracle_count.cpp); no
+   effect in this build. */
+#ifndef OC_PHASE
+#define OC_PHASE(p) ((void)0)
+#endif
+
 #define MAXM 3
 #define MAXMC 10
 #define MAXNT 4
@@ -1435,7 +1441,9 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
   int rc = OC_OK;
   for (int64_t q = 0; q < n; ++q) {
     int64_t i = list[q];
+    OC_PHASE(OC_PH_RECON);
     reconstruct(c, i, W + q * c->Mc * 4);
+    OC_PHASE(OC_PH_DT);
     int64_t ticks = 0;
     const int start = c->t[i] < c->Tsw;  /* global-step start-up (R16) */
     if (c->t[i] < c->Ts) {
@@ -1466,8 +1474,10 @@ static int phase_b(oc_ctx* c, const int64_t* list, int64_t n) {
   if (rc == OC_OK && gmin != INT64_MAX)
     for (int64_t q = 0; q < n; ++q)
       if (c->dt[list[q]] > 0 && (c->cfg.gts || c->t[list[q]] < c->Tsw)) c->dt[list[q]] = gmin;
+  OC_PHASE(OC_PH_PRED);
   if (rc == OC_OK)
     for (int64_t q = 0; q < n; ++q) element_predictor(c, list[q], W + q * c->Mc * 4);
+  OC_PHASE(OC_PH_OTHER);
   free(W);
   return rc;
 }
@@ -1688,6 +1698,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
         moved[n] = 1;
         tnew[n] = c->t[i] + c->dt[i];
       }
+  OC_PHASE(OC_PH_NODES);
   /* node solver NS_cs: mass-weighted, time-integrated vertex velocities
      (eqs. eqnNScs, eqn.NScs.weights, dtau, NodesVel, newVertex; R7) */
   for (int64_t n = 0; n < nn; ++n) {
@@ -1726,6 +1737,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
     Xnew[2 * n] = c->nX[2 * n] + D[0];
     Xnew[2 * n + 1] = c->nX[2 * n + 1] + D[1];
   }
+  OC_PHASE(OC_PH_FLUX);
   /* space-time edge and vertex fluxes through the surfaces swept by every
      edge with a moved endpoint (eqs. spacetimenodes, rusanov, STint; R8) */
   int64_t ned = c->nedges;
@@ -1794,6 +1806,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
         for (int d = 0; d < 3; ++d) N[3 * ed + d] += wq * n[d];
       }
   }
+  OC_PHASE(OC_PH_UPDATE);
   /* finite volume update with memory variables (eqs. PDEfinal, Qm2, gcl) */
   int rc = OC_OK;
   double* Qold = (double*)malloc(sizeof(double) * 4 * ne);
@@ -1850,6 +1863,7 @@ int oc_sweep(oc_ctx* c, int64_t* n_updated) {
     }
   }
   free(Qold);
+  OC_PHASE(OC_PH_OTHER);
   memcpy(c->nX, Xnew, sizeof(double) * 2 * nn);
   memcpy(c->nt, tnew, sizeof(int64_t) * nn);
   if (rc == OC_OK) {

@@ -96,3 +96,22 @@ def _oracle_fd(args):
         e = o.get_elem()
         out.append(_J(e["Q"], e["X"], mask))
     return (out[0] - out[1]) / (2 * H), log
+
+
+def _oracle_tlm(args):
+    """The oracle's tangent-linear product J'(x0) v in a process of its own
+    (spawned): the dual-number build of the oracle run from the seeded
+    tangents (vQ, vxy), the objective's derivative applied to the final
+    tangents.  The schedule is the run's own (values equal the plain
+    oracle's bit for bit); it is returned for comparison."""
+    mesh, Q0, order, n_sweeps, vQ, vxy = args
+    from oracle.pyoracle import TangentOracle
+    o = TangentOracle(order_M=order, t_end=1.0)
+    o.load_mesh(mesh)
+    o.schedule("record", n_sweeps + 2)
+    o.load_state_xy(Q0, mesh["xy"], vQ, vxy)
+    for _ in range(n_sweeps):
+        o.sweep()
+    val, tan = o.get_elem()
+    gQ, gX = _dJ(val["Q"], val["X"], _mask(mesh))
+    return float(np.sum(gQ * tan["Q"]) + np.sum(gX * tan["X"])), o.get_schedule()
