@@ -69,15 +69,21 @@ def recon_flops(M: int, members: float) -> float:
     return members * per_member + 7 * per_stencil + weights + dt
 
 
-def hbm_bytes_per_update(M: int, sw_per_elem: float) -> float:
+def hbm_bytes_per_update(M: int, sw_per_elem: float, members_per_elem: float = 0.0) -> float:
     """Compulsory DRAM bytes of one element update with perfect on-chip reuse
     in a sweep: read its state, ticks, corners and node data (~28 words) and
     its predictor tables (4 N_st words), write the new predictor and tables
     (4 N_st words), state and nodes (~30 words); read its stencil and total
-    stencil index lists (7 n_e + |S^W| int32)."""
+    stencil index lists (7 n_e + |S^W| int32); and, under local time
+    stepping (the ready elements of a sweep are sparse, so their stencils
+    barely overlap), gather for each distinct stencil member the data of its
+    virtual projection: ticks (2), corners (6), average and its tau
+    polynomial (4 (M+1)), vertex displacement polynomials (6 (M+1)) and
+    periodic offset (2) words."""
     Mc = (M + 1) * (M + 2) // 2
     Nst = Mc * (M + 1)
-    return 8.0 * (28 + 4 * Nst + 4 * Nst + 30) + 4.0 * (7 * 2 * Mc + sw_per_elem)
+    member = 8.0 * (2 + 6 + 4 * (M + 1) + 6 * (M + 1) + 2)
+    return 8.0 * (28 + 4 * Nst + 4 * Nst + 30) + 4.0 * (7 * 2 * Mc + sw_per_elem) + members_per_elem * member
 
 
 def host_info():
@@ -166,20 +172,82 @@ def aggregate(ms: float, updates: int, dist=None, device="cpu"):
     return float(mx[0]), float(sm[1])
 
 
-def workload(order: int, hc: float, flux: str = "rusanov"):
+def workload(order: int, hc: float, flux: str = "rusanov", t_switch: float = 0.01):
+    """The explosion EP1 on the graded disc; with t_switch > 0 the run takes
+    global steps (CFL 0.5) until t_switch and local steps after, the start-up
+    of Sec. 3.5 with which the fourth-order run reaches t_end (without it the
+    first local step of an element on the initial jump overshoots)."""
     from paper_1408_3719_gb300 import workloads as W
     mesh, Q = W.explosion(hc)
-    return mesh, Q, dict(order_M=order, t_end=0.25, time_quantum_log2=20, flux=flux)
+    cfg = dict(order_M=order, t_end=0.25, time_quantum_log2=20, flux=flux)
+    if t_switch > 0:
+        cfg.update(t_switch=t_switch, cfl_start=0.5)
+    return mesh, Q, cfg
 
 
-def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = None, flux: str = "rusanov"):
+def oracle_counts(order: int, flux: str = "rusanov", sweeps: int = 3):
+    """FP64 operations per element update (reconstruction with its virtual
+    projection, local step, predictor, whole update) and per space-time
+    surface (fluxes) counted by the oracle's counting build on the bounded
+    sample disc: the plain oracle's own arithmetic, an upper bound of the
+    method as the kernels formulate it."""
+    from oracle.pyoracle import Oracle, flop_counts, flop_reset
+    from paper_1408_3719_gb300 import workloads as W
+    mesh, Q = W.explosion(0.005)
+    o = Oracle(order_M=order, t_end=0.25, flux=flux, kind="count")
+    o.load_mesh(mesh)
+    o.load_state(Q)
+    tri = np.asarray(mesh["tri"])
+    edges = {tuple(sorted((int(t[k]), int(t[(k + 1) % 3])))) for t in tri for k in range(3)}
+    ea = np.array(sorted(edges))
+    flop_reset(o)
+    ups = surf = 0
+    for _ in range(sweeps):
+        _, nt0 = o.get_nodes()
+        ups += o.sweep()
+        _, nt1 = o.get_nodes()
+        moved = nt1 != nt0
+        surf += int(np.count_nonzero(moved[ea[:, 0]] | moved[ea[:, 1]]))
+    f = flop_counts(o)
+    return {"per_update": {k: f[k] / ups for k in ("recon", "dt", "predictor", "nodes", "update")},
+            "per_update_total": sum(f.values()) / ups, "flux_per_surface": f["flux"] / max(surf, 1),
+            "sample": f"{sweeps} sweeps ({ups} updates, {surf} surfaces) of the {tri.shape[0]}-triangle disc"}
+
+
+def read_ncu_counters(path):
+    """key = value lines of a committed ncu summary (profiles/); {} if absent."""
+    out = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                line = line.split("#", 1)[0].strip()
+                if "=" in line:
+                    k, v = (x.strip() for x in line.split("=", 1))
+                    try:
+                        out[k] = float(v)
+                    except ValueError:
+                        out[k] = v
+    except OSError:
+        pass
+    return out
+
+
+def kernel_source_digest():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1408_3719_gb300", "csrc", "aw_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def cpu_sample(order: int, seconds: float, warmup: int = 0, steps: int | None = None, flux: str = "rusanov",
+               t_switch: float = 0.01):
     """The oracle on a bounded sample: the same generator and scheme on a
     ~26k-triangle disc; setup untimed; sweeps timed until `seconds` elapse
     (or `steps` sweeps)."""
     from oracle.pyoracle import Oracle
     from paper_1408_3719_gb300 import workloads as W
     mesh, Q = W.explosion(0.005)
-    o = Oracle(order_M=order, t_end=0.25, flux=flux)
+    extra = dict(t_switch=t_switch, cfl_start=0.5) if t_switch > 0 else {}
+    o = Oracle(order_M=order, t_end=0.25, flux=flux, **extra)
     o.load_mesh(mesh)
     o.load_state(Q)
     for _ in range(warmup):
@@ -201,9 +269,12 @@ def _flux_tag(args):
 
 def explosion_config(args, n_tris: int, world: int) -> dict:
     """The workload keys of the explosion bench line, shared by both arms."""
+    start = (f"global steps (CFL 0.5) until t = {args.t_switch:g}, then local steps" if args.t_switch > 0
+             else "local steps from t = 0")
     return {"workload": f"cylindrical explosion EP1 on a graded disc, {n_tris} triangles, "
-                        f"P{args.order} LTS, CFL 0.5, t_end 0.25{_flux_tag(args)}",
-            "n_tris": n_tris, "order_M": args.order, "parallelism": f"replicas x{world}"}
+                        f"P{args.order} LTS, CFL 0.5, t_end 0.25, {start}{_flux_tag(args)}",
+            "n_tris": n_tris, "order_M": args.order, "t_switch": args.t_switch,
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args, rank):
@@ -214,7 +285,8 @@ def run_reference(args, rank):
     mesh, _, _ = workload(args.order, args.hc, args.flux)
     full_tris = int(mesh["tri"].shape[0])
     del mesh
-    rate, info = cpu_sample(args.order, 0, warmup=args.warmup, steps=args.steps, flux=args.flux)
+    rate, info = cpu_sample(args.order, 0, warmup=args.warmup, steps=args.steps, flux=args.flux,
+                            t_switch=args.t_switch)
     sample = (f"oracle (plain serial C, FP64) on a {info['n_tris']}-triangle graded disc, same EP1 data and "
               f"P{args.order} LTS scheme, {args.flux} flux; {info['sweeps']} timed sweeps ({info['updates']} updates) after "
               f"{args.warmup} warm-up sweeps; pre-processing untimed")
@@ -228,6 +300,21 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def warm_into_run(s, t_warm, chunk=200, max_sweeps=200000):
+    """Sweeps until every element is past t_warm (no sync point: the elements
+    keep their own times, as in the middle of a run); returns the sweeps."""
+    n = 0
+    t = np.empty(s.n_tris)
+    while n < max_sweeps:
+        s.enqueue(chunk)
+        s.sync()
+        n += chunk
+        s.get_state(t=t)
+        if t.min() >= t_warm:
+            break
+    return n, t
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1408_3719_gb300 import aleweno
@@ -239,7 +326,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     aleweno.load()
-    mesh, Q, cfg = workload(args.order, args.hc, args.flux)
+    mesh, Q, cfg = workload(args.order, args.hc, args.flux, args.t_switch)
     n_tris = int(mesh["tri"].shape[0])
     # a dedicated (non-default) stream: the library launches on it and the
     # CUDA events below are recorded on it
@@ -252,6 +339,23 @@ def run_ours(args, rank, world):
     s.load_state(Q)
     sizes = s.sizes()
     peak_gflops = aleweno.fp64_peak_gflops()
+    # into the run: through the start-up's global steps until every element
+    # is past t_warm (untimed), so that the timed sweeps are local-time-step
+    # sweeps from the middle of the run the line names; --save-state keeps
+    # that state in a file and --load-state starts from such a file (short
+    # profiling runs: a few launches instead of thousands)
+    t0 = time.perf_counter()
+    if args.load_state:
+        z = np.load(args.load_state)
+        s.set_elem({k: z[k] for k in ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")})
+        s.set_nodes(z["nX"], z["nt"])
+        warm_sweeps, t_el = int(z["sweeps"]), np.empty(n_tris)
+    else:
+        warm_sweeps, t_el = warm_into_run(s, args.t_warm)
+    if args.save_state:
+        e, (nX, nt) = s.get_elem(), s.get_nodes()
+        np.savez(args.save_state, nX=nX, nt=nt, sweeps=warm_sweeps, **e)
+    t_warm_s = time.perf_counter() - t0
     # tile shapes picked by the library's autotuner on this state (it times
     # the same sweeps for every shape and restores the state)
     if args.tiles:
@@ -261,6 +365,9 @@ def run_ours(args, rank, world):
         tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
     for _ in range(args.warmup):
         s.sweep()
+    s.get_state(t=t_el)
+    t_range = [float(t_el.min()), float(np.median(t_el)), float(t_el.max())]
+    snap, snap_nodes = (s.get_elem(), s.get_nodes()) if args.e2e else (None, None)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
     s.sync()
     clocks = ClockSampler(local)
@@ -304,80 +411,158 @@ def run_ours(args, rank, world):
     model = {"k_predict": (predictor_flops(args.order), prof_updates, "update"),
              "k_recon": (recon_flops(args.order, members), prof_updates, "update"),
              "k_flux": (flux_flops(args.order), prof_surfaces, "surface")}
+    # per-launch DRAM bytes and executed FP64 operations of the same kernels
+    # from the committed ncu capture, used only while the kernel source is
+    # the one that capture measured
+    ncu = read_ncu_counters(os.path.join(ROOT, "profiles", f"ncu_counters_explosion500k_p{args.order}.txt"))
+    ncu_valid = ncu.get("source_sha") == kernel_source_digest() and args.flux == "rusanov"
     roof = None
     if dom in model and kms[dom] > 0:
         per_unit, units, unit_name = model[dom]
         achieved = per_unit * units / (kms[dom] * 1e-3) / 1e12
         peak = peak_gflops / 1e3
+        launches = ksweeps
+        traffic = executed = None
+        if ncu_valid and f"{dom}.units" in ncu:
+            per_unit_bytes = ncu[f"{dom}.dram_bytes"] / ncu[f"{dom}.units"]
+            traffic = per_unit_bytes * units / launches
+            exec_per_unit = ncu[f"{dom}.fp64_ops"] / ncu[f"{dom}.units"]
+            executed = {"flops_per_unit": exec_per_unit,
+                        "achieved": exec_per_unit * units / (kms[dom] * 1e-3) / 1e12,
+                        "frac": exec_per_unit * units / (kms[dom] * 1e-3) / 1e12 / peak,
+                        "note": "FP64 operations the kernel executes (2 per DFMA, 1 per DADD/DMUL), ncu counters "
+                                "per unit from the committed capture"}
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FP64 DFMA throughput (aw_measure_fp64_peak, this run)",
-                f"flops_per_{unit_name}": per_unit, f"{unit_name}s_profiled": units}
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": ("DRAM bytes per launch: ncu dram__bytes_read + write per unit of the committed "
+                                 "capture x the units of an average timed launch" if traffic is not None else
+                                 "null: no ncu capture of the current kernel source"),
+                "peak_source": "measured FP64 DFMA throughput (aw_measure_fp64_peak, this run); "
+                               "MEASURED_PEAKS.json has no FP64 figure",
+                f"flops_per_{unit_name}": per_unit, f"{unit_name}s_profiled": units,
+                "flops_note": "operation count of the method's steps as the kernel formulates them (bench.py: "
+                              "predictor_flops, recon_flops, flux_flops)",
+                "executed": executed}
     # the HBM roofline this FP64-bound path is far from: compulsory bytes per
     # update x update rate, against the measured copy bandwidth
-    bpu = hbm_bytes_per_update(args.order, sizes["sw_entries"] / n_tris)
+    bpu = hbm_bytes_per_update(args.order, sizes["sw_entries"] / n_tris, members)
     hbm_peak = None
     try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             hbm_peak = json.load(f).get("hbm_gbs")
     except (OSError, ValueError):
         pass
     hbm = {"bytes_per_update": bpu, "achieved_GBs": value * bpu / 1e9, "peak_GBs": hbm_peak,
            "frac": (value * bpu / 1e9 / hbm_peak) if hbm_peak else None,
-           "note": "algorithmic (compulsory) bytes; the path is bound by the FP64 pipe, see roofline"}
+           "note": "algorithmic (compulsory) bytes, with the gathers of the stencil members' virtual data; the "
+                   "path is bound by the FP64 pipe, see roofline"}
 
-    # end to end through the C ABI with host buffers: state upload + initial
-    # phase, the same number of sweeps, state download
+    # end to end through the C ABI with host buffers: the mid-run state
+    # (the one the timed sweeps started from) uploaded from pinned host
+    # memory, e2e_sweeps sweeps, the averages read back to pinned host memory
     e2e = None
     if args.e2e:
-        s2 = aleweno.Solver(**cfg)
+        s2 = aleweno.Solver(**cfg, stream=stream.cuda_stream)
         s2.load_mesh(mesh)
         s2.set_tiles(tiles["recon_half"], tiles["pred_wide"], tiles["bpsm"])  # the shape picked above
-        Qh = np.ascontiguousarray(Q)
-        out = np.empty_like(Qh)
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in snap.items()}
+        pnX, pnt = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in snap_nodes)
+        out = torch.empty((n_tris, 4), dtype=torch.float64).pin_memory()
+        nst = args.e2e_sweeps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2.load_state(Qh)
-        s2.sync()
-        s2.enqueue(args.e2e_sweeps)
+        s2.set_elem(pin)
+        s2.set_nodes(pnX, pnt)
+        s2.enqueue(nst)
         ups = s2.sync()
         s2.get_state(out)
         el = time.perf_counter() - t0
-        nst = args.e2e_sweeps
-        e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": Qh.nbytes / nst,
-               "d2h_bytes_per_step": (out.nbytes + 16) / nst,
-               "note": "aw_load_state(host Q, with the pre-processing phase of the state) + aw_enqueue_sweeps + "
-                       "aw_sync (update count) + aw_get_state(host Q), with the tile shapes of the device-timed "
-                       f"run; mesh pre-processing ({t_mesh:.1f} s, once per mesh) excluded"}
+        h2d = sum(v.numel() * v.element_size() for v in pin.values()) + pnX.numel() * 8 + pnt.numel() * 8
+        e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": h2d / nst,
+               "d2h_bytes_per_step": (out.numel() * 8 + 16) / nst,
+               "note": "aw_set_elem_arrays + aw_set_node_arrays (the mid-run state the timed sweeps started from, "
+                       "pinned host memory) + aw_enqueue_sweeps + aw_sync (update count) + aw_get_state (averages "
+                       "to pinned host memory), host wall time, the tile shapes of the device-timed run"}
         s2.close()
+        del pin
+
+    # the whole run the line names, from the loaded state to t_end
+    full = None
+    if args.full_run and rank == 0:
+        s3 = aleweno.Solver(**cfg, stream=stream.cuda_stream)
+        s3.load_mesh(mesh)
+        s3.set_tiles(tiles["recon_half"], tiles["pred_wide"], tiles["bpsm"])
+        s3.load_state(Q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sweeps_f, ups_f = s3.advance()
+        el = time.perf_counter() - t0
+        full = {"value": ups_f / el, "unit": UNIT, "seconds": el, "updates": ups_f, "sweeps": sweeps_f,
+                "note": "aw_advance_to(t_end) from the loaded state (start-up and all local steps), host wall "
+                        "time, device-resident state"}
+        s3.close()
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_baseline:
-        rate, info = cpu_sample(args.order, args.cpu_seconds, flux=args.flux)
+        rate, info = cpu_sample(args.order, args.cpu_seconds, flux=args.flux, t_switch=args.t_switch)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle (serial C, FP64) on a {info['n_tris']}-triangle graded disc with the same EP1 "
-                         f"data and P{args.order} LTS scheme, {info['sweeps']} sweeps from t=0 "
+                         f"data and P{args.order} LTS scheme with its start-up, {info['sweeps']} sweeps from t=0 "
                          f"({info['updates']} updates, {info['seconds']:.1f} s), pre-processing untimed"}
+        try:
+            cpu["oracle_flops"] = oracle_counts(args.order, args.flux)
+        except Exception as exc:  # the counting build is context, not the baseline
+            cpu["oracle_flops"] = {"unavailable": str(exc)[:200]}
     if rank == 0:
         share_tot = sum(kms.values()) or 1.0
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {**explosion_config(args, n_tris, world),
+                           "timed_from": f"{warm_sweeps + args.warmup} sweeps into the run, element times "
+                                         f"min/median/max {t_range[0]:.4f}/{t_range[1]:.4f}/{t_range[2]:.4f}",
                            "l2": "256 MiB write between timed sweeps (L2 is 129 MB)",
-                           "updates_timed": int(updates_all), "sw_entries_per_elem": sizes["sw_entries"] / n_tris},
-                "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+                           "updates_timed": int(updates_all), "sw_entries_per_elem": sizes["sw_entries"] / n_tris,
+                           "stencil_members_per_elem": members},
+                "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "full_run": full,
                 "gpu_launches": len(kms) * args.steps,
                 "clocks": clk,
                 "kernels": {k: {"ms": v, "share": v / share_tot} for k, v in kms.items()},
                 "kernels_note": f"CUDA-event times over a second pass of {ksweeps} sweeps ({prof_updates} updates)",
                 "tiles": tiles,
                 "autotune_ms": {f"recon_half={k[0]},pred_wide={k[1]},bpsm={k[2]}": v for k, v in tune_ms.items()},
-                "fp64_peak_gflops": peak_gflops}
+                "fp64_peak_gflops": peak_gflops, "warm_s": t_warm_s}
+        s.close()
+        if args.extras and world == 1:
+            line.update(run_extras(args))
         print(json.dumps(line), flush=True)
-    s.close()
+    else:
+        s.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_extras(args):
+    """The batched and adjoint figures of the metric, measured after the main
+    line (each with its own short step count): the batched sweep over the
+    config's 256 instances against a per-instance loop, and the adjoint of
+    the 50-sweep vortex run against its forward."""
+    out = {}
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup = args.extra_steps, 3
+    try:
+        sub.order = 2
+        out["batched"] = run_batched(sub, 0, 1, emit=False)
+        out["batched_over_loop"] = out["batched"]["batched_over_loop"]
+    except Exception as exc:
+        out["batched"] = {"unavailable": str(exc)[:200]}
+    try:
+        sub.order = 2
+        out["adjoint"] = run_adjoint(sub, emit=False)
+        out["adjoint_over_forward"] = out["adjoint"]["adjoint_over_forward"]
+    except Exception as exc:
+        out["adjoint"] = {"unavailable": str(exc)[:200]}
+    return out
 
 
 def shard_instances(sizes, world):
@@ -392,7 +577,7 @@ def shard_instances(sizes, world):
     return [sorted(p) for p in parts]
 
 
-def run_batched(args, rank=0, world=1):
+def run_batched(args, rank=0, world=1, emit=True):
     """Config 4: many independent explosion / shock-tube instances advanced by
     one sweep over the batch, against a loop that runs the same instances one
     context at a time on the same GPU.  With N ranks the instances are
@@ -482,10 +667,14 @@ def run_batched(args, rank=0, world=1):
                                   "note": "same instances, one context per instance (default tiles), one sweep "
                                           "of each per step"},
             "batched_over_loop": vb / vl}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return {"value": vb, "unit": UNIT, "ms_per_step": msb / args.steps, "steps": args.steps,
+            "workload": line["config"]["workload"], "per_instance_loop": line["per_instance_loop"],
+            "batched_over_loop": vb / vl, "tiles": tiles}
 
 
-def run_adjoint(args):
+def run_adjoint(args, emit=True):
     """Config 5: gradient of the kinetic energy in the disc r < 1 about the
     vortex centre after 50 LTS sweeps of P2 on the ~50k-triangle isentropic
     vortex, with respect to the initial averages and node positions
@@ -573,7 +762,11 @@ def run_adjoint(args):
             "adjoint_over_forward": ma / (ml + mp), "adjoint_over_sweeps": ma / mp,
             "note": "forward = aw_load_state (pre-processing phase over every element) + the sweeps: the map "
                     "the gradient differentiates"}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return {"value": line["value"], "unit": UNIT, "steps": args.steps, "workload": line["config"]["workload"],
+            "forward_ms": ml + mp, "adjoint_ms": ma, "adjoint_over_forward": ma / (ml + mp),
+            "adjoint_over_sweeps": ma / mp}
 
 
 def main():
@@ -598,6 +791,17 @@ def main():
     ap.add_argument("--flux", default="rusanov", choices=["rusanov", "osher"],
                     help="numerical flux of the explosion workload and its oracle sample")
     ap.add_argument("--objective", default="disc", choices=["disc", "global"])
+    ap.add_argument("--t-switch", type=float, default=0.01,
+                    help="global steps until this time, local steps after (0: local steps from t = 0)")
+    ap.add_argument("--t-warm", type=float, default=0.02,
+                    help="untimed sweeps until every element is past this time before the timed sweeps")
+    ap.add_argument("--no-full-run", dest="full_run", action="store_false",
+                    help="skip the run from the loaded state to t_end")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batched and adjoint figures after the main line")
+    ap.add_argument("--extra-steps", type=int, default=10)
+    ap.add_argument("--save-state", default=None, help="write the warmed-up state to this .npz file")
+    ap.add_argument("--load-state", default=None, help="start from a state written by --save-state")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--min-tris", type=int, default=2000)
     ap.add_argument("--max-tris", type=int, default=60000)

@@ -25,6 +25,11 @@
  * Errors: every entry point returns AW_OK (0) or a negative AW_ERR_* code and
  * leaves a message for aw_last_error().  No exception crosses the ABI.  Calls
  * on one context are not thread-safe; different contexts are independent.
+ *
+ * Devices: a context lives on the device that is current when aw_create is
+ * called (its stream, memory and captured graphs belong to it).  Every entry
+ * point taking a context makes that device current for the call and gives the
+ * caller's current device back before returning.
  */
 #ifndef ALEWENO_H
 #define ALEWENO_H
@@ -132,8 +137,21 @@ int aw_lts_sweep(aw_ctx* ctx, int64_t* n_updated);
 /* One global time step (the GTS reference of Sec. 3.2): requires gts = 1. */
 int aw_gts_step(aw_ctx* ctx, int64_t* n_updated);
 
-/* Run sweeps until every element reached min(t, t_end) or max_sweeps sweeps
- * ran; t must be t_end or a multiple of the tick.  Outputs may be NULL. */
+/* Run sweeps until every element reached the sync time min(t, t_end), or
+ * max_sweeps sweeps ran (the computational phase of Sec. 2.6 runs every element
+ * to a time).  A sync time before t_end follows the same rule as the final
+ * time: every local step is clipped so that it ends at or before the sync
+ * time, and elements stop there; the run to t is then the run whose final
+ * time is t.  Moving the sync time back (below steps already taken) cuts
+ * each step that crosses it and re-solves that element's predictor over the
+ * shorter step from its own tau = 0 dofs; moving it forward gives each
+ * element stopped at the old sync time its reconstruction, local step and
+ * predictor there.  The sync time stays until the next aw_advance_to
+ * (aw_lts_sweep updates nothing once every element reached it);
+ * aw_load_state resets it to t_end.  t < t_end must be a whole number of
+ * ticks and not behind any element's time; INVALID_ARG otherwise, for a
+ * batch, or with a frozen schedule (aw_schedule mode 1 or 2).  Outputs may be
+ * NULL: *sweeps_done counts sweeps that updated at least one element. */
 int aw_advance_to(aw_ctx* ctx, double t, int64_t max_sweeps, int64_t* sweeps_done,
                   int64_t* updates_done);
 
@@ -183,13 +201,16 @@ const char* aw_kernel_name(int k);
  * callers that cannot call cudaMalloc -- code running between the launches of
  * an application that owns all device memory through its own pool, or a
  * latency-critical loop where cudaMalloc's implicit device synchronisation is
- * not acceptable.  The caller passes the outputs: ready_out, a device array
+ * not acceptable.  The work runs on the context's device (current at
+ * aw_create), whichever device is current at the call; the caller's device is
+ * given back.  The caller passes the outputs: ready_out, a device array
  * with room for n_tris int32, receives the ready element indices in ascending
  * order; n_ready_out, a device int64, receives their number.  The work is
  * enqueued on the context's stream and not waited for.  Scratch is a fixed
  * 16 KB array in device memory that every GPU loading the library holds until
- * the process exits; the first call on a device looks its address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * the process exits; the first call for a device looks that device's copy up
+ * (cudaGetSymbolAddress, with the context's device current), so make that
+ * first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other contexts) race and must be serialised by the caller.  Meshes with more
  * than 1,048,576 triangles are rejected with AW_ERR_INVALID_ARG; STATE without

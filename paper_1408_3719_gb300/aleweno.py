@@ -132,6 +132,14 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _arr(a, dtype):
+    """numpy arrays are made contiguous in dtype; torch tensors (host,
+    pinned or device) pass as they are (the caller gives the layout)."""
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
 class Solver:
     """One GPU context: mesh, LTS state and configuration."""
 
@@ -265,8 +273,13 @@ class Solver:
         return n.value
 
     def advance(self, max_sweeps=10 ** 12):
+        return self.advance_to(self.t_end, max_sweeps)
+
+    def advance_to(self, t, max_sweeps=10 ** 12):
+        """Sweeps until every element reached the sync time t (t_end, or a
+        whole number of ticks not behind any element); (sweeps, updates)."""
         s, u = C.c_int64(0), C.c_int64(0)
-        self._check(self.lib.aw_advance_to(self.h, self.t_end, max_sweeps, C.byref(s), C.byref(u)))
+        self._check(self.lib.aw_advance_to(self.h, float(t), int(max_sweeps), C.byref(s), C.byref(u)))
         return s.value, u.value
 
     def enqueue(self, n):
@@ -292,7 +305,7 @@ class Solver:
         return out
 
     def set_elem(self, st):
-        arrs = [np.ascontiguousarray(st[k], dtype=np.int64 if k in ("t", "dt", "count") else np.float64)
+        arrs = [_arr(st[k], np.int64 if k in ("t", "dt", "count") else np.float64)
                 for k in ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")]
         self._check(self.lib.aw_set_elem_arrays(self.h, *[_ptr(a) for a in arrs]))
 
@@ -303,8 +316,8 @@ class Solver:
         return X, t
 
     def set_nodes(self, X, t):
-        X = np.ascontiguousarray(X, dtype=np.float64)
-        t = np.ascontiguousarray(t, dtype=np.int64)
+        X = _arr(X, np.float64)
+        t = _arr(t, np.int64)
         self._check(self.lib.aw_set_node_arrays(self.h, _ptr(X), _ptr(t)))
 
     def update_counts(self):

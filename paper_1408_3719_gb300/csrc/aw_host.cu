@@ -22,6 +22,7 @@ struct aw_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  int device = -1;           // current device at aw_create: every entry point runs there
   int nsm = 0;
   bool have_mesh = false, have_state = false, failed = false;
   bool moving_wall = false;  // the mesh has a moving slip wall or a Kidder boundary (tags 2, 3)
@@ -45,6 +46,8 @@ struct aw_ctx {
   std::vector<int> tri_h;                // host copies for aw_load_state_xy
   std::vector<double> cshift_h;
   bool fresh = false;                    // a state was loaded and no sweep has run since
+  bool batch = false;                    // loaded by aw_load_batch (ticks differ per instance)
+  long long t_sync = 0;                  // the sync time in ticks (a copy of the device's)
   // frozen schedule (record / replay of the dt ticks)
   long long* d_sched = nullptr;
   // checkpointed forward run and its adjoint
@@ -683,7 +686,24 @@ int reset_sweep_state(aw_ctx* c) {
   CK(cudaMemsetAsync(d.cnt, 0, sizeof(Counters), c->stream));
   static const int one = 1;  // stamps are 0: the first sweep must be epoch 1
   CK(cudaMemcpyAsync(&d.cnt->epoch, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&d.cnt->t_sync, &c->t_sync, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return AW_OK;
+}
+
+// elements with t < t_sync, counted on the host from the device times
+int count_unfinished(aw_ctx* c, long long* max_t) {
+  std::vector<long long> th(c->ne);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(th.data(), c->d.t, c->ne * sizeof(long long), cudaMemcpyDeviceToHost));
+  int unf = 0;
+  long long mx = 0;
+  for (long long v : th) {
+    unf += v < c->t_sync;
+    mx = std::max(mx, v);
+  }
+  if (max_t) *max_t = mx;
+  CK(cudaMemcpy(&c->d.cnt->n_unfinished, &unf, sizeof(int), cudaMemcpyHostToDevice));
   return AW_OK;
 }
 
@@ -712,8 +732,9 @@ namespace aw {
 bool ctx_view(aw_ctx* c, CtxView* v) {
   if (!c || !c->have_state || c->failed) return false;
   v->d = &c->d;
-  v->T = c->tab.T;
+  v->T = c->t_sync;
   v->stream = c->stream;
+  v->device = c->device;
   return true;
 }
 void ctx_error(aw_ctx* c, const char* msg) {
@@ -823,6 +844,7 @@ int aw_create(const aw_config* cfg, aw_ctx** out) {
     delete c;
     return AW_ERR_CUDA;
   }
+  c->device = dev;
   if (cfg->cuda_stream) c->stream = (cudaStream_t)cfg->cuda_stream;
   else {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return AW_ERR_CUDA; }
@@ -834,6 +856,7 @@ int aw_create(const aw_config* cfg, aw_ctx** out) {
 }
 
 void aw_destroy(aw_ctx* c) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_all(c);
@@ -858,6 +881,7 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
     return set_err(c, AW_ERR_INVALID_ARG, "bad mesh sizes or null arrays");
   if ((shift == nullptr) != (period == nullptr)) return set_err(c, AW_ERR_INVALID_ARG, "shift and period go together");
   free_all(c);
+  c->t_sync = c->tab.T;
   HostMesh m;
   m.ne = (int)n_tris;
   m.nn = (int)n_nodes;
@@ -946,11 +970,14 @@ static int load_common(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_t
 
 int aw_load_mesh(aw_ctx* c, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri,
                  const int8_t* bc, const int8_t* shift, const double* period) {
+  DeviceGuard dg_(c ? c->device : -1);
+  if (c) c->batch = false;
   return load_common(c, n_nodes, xy, n_tris, tri, bc, shift, period, nullptr);
 }
 
 int aw_load_batch(aw_ctx* c, int n_inst, const int64_t* node_offsets, const int64_t* tri_offsets,
                   const double* t_end, const double* xy, const int32_t* tri, const int8_t* bc) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (n_inst < 1 || !node_offsets || !tri_offsets || !t_end || !xy || !tri || !bc)
     return set_err(c, AW_ERR_INVALID_ARG, "aw_load_batch: null arrays or no instance");
@@ -977,7 +1004,9 @@ int aw_load_batch(aw_ctx* c, int n_inst, const int64_t* node_offsets, const int6
       }
     }
   }
-  return load_common(c, nn, xy, ne, gtri.data(), bc, nullptr, nullptr, et.data());
+  const int rc = load_common(c, nn, xy, ne, gtri.data(), bc, nullptr, nullptr, et.data());
+  c->batch = rc == AW_OK;
+  return rc;
 }
 
 static int load_state_impl(aw_ctx* c, const double* Q, const double* xy) {
@@ -1023,6 +1052,7 @@ static int load_state_impl(aw_ctx* c, const double* Q, const double* xy) {
     CK(cudaMemcpyAsync(d.nX, c->xy0.data(), 2 * nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   }
   CK(cudaMemsetAsync(d.nt, 0, nn * sizeof(long long), c->stream));
+  c->t_sync = c->tab.T;
   int rc0 = reset_sweep_state(c);
   if (rc0) return rc0;
   {
@@ -1043,9 +1073,13 @@ static int load_state_impl(aw_ctx* c, const double* Q, const double* xy) {
   return AW_OK;
 }
 
-int aw_load_state(aw_ctx* c, const double* Q) { return load_state_impl(c, Q, nullptr); }
+int aw_load_state(aw_ctx* c, const double* Q) {
+  DeviceGuard dg_(c ? c->device : -1);
+  return load_state_impl(c, Q, nullptr);
+}
 
 int aw_load_state_xy(aw_ctx* c, const double* Q, const double* xy) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !xy) return AW_ERR_INVALID_ARG;
   return load_state_impl(c, Q, xy);
 }
@@ -1108,27 +1142,63 @@ static int do_sweeps(aw_ctx* c, int64_t n, int64_t* n_updated, bool wait) {
 }
 
 int aw_lts_sweep(aw_ctx* c, int64_t* n_updated) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   return do_sweeps(c, 1, n_updated, true);
 }
 
 int aw_gts_step(aw_ctx* c, int64_t* n_updated) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "aw_gts_step needs a context created with gts = 1");
   return do_sweeps(c, 1, n_updated, true);
 }
 
+// Reading R18: the run to a sync time t_s is the run whose final time is t_s.
+// Moving the sync time back cuts the steps that cross it (predictors
+// re-solved over the shorter steps); moving it forward gives the elements
+// stopped at the old sync time their phase B there.
+static int set_sync_time(aw_ctx* c, long long Tn) {
+  if (Tn == c->t_sync) return AW_OK;
+  if (c->d.sched_mode != 0)
+    return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to: a sync time before t_end with a frozen schedule");
+  long long max_t = 0;
+  int rc = count_unfinished(c, &max_t);
+  if (rc) return rc;
+  if (max_t > Tn) return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to: an element is beyond the sync time");
+  const long long Told = c->t_sync;
+  c->t_sync = Tn;
+  c->fresh = false;  // the adjoint starts from a state just loaded
+  CK(cudaMemcpyAsync(&c->d.cnt->t_sync, &c->t_sync, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  if (Tn < Told) launch_sync_cut(c->tab, c->d, c->nsm, c->stream, Tn, c->tiles);
+  else launch_sync_resume(c->tab, c->d, c->nsm, c->stream, Told, c->tiles);
+  CK(cudaGetLastError());
+  if ((rc = count_unfinished(c, nullptr))) return rc;
+  if ((rc = sync_counters(c))) return rc;
+  return check_device_error(c);
+}
+
 int aw_advance_to(aw_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done, int64_t* updates_done) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
-  if (!(t >= c->cfg.t_end))
-    return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to runs to t_end (element times are local; pass t >= t_end)");
+  if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
+  if (max_sweeps < 0) return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to: max_sweeps < 0");
+  long long Tn = c->tab.T;
+  if (t < c->cfg.t_end) {
+    if (c->batch) return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to: a batch runs to its instances' t_end");
+    const double r = t / c->tab.tick;
+    if (!(r >= 0.0) || r != std::floor(r))
+      return set_err(c, AW_ERR_INVALID_ARG, "aw_advance_to: t is not a whole number of ticks");
+    Tn = (long long)r;
+  }
+  int rc = set_sync_time(c, Tn);
+  if (rc) return rc;
   // sweeps go out in chunks between host checks; a sweep with an empty ready
   // set changes nothing, so overshooting the end of the run is harmless
-  int rc = sync_counters(c);
-  if (rc) return rc;
+  if ((rc = sync_counters(c))) return rc;
   const long long u0 = c->hcnt->updates, p0 = c->hcnt->productive;
   int64_t issued = 0, chunk = 8;
-  while (issued < max_sweeps) {
+  while (issued < max_sweeps && c->hcnt->n_unfinished > 0) {
     const int64_t n = std::min<int64_t>(chunk, max_sweeps - issued);
     if ((rc = do_sweeps(c, n, nullptr, true))) return rc;
     issued += n;
@@ -1145,11 +1215,13 @@ int aw_advance_to(aw_ctx* c, double t, int64_t max_sweeps, int64_t* sweeps_done,
 }
 
 int aw_enqueue_sweeps(aw_ctx* c, int64_t n) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || n < 0) return AW_ERR_INVALID_ARG;
   return do_sweeps(c, n, nullptr, false);
 }
 
 int aw_sync(aw_ctx* c, int64_t* updates_since) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   int rc = sync_counters(c);
   if (rc) return rc;
@@ -1160,6 +1232,7 @@ int aw_sync(aw_ctx* c, int64_t* updates_since) {
 }
 
 int aw_get_state(aw_ctx* c, double* Q, double* t_elem) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   CK(cudaStreamSynchronize(c->stream));
@@ -1175,6 +1248,7 @@ int aw_get_state(aw_ctx* c, double* Q, double* t_elem) {
 }
 
 int aw_get_nodes(aw_ctx* c, double* xy, double* t_node) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   CK(cudaStreamSynchronize(c->stream));
@@ -1190,6 +1264,7 @@ int aw_get_nodes(aw_ctx* c, double* xy, double* t_node) {
 }
 
 int aw_get_update_counts(aw_ctx* c, int64_t* per_elem, int64_t* total) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   int rc = sync_counters(c);
@@ -1201,6 +1276,7 @@ int aw_get_update_counts(aw_ctx* c, int64_t* per_elem, int64_t* total) {
 
 int aw_get_elem_arrays(aw_ctx* c, double* Q, double* QM, double* HM, int64_t* t, int64_t* dt, double* X,
                        int64_t* count, double* qhat) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   CK(cudaStreamSynchronize(c->stream));
@@ -1218,6 +1294,7 @@ int aw_get_elem_arrays(aw_ctx* c, double* Q, double* QM, double* HM, int64_t* t,
 
 int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const double* HM, const int64_t* t,
                        const int64_t* dt, const double* X, const int64_t* count, const double* qhat) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !Q || !QM || !HM || !t || !dt || !X || !count || !qhat) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   const size_t ne = c->ne;
@@ -1233,13 +1310,7 @@ int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const doubl
   CK(cudaMemcpy(c->d.qhat, qhat, ne * c->tab.Nst * 4 * sizeof(double), cudaMemcpyDefault));
   int rc0 = reset_sweep_state(c);
   if (rc0) return rc0;
-  {
-    std::vector<long long> th(ne);
-    CK(cudaMemcpy(th.data(), t, ne * sizeof(long long), cudaMemcpyDefault));
-    int unf = 0;
-    for (long long v : th) unf += v < c->tab.T;
-    CK(cudaMemcpy(&c->d.cnt->n_unfinished, &unf, sizeof(int), cudaMemcpyHostToDevice));
-  }
+  if ((rc0 = count_unfinished(c, nullptr))) return rc0;
 
   launch_products(c->tab, c->d, c->nsm, c->stream);
   CK(cudaGetLastError());
@@ -1252,6 +1323,7 @@ int aw_set_elem_arrays(aw_ctx* c, const double* Q, const double* QM, const doubl
 }
 
 int aw_get_node_arrays(aw_ctx* c, double* X, int64_t* t) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   CK(cudaStreamSynchronize(c->stream));
@@ -1261,6 +1333,7 @@ int aw_get_node_arrays(aw_ctx* c, double* X, int64_t* t) {
 }
 
 int aw_set_node_arrays(aw_ctx* c, const double* X, const int64_t* t) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !X || !t) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   CK(cudaStreamSynchronize(c->stream));
@@ -1270,6 +1343,7 @@ int aw_set_node_arrays(aw_ctx* c, const double* X, const int64_t* t) {
 }
 
 int aw_diagnostics(aw_ctx* c, double* out) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !out) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   int rc = sync_counters(c);
@@ -1284,6 +1358,7 @@ int aw_diagnostics(aw_ctx* c, double* out) {
 }
 
 int aw_sizes(aw_ctx* c, int64_t* out) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !out) return AW_ERR_INVALID_ARG;
   out[0] = c->ne; out[1] = c->nn; out[2] = c->ned; out[3] = c->tab.Nst; out[4] = c->sw_total;
   out[5] = c->u_total;
@@ -1291,6 +1366,7 @@ int aw_sizes(aw_ctx* c, int64_t* out) {
 }
 
 int aw_profile_enable(aw_ctx* c, int on) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   int rc = sync_counters(c);
   if (rc) return rc;
@@ -1301,6 +1377,7 @@ int aw_profile_enable(aw_ctx* c, int on) {
 }
 
 int aw_profile_read(aw_ctx* c, double* ms, int64_t* sweeps) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   int rc = sync_counters(c);
   if (rc) return rc;
@@ -1321,6 +1398,7 @@ int aw_measure_fp64_peak(double* gflops) {
 }
 
 int aw_schedule(aw_ctx* c, int mode, int64_t k) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || mode < 0 || mode > 2) return AW_ERR_INVALID_ARG;
   if (!c->have_mesh) return set_err(c, AW_ERR_STATE, "no mesh loaded");
   if (mode != 0 && c->cfg.gts) return set_err(c, AW_ERR_INVALID_ARG, "the schedule log is for local time stepping");
@@ -1343,6 +1421,7 @@ int aw_schedule(aw_ctx* c, int mode, int64_t k) {
 }
 
 int aw_get_schedule(aw_ctx* c, int64_t* out) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !out) return AW_ERR_INVALID_ARG;
   if (!c->d_sched) return set_err(c, AW_ERR_STATE, "no recorded schedule");
   CK(cudaStreamSynchronize(c->stream));
@@ -1351,6 +1430,7 @@ int aw_get_schedule(aw_ctx* c, int64_t* out) {
 }
 
 int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || n_sweeps < 0 || ckpt_every < 1) return AW_ERR_INVALID_ARG;
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
   if (!c->fresh) return set_err(c, AW_ERR_STATE, "aw_adjoint_forward starts from a state just loaded");
@@ -1397,6 +1477,7 @@ int aw_adjoint_forward(aw_ctx* c, int64_t n_sweeps, int64_t ckpt_every) {
 }
 
 int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* dJdxy, double* gQ0, double* gxy0) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c) return AW_ERR_INVALID_ARG;
   if (!c->adj_ready || c->failed) return set_err(c, AW_ERR_STATE, "no recorded forward run (call aw_adjoint_forward)");
   const size_t ne = c->ne, nn = c->nn, Nt = c->tab.Nt;
@@ -1466,6 +1547,7 @@ int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* 
 }
 
 int aw_set_tiles(aw_ctx* c, const int32_t* tiles) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !tiles) return AW_ERR_INVALID_ARG;
   if (tiles[0] < 0 || tiles[0] > 1 || tiles[1] < 0 || tiles[1] > 1 || tiles[2] < 1 || tiles[2] > 64)
     return set_err(c, AW_ERR_INVALID_ARG, "tiles: recon_half and pred_wide are 0 or 1, blocks per SM in [1, 64]");
@@ -1478,6 +1560,7 @@ int aw_set_tiles(aw_ctx* c, const int32_t* tiles) {
 }
 
 int aw_get_tiles(aw_ctx* c, int32_t* tiles) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || !tiles) return AW_ERR_INVALID_ARG;
   tiles[0] = c->tiles.recon_half;
   tiles[1] = c->tiles.pred_wide;
@@ -1486,6 +1569,7 @@ int aw_get_tiles(aw_ctx* c, int32_t* tiles) {
 }
 
 int aw_autotune(aw_ctx* c, int64_t n_sweeps, double* ms, int32_t* best) {
+  DeviceGuard dg_(c ? c->device : -1);
   if (!c || n_sweeps < 1) return AW_ERR_INVALID_ARG;
   if (!c->have_state || c->failed) return set_err(c, AW_ERR_STATE, "no valid state (load a state first)");
   CK(cudaStreamSynchronize(c->stream));

@@ -132,7 +132,7 @@ struct Counters {
   int n_moved;
   int n_active;
   int n_touched;
-  int n_unfinished;  // elements with t < t_end (maintained across sweeps)
+  int n_unfinished;  // elements with t < t_sync (maintained across sweeps)
   int n_cand[2];
   int cand_valid;    // 0: the next sweep checks every element
   int err_code;
@@ -146,6 +146,8 @@ struct Counters {
   int finish_blocks;
   long long updates_since_sync;
   long long surfaces;            // space-time edge surfaces integrated (all sweeps)
+  long long t_sync;              // sync time in ticks: steps are clipped at it and elements
+                                 // stop there (T unless aw_advance_to set an earlier time)
 };
 
 // Tile shapes of a sweep's kernels (they change no arithmetic): recon_half
@@ -167,6 +169,12 @@ void launch_sweep(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, cudaEve
                   cudaStream_t side = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 void launch_initial(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, const Tiles& tl);
 void launch_products(const Tab& tab, const Dev& d, int nsm, cudaStream_t s);
+// a new sync time Tn below the current one: every step crossing Tn is cut back
+// to it and its predictor re-solved from the element's own tau = 0 dofs
+void launch_sync_cut(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, long long Tn, const Tiles& tl);
+// a new sync time above the current one Told: the elements stopped at Told get
+// their phase B (reconstruction, step, predictor)
+void launch_sync_resume(const Tab& tab, const Dev& d, int nsm, cudaStream_t s, long long Told, const Tiles& tl);
 double measure_fp64_peak();
 // k_ready, k_nodes, k_edges of one sweep: ready/moved/active/touched lists
 // and the new node positions, without changing the state
@@ -191,10 +199,31 @@ int adjoint_selftest(const Tab& tab, unsigned long long seed, double* report);
 
 struct aw_ctx;
 namespace aw {
+// Makes a context's device current for the life of an entry point and gives
+// the caller's device back afterwards: a context's stream, kernels, memory
+// and graphs belong to the device that was current at aw_create.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0 && cudaGetDevice(&prev_) == cudaSuccess && prev_ != dev && cudaSetDevice(dev) == cudaSuccess)
+      switched_ = true;
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool switched_ = false;
+};
+
 struct CtxView {
   const Dev* d;
-  long long T;
+  long long T;          // the sync time in ticks (elements at or beyond it are not updated)
   cudaStream_t stream;
+  int device;           // the device of the context
 };
 // false if the context has no valid state
 bool ctx_view(aw_ctx* c, CtxView* v);

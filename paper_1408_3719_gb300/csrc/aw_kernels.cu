@@ -57,6 +57,7 @@ __global__ void k_ready(Tab T, Dev d) {
   // prefix counts.
   constexpr int GL = 8, UN = 4;
   const int epoch = d.cnt->epoch;
+  const long long Ts = d.cnt->t_sync;
   const int par = epoch & 1;
   const bool listed = d.cnt->cand_valid != 0 && !T.gts;
   const int n_items = listed ? d.cnt->n_cand[par] : d.ne;
@@ -75,7 +76,7 @@ __global__ void k_ready(Tab T, Dev d) {
     if (q < n_items) {
       i = listed ? clist[q] : q;
       const long long ti = d.t[i];
-      if (ti < T.T) {
+      if (ti < Ts) {
         tn = ti + d.dt[i];
         ready = true;
         for (int base = d.sw_ptr[i], pe = d.sw_ptr[i + 1]; base < pe; base += GL * UN) {
@@ -510,6 +511,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
 
 __global__ void k_update(Tab T, Dev d) {
   const int epoch = d.cnt->epoch;
+  const long long Ts = d.cnt->t_sync;
   const int n_touched = d.cnt->n_touched;
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n_touched; base += stride) {
@@ -559,7 +561,7 @@ __global__ void k_update(Tab T, Dev d) {
         gcl = fmax(fabs(res[0]), fmax(fabs(res[1]), fabs(res[2]))) / Aold;
         for (int k = 0; k < 6; ++k) d.X[6 * i + k] = Xn[k];
         d.t[i] += d.dt[i];
-        if (d.t[i] >= T.T) atomicSub(&d.cnt->n_unfinished, 1);
+        if (d.t[i] >= Ts) atomicSub(&d.cnt->n_unfinished, 1);
         d.count[i] += 1;
         if (!(Qn[0] > 0.0) || !(pressure(T, Qn) > 0.0) || !(Anew > 0.0)) set_error(d.cnt, -3, i);
       } else {
@@ -1054,6 +1056,7 @@ k_recon_coop(Tab T, Dev d, int initial) {
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int k = tid; k < Mc * NU; k += nth) sBn[k] = T.Bnod[k / NU][k % NU];
   const int n_ready = initial ? d.ne : d.cnt->n_ready;
+  const long long Ts = d.cnt->t_sync;
   for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
     // P0: element set-up
     if (tid < G) {
@@ -1138,7 +1141,7 @@ k_recon_coop(Tab T, Dev d, int initial) {
       {
         const int j = k == 0 ? i : d.nbr[3 * (size_t)i + k - 1];
         double dtc = DBL_MAX;
-        if (j >= 0 && ti < T.T) {
+        if (j >= 0 && ti < Ts) {
           virtual_data<M>(T, d, j, ti, Xv, Qv);
           double per = 0.0;
 #pragma unroll
@@ -1218,26 +1221,53 @@ k_recon_coop(Tab T, Dev d, int initial) {
         for (int b = 0; b <= a; ++b) nm[a * (a + 1) / 2 + b] = L[a][b];
     }
     __syncthreads();
-    // P3b: the two triangular solves, one right-hand side per item
+    // P3b: the two triangular solves, one right-hand side per item, then one
+    // step of the corrected semi-normal equations (Bjorck): r = b - A y over
+    // the stencil's rows, solve L L^T dy = A^T r with the same factor,
+    // y += dy.  The normal equations square the condition number of A; the
+    // correction brings y to the accuracy of an orthogonal factorisation.
     for (int item = tid; item < G * kNSten * 4; item += nth) {
       const int es = item / 4, v = item % 4, e = es / kNSten, s = es % kNSten;
       if (!sVal[e] || !sOk[e * kNSten + s]) continue;
       const double* nm = sNrm + (size_t)es * NN;
       double* cs = sC + (size_t)es * NU * 4;
-      double y[NU];
+      const unsigned char* st = sSt + es * NE;
+      const double* R0 = sRow + (size_t)e * (MaxU + 1) * RW;
+      double y[NU], z[NU];
 #pragma unroll
-      for (int a = 0; a < NU; ++a) {
-        double acc = nm[NL + a * 4 + v];
+      for (int a = 0; a < NU; ++a) z[a] = nm[NL + a * 4 + v];
 #pragma unroll
-        for (int k = 0; k < a; ++k) acc -= nm[a * (a + 1) / 2 + k] * y[k];
-        y[a] = acc * nm[a * (a + 1) / 2 + a];
-      }
+      for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-      for (int a = NU - 1; a >= 0; --a) {
-        double acc = y[a];
+        for (int a = 0; a < NU; ++a) {
+          double acc = z[a];
 #pragma unroll
-        for (int k = a + 1; k < NU; ++k) acc -= nm[k * (k + 1) / 2 + a] * y[k];
-        y[a] = acc * nm[a * (a + 1) / 2 + a];
+          for (int k = 0; k < a; ++k) acc -= nm[a * (a + 1) / 2 + k] * z[k];
+          z[a] = acc * nm[a * (a + 1) / 2 + a];
+        }
+#pragma unroll
+        for (int a = NU - 1; a >= 0; --a) {
+          double acc = z[a];
+#pragma unroll
+          for (int k = a + 1; k < NU; ++k) acc -= nm[k * (k + 1) / 2 + a] * z[k];
+          z[a] = acc * nm[a * (a + 1) / 2 + a];
+        }
+        if (pass == 0) {
+#pragma unroll
+          for (int a = 0; a < NU; ++a) { y[a] = z[a]; z[a] = 0.0; }
+#pragma unroll
+          for (int m = 1; m < NE; ++m) {
+            const double* r = R0 + (size_t)st[m] * RW;
+            double res = r[NU + v];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) res -= r[a] * y[a];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) z[a] += r[a] * res;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < NU; ++a) y[a] += z[a];
+        }
       }
 #pragma unroll
       for (int a = 0; a < NU; ++a) cs[a * 4 + v] = y[a];
@@ -1349,7 +1379,7 @@ k_recon_coop(Tab T, Dev d, int initial) {
       } else {
         const long long ti = d.t[i];
         long long tks = 0;
-        if (ti < T.T) {
+        if (ti < Ts) {
           double best = DBL_MAX;
           bool bad = false;
           for (int c = 0; c < 4; ++c) {
@@ -1363,7 +1393,7 @@ k_recon_coop(Tab T, Dev d, int initial) {
           }
           const double rt = floor(best / d.etick[i]);
           const bool start = ti < T.Tsw;  // global-step start-up
-          const long long end = start ? T.Tsw : T.T;
+          const long long end = start ? (T.Tsw < Ts ? T.Tsw : Ts) : Ts;
           tks = rt > (double)(end - ti) ? end - ti : (long long)rt;
           if (tks < 1) tks = 1;
           if (T.gts || start) atomicMin(&d.cnt->gts_min, tks);
@@ -1426,6 +1456,41 @@ k_recon_coop(Tab T, Dev d, int initial) {
       d.w0[(size_t)(base + e) * Mc * 4 + item % (Mc * 4)] = sW0[item];
     }
     __syncthreads();
+  }
+}
+
+// A new sync time Tn below the current one: every element whose step crosses
+// Tn takes the step Tn - t instead and is listed (with its tau = 0 dofs, the
+// scaled WENO values, as the predictor's nodal input) for a new predictor.
+template <int M>
+__global__ void k_sync_cut(Dev d, long long Tn) {
+  constexpr int Mc = (M + 1) * (M + 2) / 2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ne; i += gridDim.x * blockDim.x) {
+    const long long ti = d.t[i];
+    if (!(ti < Tn && ti + d.dt[i] > Tn)) continue;
+    d.dt[i] = Tn - ti;
+    atomicMin(&d.cnt->gts_min, Tn - ti);
+    const int slot = atomicAdd(&d.cnt->n_ready, 1);
+    d.ready_list[slot] = i;
+    const double* q0 = d.qhat + (size_t)i * (Mc * (M + 1)) * 4;
+    double* w = d.w0 + (size_t)slot * Mc * 4;
+#pragma unroll
+    for (int k = 0; k < Mc * 4; ++k) w[k] = q0[k];
+  }
+}
+
+// A new sync time above the current one Told: the elements stopped at Told
+// are listed for their phase B.
+__global__ void k_sync_resume(Dev d, long long Told) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.ne; i += gridDim.x * blockDim.x)
+    if (d.t[i] == Told) d.ready_list[atomicAdd(&d.cnt->n_ready, 1)] = i;
+}
+
+__global__ void k_sync_done(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    d.cnt->n_ready = 0;
+    d.cnt->gts_min = LLONG_MAX;
+    d.cnt->cand_valid = 0;  // new steps: the next sweep tests every element
   }
 }
 
@@ -1513,6 +1578,23 @@ void initial_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, const Til
 }
 
 template <int M>
+void sync_cut_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, long long Tn, const Tiles& tl) {
+  k_sync_done<<<1, 32, 0, s>>>(d);
+  k_sync_cut<M><<<nsm * 4, 256, 0, s>>>(d, Tn);
+  launch_predict<M>(T, d, nsm, s, 0, tl);
+  k_sync_done<<<1, 32, 0, s>>>(d);
+}
+
+template <int M>
+void sync_resume_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s, long long Told, const Tiles& tl) {
+  k_sync_done<<<1, 32, 0, s>>>(d);
+  k_sync_resume<<<nsm * 4, 256, 0, s>>>(d, Told);
+  launch_recon<M>(T, d, nsm, s, 0, tl);
+  launch_predict<M>(T, d, nsm, s, 0, tl);
+  k_sync_done<<<1, 32, 0, s>>>(d);
+}
+
+template <int M>
 void lists_impl(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
   const int grid_all_e = (d.ne + kBlock - 1) / kBlock;
   const int grid_w = nsm * 8;
@@ -1565,6 +1647,22 @@ void launch_phase_a_lists(const Tab& T, const Dev& d, int nsm, cudaStream_t s) {
     case 1: lists_impl<1>(T, d, nsm, s); break;
     case 2: lists_impl<2>(T, d, nsm, s); break;
     default: lists_impl<3>(T, d, nsm, s); break;
+  }
+}
+
+void launch_sync_cut(const Tab& T, const Dev& d, int nsm, cudaStream_t s, long long Tn, const Tiles& tl) {
+  switch (T.M) {
+    case 1: sync_cut_impl<1>(T, d, nsm, s, Tn, tl); break;
+    case 2: sync_cut_impl<2>(T, d, nsm, s, Tn, tl); break;
+    default: sync_cut_impl<3>(T, d, nsm, s, Tn, tl); break;
+  }
+}
+
+void launch_sync_resume(const Tab& T, const Dev& d, int nsm, cudaStream_t s, long long Told, const Tiles& tl) {
+  switch (T.M) {
+    case 1: sync_resume_impl<1>(T, d, nsm, s, Told, tl); break;
+    case 2: sync_resume_impl<2>(T, d, nsm, s, Told, tl); break;
+    default: sync_resume_impl<3>(T, d, nsm, s, Told, tl); break;
   }
 }
 

@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(kBlockNA) k_na_write(aw::Dev d, long long T, c
   if (r) out[base + __popc(m & ((1u << lane) - 1u))] = i;
 }
 
-// address of this device's copy of the scratch array (set up once per device)
-int scratch_address(unsigned int** p) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AW_ERR_CUDA;
+// address of device dev's copy of the scratch array (looked up once per
+// device, with that device current)
+int scratch_address(int dev, unsigned int** p) {
+  if (dev < 0 || dev >= kMaxDevices) return AW_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* a = nullptr;
@@ -102,6 +102,10 @@ extern "C" int aw_ready_set_noalloc(aw_ctx* ctx, int32_t* ready_out, int64_t* n_
     aw::ctx_error(ctx, "aw_ready_set_noalloc: no valid state loaded");
     return AW_ERR_STATE;
   }
+  // the context's device is current from here on (its stream and its copy of
+  // the scratch array belong to it); the caller's device is given back
+  aw::DeviceGuard guard(v.device);
+  cudaGetLastError();  // a launch error left by earlier work is not this call's
   const int ne = v.d->ne;
   const int nb = (ne + kBlockNA - 1) / kBlockNA;
   if (nb > kMaxBlocksNA) {
@@ -109,15 +113,23 @@ extern "C" int aw_ready_set_noalloc(aw_ctx* ctx, int32_t* ready_out, int64_t* n_
     return AW_ERR_INVALID_ARG;
   }
   unsigned int* scratch = nullptr;
-  if (scratch_address(&scratch) != AW_OK) {
+  if (scratch_address(v.device, &scratch) != AW_OK) {
     aw::ctx_error(ctx, "aw_ready_set_noalloc: cudaGetSymbolAddress failed");
     return AW_ERR_CUDA;
   }
   k_na_count<<<nb, kBlockNA, 0, v.stream>>>(*v.d, v.T, scratch);
+  if (cudaGetLastError() != cudaSuccess) {
+    aw::ctx_error(ctx, "aw_ready_set_noalloc: launch of the counting kernel failed");
+    return AW_ERR_CUDA;
+  }
   k_na_scan<<<1, 1024, 0, v.stream>>>(scratch, nb, reinterpret_cast<long long*>(n_ready_out));
+  if (cudaGetLastError() != cudaSuccess) {
+    aw::ctx_error(ctx, "aw_ready_set_noalloc: launch of the scan kernel failed");
+    return AW_ERR_CUDA;
+  }
   k_na_write<<<nb, kBlockNA, 0, v.stream>>>(*v.d, v.T, scratch, ready_out);
   if (cudaGetLastError() != cudaSuccess) {
-    aw::ctx_error(ctx, "aw_ready_set_noalloc: kernel launch failed");
+    aw::ctx_error(ctx, "aw_ready_set_noalloc: launch of the listing kernel failed");
     return AW_ERR_CUDA;
   }
   return AW_OK;

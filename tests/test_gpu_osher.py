@@ -76,6 +76,7 @@ def test_single_sweep_from_snapshot(aw, case):
     assert np.abs(gX - oX).max() < 1e-12 * np.abs(oX).max()
     qs = np.abs(eo["Q"]).max()
     assert np.abs(eg["QM"] - eo["QM"]).max() / qs < 1e-12
+    assert rel(eg["qhat"].reshape(-1, 4), eo["qhat"].reshape(-1, 4)) < 1e-12
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
