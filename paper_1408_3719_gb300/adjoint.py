@@ -15,25 +15,45 @@ import numpy as np
 import torch
 
 
+def _settle(t):
+    """The library reads and writes through its own stream: finish the work
+    queued on torch's current stream of t's device first."""
+    if t.device.type == "cuda":
+        torch.cuda.current_stream(t.device).synchronize()
+
+
 class LtsRun(torch.autograd.Function):
+    """Tensors stay where they are: device tensors are handed to the C ABI
+    by pointer (no host round trip), host tensors likewise."""
+
     @staticmethod
     def forward(ctx, Q0, xy0, solver, n_sweeps, ckpt_every=10):
-        Qh = Q0.detach().to("cpu", torch.float64).contiguous().numpy()
-        xyh = xy0.detach().to("cpu", torch.float64).contiguous().numpy()
-        solver.load_state_xy(Qh, xyh)
+        dev = Q0.device
+        Qd = Q0.detach().to(dtype=torch.float64).contiguous()
+        xyd = xy0.detach().to(device=dev, dtype=torch.float64).contiguous()
+        _settle(Qd)
+        solver.load_state_xy(Qd, xyd)
         solver.adjoint_forward(int(n_sweeps), int(ckpt_every))
-        e = solver.get_elem()
+        Q = torch.empty((solver.n_tris, 4), dtype=torch.float64, device=dev)
+        X = torch.empty((solver.n_tris, 6), dtype=torch.float64, device=dev)
+        solver.get_elem_into(Q=Q, X=X)
         ctx.solver = solver
-        ctx.dev = Q0.device
-        return (torch.from_numpy(e["Q"]).to(Q0.device), torch.from_numpy(e["X"]).to(Q0.device))
+        ctx.dev = dev
+        ctx.n_nodes = xy0.shape[0]
+        return Q, X
 
     @staticmethod
     def backward(ctx, gQ, gX):
-        s = ctx.solver
-        gq = None if gQ is None else gQ.detach().to("cpu", torch.float64).contiguous().numpy()
-        gx = None if gX is None else gX.detach().to("cpu", torch.float64).contiguous().numpy()
-        gQ0, gxy0 = s.adjoint(gq, gx, None)
-        return torch.from_numpy(gQ0).to(ctx.dev), torch.from_numpy(gxy0).to(ctx.dev), None, None, None
+        s, dev = ctx.solver, ctx.dev
+        gq = None if gQ is None else gQ.detach().to(device=dev, dtype=torch.float64).contiguous()
+        gx = None if gX is None else gX.detach().to(device=dev, dtype=torch.float64).contiguous()
+        for g in (gq, gx):
+            if g is not None:
+                _settle(g)
+        gQ0 = torch.empty((s.n_tris, 4), dtype=torch.float64, device=dev)
+        gxy0 = torch.empty((ctx.n_nodes, 2), dtype=torch.float64, device=dev)
+        s.adjoint(gq, gx, None, out_Q=gQ0, out_xy=gxy0)
+        return gQ0, gxy0, None, None, None
 
 
 def triangle_areas(X):

@@ -304,6 +304,16 @@ class Solver:
                                                            ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")]))
         return out
 
+    def get_elem_into(self, **out):
+        """Copy the named element arrays (Q, QM, HM, t, dt, X, count, qhat)
+        into the given buffers: numpy arrays or torch tensors (host or
+        device, contiguous, of the layout of include/aleweno.h)."""
+        keys = ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")
+        bad = set(out) - set(keys)
+        if bad:
+            raise ValueError(f"unknown element arrays {sorted(bad)}")
+        self._check(self.lib.aw_get_elem_arrays(self.h, *[_ptr(out.get(k)) for k in keys]))
+
     def set_elem(self, st):
         arrs = [_arr(st[k], np.int64 if k in ("t", "dt", "count") else np.float64)
                 for k in ("Q", "QM", "HM", "t", "dt", "X", "count", "qhat")]

@@ -185,8 +185,10 @@ def test_autograd_function_gives_the_adjoint_gradient():
     xyt = torch.tensor(mesh["xy"], dtype=torch.float64, device="cuda", requires_grad=True)
     mask = torch.tensor(_mask(mesh), device="cuda")
     Q, X = LtsRun.apply(Qt, xyt, s, 10, 5)
+    assert Q.is_cuda and X.is_cuda  # the run's outputs stay on the device
     J = kinetic_energy(Q, X, mask)
     J.backward()
+    assert Qt.grad.is_cuda and xyt.grad.is_cuda
     run = GpuCase(aleweno, mesh, Q0, 2, 10, 5)
     assert abs(J.item() - run.J0) <= 1e-14 * abs(run.J0)
     assert np.abs(Qt.grad.cpu().numpy() - run.gQ0).max() <= 1e-12 * np.abs(run.gQ0).max()
