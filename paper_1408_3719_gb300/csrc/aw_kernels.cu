@@ -740,8 +740,20 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
   // that fits the block, otherwise after the tau > 0 nodes.
   constexpr int nBot = G * Mc, nTop = G * Mc * (Nt - 1), nBotPad = (nBot + 31) / 32 * 32;
   constexpr bool padBot = nBotPad + nTop <= TH;
+  // When one element's tau > 0 nodes nearly fill a warp (30 of 32 lanes at
+  // fourth order), each element gets a warp of its own: the warps of the
+  // elements a round leaves empty (balanced rounds give a block fewer than G
+  // elements) then issue no instruction at all.
+  constexpr int nTopE = Mc * (Nt - 1);
+  constexpr bool perWarp = nTopE > 16 && nTopE <= 32 && nBotPad + 32 * G <= TH;
   int t, rr;
-  if (padBot) {
+  if (perWarp) {
+    const int x = threadIdx.x;
+    const int ew = (x - nBotPad) >> 5, k = (x - nBotPad) & 31;
+    if (x < nBot) { t = 0; rr = x; }
+    else if (x >= nBotPad && ew < G && k < nTopE) { t = 1 + k / Mc; rr = ew * Mc + k % Mc; }
+    else { t = Nt; rr = 0; }
+  } else if (padBot) {
     const int x = threadIdx.x;
     if (x < nBot) { t = 0; rr = x; }
     else if (x >= nBotPad && x < nBotPad + nTop) { t = 1 + (x - nBotPad) / nBot; rr = (x - nBotPad) % nBot; }
@@ -755,9 +767,15 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
   const int e = t < Nt ? rr / Mc : G;
   const int s = rr % Mc, l = (t < Nt ? t : 0) * Mc + s;
   const double gm1 = T.gamma - 1.0;
-  for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
+  for (int consumed = 0; consumed < n_ready;) {
+    // balanced rounds, as in the reconstruction
+    const int per = min(G, (n_ready - consumed + (int)gridDim.x - 1) / (int)gridDim.x);
+    const int base = consumed + (int)blockIdx.x * per;
+    const int cnt = max(0, min(per, n_ready - base));
+    consumed += per * (int)gridDim.x;
+    if (cnt == 0) continue;  // block-uniform
     const int pos = base + e;
-    const bool live = e < G && pos < n_ready;
+    const bool live = e < cnt;
     if (live && l == 0) {
       const int i = initial ? pos : d.ready_list[pos];
       long long dtk = d.dt[i];
@@ -1057,11 +1075,19 @@ k_recon_coop(Tab T, Dev d, int initial) {
   for (int k = tid; k < Mc * NU; k += nth) sBn[k] = T.Bnod[k / NU][k % NU];
   const int n_ready = initial ? d.ne : d.cnt->n_ready;
   const long long Ts = d.cnt->t_sync;
-  for (int base = blockIdx.x * G; base < n_ready; base += gridDim.x * G) {
+  for (int consumed = 0; consumed < n_ready;) {
+    // balanced rounds: every block takes the same number of elements (at
+    // most G) per round, so that the elements of the last round spread over
+    // all blocks instead of stacking on a few of them
+    const int per = min(G, (n_ready - consumed + (int)gridDim.x - 1) / (int)gridDim.x);
+    const int base = consumed + (int)blockIdx.x * per;
+    const int cnt = max(0, min(per, n_ready - base));
+    consumed += per * (int)gridDim.x;
+    if (cnt == 0) continue;  // block-uniform
     // P0: element set-up
     if (tid < G) {
       const int e = tid, pos = base + e;
-      const bool v = pos < n_ready;
+      const bool v = e < cnt;
       sVal[e] = v;
       int nU = 0;
       if (v) {
@@ -1205,7 +1231,7 @@ k_recon_coop(Tab T, Dev d, int initial) {
         double dd = L[a][a];
 #pragma unroll
         for (int k = 0; k < a; ++k) dd -= L[a][k] * L[a][k];
-        const double il = 1.0 / sqrt(dd);
+        const double il = rsqrt(dd);
         L[a][a] = il;
 #pragma unroll
         for (int b = a + 1; b < NU; ++b) {
@@ -1527,7 +1553,10 @@ template <int M, int TH>
 void launch_predict_t(const Tab& T, const Dev& d, int nsm, cudaStream_t s, int initial, int bpsm) {
   using S = PredShape<M, TH>;
   const int need = (d.ne + S::G - 1) / S::G;
-  const int grid = initial ? need : std::min(need, nsm * bpsm);
+  // sweeps: the blocks that fit on the GPU at once (the launch bounds' two or
+  // three per SM), so that balanced rounds give every SM the same elements
+  const int grid = initial ? need : std::min(need, nsm * (TH >= 256 ? 2 : 3));
+  (void)bpsm;
   k_predict_coop<M, TH><<<grid, S::kThreads, 0, s>>>(T, d, initial, T.gts);
 }
 

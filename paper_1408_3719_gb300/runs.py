@@ -122,11 +122,11 @@ def explosion(order=2, hc=0.00114, gts=False, flux="rusanov", cfl=0.5, t_switch=
     return info
 
 
-def riemann(case="RP1", order=2, gts=False, flux="osher", jitter=0.0):
+def riemann(case="RP1", order=2, gts=False, flux="osher", jitter=0.0, cfl=0.5):
     """A shock tube of Sec. 3.2 as the paper sets it up; density L1 error of
     the averages against the exact solution, weighted by area."""
     mesh, Q, t_end = W.riemann_problem(case, jitter=jitter)
-    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux)
+    e, info = _run(mesh, Q, order_M=order, t_end=t_end, gts=gts, flux=flux, cfl=cfl)
     A = _areas(e["X"])
     cx = e["X"].reshape(-1, 3, 2).mean(1)[:, 0]
     left, right, _ = W.RIEMANN_PROBLEMS[case]
@@ -259,7 +259,7 @@ def main():
     ap.add_argument("--n", type=int, nargs="+", default=[45, 90, 179])
     ap.add_argument("--hc", type=float, default=0.00114)
     ap.add_argument("--cfl", type=float, default=0.5,
-                    help="explosion, ep, saltzman: CFL number of eq. timestep (saltzman: after its start-up)")
+                    help="explosion, rp, ep, saltzman: CFL number of eq. timestep (saltzman: after its start-up)")
     ap.add_argument("--t-switch", type=float, default=0.0,
                     help="explosion, ep: global steps until this time, then local steps")
     ap.add_argument("--cfl-start", type=float, default=0.0, help="explosion, ep: CFL of the start-up steps")
@@ -277,7 +277,7 @@ def main():
         except RuntimeError as err:
             print(json.dumps(dict(config="Saltzman", gts=a.gts, failed=str(err)[:600])), flush=True)
     elif a.case == "rp":
-        print(json.dumps(riemann(a.problem or "RP1", a.order or 2, a.gts, flux)), flush=True)
+        print(json.dumps(riemann(a.problem or "RP1", a.order or 2, a.gts, flux, cfl=a.cfl)), flush=True)
     elif a.case == "ep":
         print(json.dumps(explosion_paper(a.problem or "EP1", a.order or 2, a.gts, flux, a.t_end, cfl=a.cfl,
                                          t_switch=a.t_switch, cfl_start=a.cfl_start or a.cfl)), flush=True)
