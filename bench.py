@@ -62,6 +62,7 @@ def recon_flops(M: int, members: float) -> float:
     per_stencil = ((NE - 1) * (NU * (NU + 1) + 8 * NU)  # normal equations
                    + NU ** 3 / 3 + 2 * NU               # Cholesky
                    + 4 * 2 * NU * NU                    # two triangular solves, 4 right-hand sides
+                   + 4 * (4 * (NE - 1) * NU + 2 * NU * NU)  # one refinement: r = b - A y, A^T r, two solves
                    + NU * 32                            # characteristic projection
                    + 4 * (NU * (NU + 1) + NU))          # smoothness indicators
     weights = 4 * (7 * 8 + NU * 7 * 2) + NU * 32 + Mc * 4 * NU * 2
@@ -414,7 +415,7 @@ def run_ours(args, rank, world):
     # per-launch DRAM bytes and executed FP64 operations of the same kernels
     # from the committed ncu capture, used only while the kernel source is
     # the one that capture measured
-    ncu = read_ncu_counters(os.path.join(ROOT, "profiles", f"ncu_counters_explosion500k_p{args.order}.txt"))
+    ncu = read_ncu_counters(os.path.join(ROOT, "profiles", f"ncu_counters_explosion_p{args.order}.txt"))
     ncu_valid = ncu.get("source_sha") == kernel_source_digest() and args.flux == "rusanov"
     roof = None
     if dom in model and kms[dom] > 0:
