@@ -132,7 +132,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -225,7 +225,7 @@ def read_ncu_counters(path):
                 if "=" in line:
                     k, v = (x.strip() for x in line.split("=", 1))
                     try:
-                        out[k] = float(v)
+                        out[k] = v if k == "source_sha" else float(v)
                     except ValueError:
                         out[k] = v
     except OSError:
@@ -364,18 +364,21 @@ def run_ours(args, rank, world):
         tiles, tune_ms = s.get_tiles(), {}
     else:
         tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
+    # the mid-run state for the end-to-end measurement below
+    snap, snap_nodes = (s.get_elem(), s.get_nodes()) if args.e2e else (None, None)
+    # clocks and throttle reasons sampled from the warm-up sweeps through the
+    # timed region (which alone lasts ~10 ms)
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         s.sweep()
     s.get_state(t=t_el)
     t_range = [float(t_el.min()), float(np.median(t_el)), float(t_el.max())]
-    snap, snap_nodes = (s.get_elem(), s.get_nodes()) if args.e2e else (None, None)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > 129 MB L2
     s.sync()
-    clocks = ClockSampler(local)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
@@ -459,7 +462,7 @@ def run_ours(args, rank, world):
                    "path is bound by the FP64 pipe, see roofline"}
 
     # end to end through the C ABI with host buffers: the mid-run state
-    # (the one the timed sweeps started from) uploaded from pinned host
+    # (taken just before the driver's warm-up sweeps) uploaded from pinned host
     # memory, e2e_sweeps sweeps, the averages read back to pinned host memory
     e2e = None
     if args.e2e:
@@ -481,7 +484,7 @@ def run_ours(args, rank, world):
         h2d = sum(v.numel() * v.element_size() for v in pin.values()) + pnX.numel() * 8 + pnt.numel() * 8
         e2e = {"value": ups / el, "unit": UNIT, "h2d_bytes_per_step": h2d / nst,
                "d2h_bytes_per_step": (out.numel() * 8 + 16) / nst,
-               "note": "aw_set_elem_arrays + aw_set_node_arrays (the mid-run state the timed sweeps started from, "
+               "note": "aw_set_elem_arrays + aw_set_node_arrays (the mid-run state before the driver's warm-up sweeps, "
                        "pinned host memory) + aw_enqueue_sweeps + aw_sync (update count) + aw_get_state (averages "
                        "to pinned host memory), host wall time, the tile shapes of the device-timed run"}
         s2.close()

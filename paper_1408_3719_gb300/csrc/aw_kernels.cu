@@ -70,11 +70,12 @@ __global__ void k_ready(Tab T, Dev d) {
   if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->gts_min = LLONG_MAX;
   for (int qb = warp * (32 / GL); qb < n_items; qb += nwarps * (32 / GL)) {  // warp-uniform
     const int q = qb + lane / GL;
-    int i = -1;
+    int i = -1, vn = -1;
     long long tn = 0;
     bool ready = false;
     if (q < n_items) {
       i = listed ? clist[q] : q;
+      if (gl < 3) vn = d.tri[3 * i + gl];  // the vertex this lane moves if i is ready, loaded early
       const long long ti = d.t[i];
       if (ti < Ts) {
         tn = ti + d.dt[i];
@@ -113,7 +114,7 @@ __global__ void k_ready(Tab T, Dev d) {
     bool claim = false;
     int n = -1;
     if (ready && gl < 3) {
-      n = d.tri[3 * i + gl];
+      n = vn;
       d.ntn[n] = tn;
       claim = atomicExch(&d.node_moved[n], epoch) != epoch;
     }
@@ -133,11 +134,14 @@ __global__ void k_finish(Tab T, Dev d) {
   const int n_moved = d.cnt->n_moved;
   const int n_ready = d.cnt->n_ready;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  // loads before stores (a load after a store that may alias it waits for it)
   for (int q = gtid; q < n_moved; q += nth) {
     const int n = d.moved_list[q];
-    d.nX[2 * n] = d.nXn[2 * n];
-    d.nX[2 * n + 1] = d.nXn[2 * n + 1];
-    d.nt[n] = d.ntn[n];
+    const double x = d.nXn[2 * n], y = d.nXn[2 * n + 1];
+    const long long tn = d.ntn[n];
+    d.nX[2 * n] = x;
+    d.nX[2 * n + 1] = y;
+    d.nt[n] = tn;
   }
   if (!T.gts) {
     const int par = (epoch + 1) & 1;
@@ -145,12 +149,16 @@ __global__ void k_finish(Tab T, Dev d) {
     const int lane = threadIdx.x & 31;
     for (int q = gtid >> 5; q < n_ready; q += nth >> 5) {
       const int i = d.ready_list[q];
-      for (int p = d.sw_ptr[i] + lane, pe = d.sw_ptr[i + 1]; p < pe; p += 32) {
-        const int j = d.sw[p];
-        if (atomicExch(&d.cand_stamp[j], epoch) != epoch) {
-          const int s2 = atomicAdd(&d.cnt->n_cand[par], 1);
-          clist[s2] = j;
-        }
+      for (int p = d.sw_ptr[i] + lane, pe = d.sw_ptr[i + 1]; p < pe; p += 96) {
+        int jj[3];  // three chunks of the total stencil loaded before their atomics
+#pragma unroll
+        for (int u = 0; u < 3; ++u) jj[u] = p + 32 * u < pe ? d.sw[p + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (jj[u] >= 0 && atomicExch(&d.cand_stamp[jj[u]], epoch) != epoch) {
+            const int s2 = atomicAdd(&d.cnt->n_cand[par], 1);
+            clist[s2] = jj[u];
+          }
       }
     }
   }
@@ -188,10 +196,18 @@ __global__ void k_nodes_grp(Tab T, Dev d) {
     const int item = base + threadIdx.x;
     const int q = item / GS, lane = item % GS;
     double num0 = 0.0, num1 = 0.0, den = 0.0;
-    int n = -1;
+    int n = -1, ty = 0;
+    double nnx = 0.0, nny = 0.0, x0 = 0.0, y0 = 0.0;
     if (item < n_items) {
       n = d.moved_list[q];
       const long long tk0 = d.nt[n], tk1 = d.ntn[n];
+      if (lane == 0) {  // the node's own data, loaded beside the Voronoi loop's
+        ty = d.node_type[n];
+        nnx = d.node_n[2 * n];
+        nny = d.node_n[2 * n + 1];
+        x0 = d.nX[2 * n];
+        y0 = d.nX[2 * n + 1];
+      }
       for (int p = d.v2e_ptr[n] + lane, pe = d.v2e_ptr[n + 1]; p < pe; p += GS) {
         const int j = d.v2e[p];
         const int k = d.v2e_loc[p];
@@ -230,9 +246,8 @@ __global__ void k_nodes_grp(Tab T, Dev d) {
     if (item < n_items && lane == 0) {
       const double iden = 1.0 / den;
       double D0 = num0 * iden, D1 = num1 * iden;
-      const int ty = d.node_type[n];
       if (ty == 1) {
-        const double nx = d.node_n[2 * n], ny = d.node_n[2 * n + 1];
+        const double nx = nnx, ny = nny;
         const double dn = D0 * nx + D1 * ny;
         D0 -= dn * nx;
         D1 -= dn * ny;
@@ -243,8 +258,8 @@ __global__ void k_nodes_grp(Tab T, Dev d) {
         D0 = T.wall_u * span;
         D1 = T.wall_v * span;
       }
-      d.nXn[2 * n] = d.nX[2 * n] + D0;
-      d.nXn[2 * n + 1] = d.nX[2 * n + 1] + D1;
+      d.nXn[2 * n] = x0 + D0;
+      d.nXn[2 * n + 1] = y0 + D1;
     }
   }
 }
@@ -258,11 +273,12 @@ __global__ void k_edges(Dev d) {
     const int n = d.moved_list[item >> 3];
     for (int p = d.n2e_ptr[n] + (item & 7), pe = d.n2e_ptr[n + 1]; p < pe; p += 8) {
       const int ed = d.n2e[p];
+      const int ee[2] = {d.edge_elem[2 * ed], d.edge_elem[2 * ed + 1]};  // loaded beside the claim
       if (atomicExch(&d.edge_act[ed], epoch) == epoch) continue;
       const int slot = atomicAdd(&d.cnt->n_active, 1);
       d.active_list[slot] = ed;
       for (int k = 0; k < 2; ++k) {
-        const int e = d.edge_elem[2 * ed + k];
+        const int e = ee[k];
         if (e >= 0 && atomicExch(&d.elem_touch[e], epoch) != epoch) {
           const int s2 = atomicAdd(&d.cnt->n_touched, 1);
           d.touch_list[s2] = e;
@@ -510,6 +526,9 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
 }
 
 __global__ void k_update(Tab T, Dev d) {
+  // Every load of a thread is issued before its first store: a load after a
+  // store to memory that might alias it waits for the store, and this kernel
+  // is a chain of dependent gathers whose round trips set its duration.
   const int epoch = d.cnt->epoch;
   const long long Ts = d.cnt->t_sync;
   const int n_touched = d.cnt->n_touched;
@@ -519,57 +538,93 @@ __global__ void k_update(Tab T, Dev d) {
     bool upd = false;
     double gcl = 0.0;  // GCL residual of this thread's update (non-negative)
     if (q < n_touched) {
-      int i = d.touch_list[q];
-      bool ready = d.elem_ready[i] == epoch;
-      double sg[3];
+      const int i = d.touch_list[q];
+      const bool ready = d.elem_ready[i] == epoch;
       int eds[3];
       bool act[3];
+      double sg[3], Ge[3][4], Ne[3][3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) eds[e] = d.elem_edge[3 * i + e];
+#pragma unroll
       for (int e = 0; e < 3; ++e) {
-        int ed = d.elem_edge[3 * i + e];
-        eds[e] = ed;
-        act[e] = d.edge_act[ed] == epoch;
-        sg[e] = d.edge_elem[2 * ed] == i ? 1.0 : -1.0;
+        act[e] = d.edge_act[eds[e]] == epoch;
+        sg[e] = d.edge_elem[2 * eds[e]] == i ? 1.0 : -1.0;
       }
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Ge[e][v] = act[e] ? d.G[4 * (size_t)eds[e] + v] : 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Ne[e][c] = act[e] ? d.N[4 * (size_t)eds[e] + c] : 0.0;
+      }
+      double Qo[4], QMo[4], HMo[3];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { Qo[v] = d.Q[4 * i + v]; QMo[v] = d.QM[4 * i + v]; }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) HMo[c] = d.HM[4 * i + c];
       if (ready) {
         upd = true;
-        double Xn[6];
+        double Xo[6], Xn[6];
+        int nd[3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Xo[k] = d.X[6 * i + k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nd[k] = d.tri[3 * i + k];
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-          int n = d.tri[3 * i + k];
-          Xn[2 * k] = d.nXn[2 * n] + d.cshift[6 * i + 2 * k];
-          Xn[2 * k + 1] = d.nXn[2 * n + 1] + d.cshift[6 * i + 2 * k + 1];
+          Xn[2 * k] = d.nXn[2 * nd[k]] + d.cshift[6 * i + 2 * k];
+          Xn[2 * k + 1] = d.nXn[2 * nd[k] + 1] + d.cshift[6 * i + 2 * k + 1];
         }
-        double Aold = area6(d.X + 6 * i), Anew = area6(Xn);
+        const long long ti = d.t[i], dti = d.dt[i], ci = d.count[i];
+        double Aold = area6(Xo), Anew = area6(Xn);
         double Qn[4];
         for (int v = 0; v < 4; ++v) {
-          double acc = Aold * d.Q[4 * i + v];
+          double acc = Aold * Qo[v];
           for (int e = 0; e < 3; ++e)
-            if (act[e]) acc -= sg[e] * d.G[4 * (size_t)eds[e] + v];
-          acc += d.QM[4 * i + v];
+            if (act[e]) acc -= sg[e] * Ge[e][v];
+          acc += QMo[v];
           Qn[v] = acc / Anew;
-          d.Q[4 * i + v] = Qn[v];
-          d.QM[4 * i + v] = 0.0;
         }
         double res[3];
         for (int c = 0; c < 3; ++c) {
           double acc = 0.0;
           for (int e = 0; e < 3; ++e)
-            if (act[e]) acc += sg[e] * d.N[4 * (size_t)eds[e] + c];
-          res[c] = acc - d.HM[4 * i + c];
-          d.HM[4 * i + c] = 0.0;
+            if (act[e]) acc += sg[e] * Ne[e][c];
+          res[c] = acc - HMo[c];
         }
         res[2] += Anew - Aold;
         gcl = fmax(fabs(res[0]), fmax(fabs(res[1]), fabs(res[2]))) / Aold;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          d.Q[4 * i + v] = Qn[v];
+          d.QM[4 * i + v] = 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d.HM[4 * i + c] = 0.0;
+#pragma unroll
         for (int k = 0; k < 6; ++k) d.X[6 * i + k] = Xn[k];
-        d.t[i] += d.dt[i];
-        if (d.t[i] >= Ts) atomicSub(&d.cnt->n_unfinished, 1);
-        d.count[i] += 1;
+        d.t[i] = ti + dti;
+        if (ti + dti >= Ts) atomicSub(&d.cnt->n_unfinished, 1);
+        d.count[i] = ci + 1;
         if (!(Qn[0] > 0.0) || !(pressure(T, Qn) > 0.0) || !(Anew > 0.0)) set_error(d.cnt, -3, i);
       } else {
-        for (int e = 0; e < 3; ++e) {
-          if (!act[e]) continue;
-          for (int v = 0; v < 4; ++v) d.QM[4 * i + v] -= sg[e] * d.G[4 * (size_t)eds[e] + v];
-          for (int c = 0; c < 3; ++c) d.HM[4 * i + c] -= sg[e] * d.N[4 * (size_t)eds[e] + c];
+        double QMn[4], HMn[3];
+        for (int v = 0; v < 4; ++v) {
+          double acc = QMo[v];
+          for (int e = 0; e < 3; ++e)
+            if (act[e]) acc -= sg[e] * Ge[e][v];
+          QMn[v] = acc;
         }
+        for (int c = 0; c < 3; ++c) {
+          double acc = HMo[c];
+          for (int e = 0; e < 3; ++e)
+            if (act[e]) acc -= sg[e] * Ne[e][c];
+          HMn[c] = acc;
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d.QM[4 * i + v] = QMn[v];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d.HM[4 * i + c] = HMn[c];
       }
     }
     unsigned um = __ballot_sync(0xffffffffu, upd);
