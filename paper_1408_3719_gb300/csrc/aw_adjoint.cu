@@ -11,7 +11,8 @@
 //   k_adj_nodes   node solver NS_cs (eqs. eqnNScs, NodesVel, newVertex)
 // The lists of the sweep (ready elements, moved nodes, active edges, touched
 // elements) and the new node positions come from re-running the forward
-// k_ready, k_nodes and k_edges on the restored sweep-start state.  Scatters to
+// k_ready, k_nodes and k_edges on the sweep-start state, which they read
+// where its snapshot holds it (they write only lists and scratch).  Scatters to
 // other elements and nodes use atomics; the slots an element owns (its
 // tables, its edges' traces) are written by one thread only.
 #include <algorithm>

@@ -672,6 +672,8 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
 // Predictor of one element and its derived tables
 // ---------------------------------------------------------------------------
 constexpr int kMaxIt = 6;  // Picard iterations the reverse can store
+// slots of a node's metric terms (node_geo)
+enum { kGxx, kGxe, kGyx, kGye, kGxt, kGyt, kGid, kGxix, kGxiy, kGetx, kGety, kGxit, kGett, kNGeo };
 
 template <int M>
 struct PredTape {
@@ -696,6 +698,7 @@ template <int M>
 struct PredWork {
   using S = Sz<M>;
   double q[S::Nst][4], x[S::Nst][2], F[S::Nst][4], G[S::Nst][4], P[S::Nst][4], V[S::Nst][2];
+  double geo[S::Nst][kNGeo];
 };
 template <int M>
 struct PredRev {
@@ -707,44 +710,66 @@ struct PredRev {
   double dq[S::Nst][6][4], dx[S::Nst][6];
   double part[S::Nst][4][6];  // per variable: adjoints of xi_t, eta_t, xi_x, eta_x, xi_y, eta_y
   double fgq[S::Nst][3][4];   // per variable: gathered adjoints of q, f, g at a node
-  double geo[S::Nst][13];     // metric terms of every node (xx xe yx ye xt yt idet xix xiy etx ety xit ett)
+  double geo[S::Nst][kNGeo];  // metric terms of every node (node_geo)
 };
 
-// the metric terms of node (t, s) and the derivative sums of one variable v
-struct NodeGeoV {
-  double Qx, Qe, fx, fe, gx, ge;
-  double xx, xe, yx, ye, xt, yt, idet, xix, xiy, etx, ety, xit, ett;
-};
-
+// metric terms of node (t, s) of an iterate: x_xi, x_eta, y_xi, y_eta, x_tau,
+// y_tau (per unit time), 1/det and the inverse map xi_x, xi_y, eta_x, eta_y,
+// xi_t, eta_t, stored as geo[13] in that order (xx xe yx ye xt yt idet xix xiy
+// etx ety xit ett)
 template <int M>
-AW_HD inline void node_geo_v(const Tab& T, const double (*q)[4], const double (*x)[2], const double (*F)[4],
-                             const double (*G)[4], int t, int s, int v, double idt, bool stat, NodeGeoV& n) {
+AW_HD inline void node_geo(const Tab& T, const double (*x)[2], int t, int s, double idt, bool stat, double* g) {
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt;
-  n.Qx = n.Qe = n.fx = n.fe = n.gx = n.ge = 0.0;
-  n.xx = n.xe = n.yx = n.ye = 0.0;
+  double xx = 0.0, xe = 0.0, yx = 0.0, ye = 0.0;
   for (int r = 0; r < Mc; ++r) {
     const double a = T.Dxi[s][r], b = T.Deta[s][r];
     const int lr = t * Mc + r;
-    n.Qx += a * q[lr][v]; n.Qe += b * q[lr][v];
-    n.fx += a * F[lr][v]; n.fe += b * F[lr][v];
-    n.gx += a * G[lr][v]; n.ge += b * G[lr][v];
-    n.xx += a * x[lr][0]; n.xe += b * x[lr][0];
-    n.yx += a * x[lr][1]; n.ye += b * x[lr][1];
+    xx += a * x[lr][0]; xe += b * x[lr][0];
+    yx += a * x[lr][1]; ye += b * x[lr][1];
   }
-  n.xt = n.yt = 0.0;
+  double xt = 0.0, yt = 0.0;
   if (!stat) {
     for (int u = 0; u < Nt; ++u) {
-      n.xt += T.Dtau[t][u] * x[u * Mc + s][0];
-      n.yt += T.Dtau[t][u] * x[u * Mc + s][1];
+      xt += T.Dtau[t][u] * x[u * Mc + s][0];
+      yt += T.Dtau[t][u] * x[u * Mc + s][1];
     }
-    n.xt *= idt;
-    n.yt *= idt;
+    xt *= idt;
+    yt *= idt;
   }
-  n.idet = 1.0 / (n.xx * n.ye - n.xe * n.yx);
-  n.xix = n.ye * n.idet; n.xiy = -n.xe * n.idet; n.etx = -n.yx * n.idet; n.ety = n.xx * n.idet;
-  n.xit = -(n.xix * n.xt + n.xiy * n.yt);
-  n.ett = -(n.etx * n.xt + n.ety * n.yt);
+  const double idet = 1.0 / (xx * ye - xe * yx);
+  const double xix = ye * idet, xiy = -xe * idet, etx = -yx * idet, ety = xx * idet;
+  g[kGxx] = xx; g[kGxe] = xe; g[kGyx] = yx; g[kGye] = ye; g[kGxt] = xt; g[kGyt] = yt; g[kGid] = idet;
+  g[kGxix] = xix; g[kGxiy] = xiy; g[kGetx] = etx; g[kGety] = ety;
+  g[kGxit] = -(xix * xt + xiy * yt);
+  g[kGett] = -(etx * xt + ety * yt);
+}
+
+// reference-space derivatives of variable v of q, f and g at node (t, s):
+// d = {Q_xi, Q_eta, f_xi, f_eta, g_xi, g_eta}
+template <int M>
+AW_HD inline void node_sums_v(const Tab& T, const double (*q)[4], const double (*F)[4], const double (*G)[4], int t,
+                              int s, int v, double* d) {
+  using S = Sz<M>;
+  constexpr int Mc = S::Mc;
+  double Qx = 0.0, Qe = 0.0, fx = 0.0, fe = 0.0, gx = 0.0, ge = 0.0;
+  for (int r = 0; r < Mc; ++r) {
+    const double a = T.Dxi[s][r], b = T.Deta[s][r];
+    const int lr = t * Mc + r;
+    Qx += a * q[lr][v]; Qe += b * q[lr][v];
+    fx += a * F[lr][v]; fe += b * F[lr][v];
+    gx += a * G[lr][v]; ge += b * G[lr][v];
+  }
+  d[0] = Qx; d[1] = Qe; d[2] = fx; d[3] = fe; d[4] = gx; d[5] = ge;
+}
+
+// first item of the per-node metric work in a loop that shares its pass with
+// the Nst per-node items: the next warp boundary for a multi-warp team, so
+// that the two kinds of work run on different warps
+template <int M, class Tm>
+AW_HD inline int geo_offset(const Tm& tm) {
+  constexpr int Nst = Sz<M>::Nst;
+  return tm.size >= 64 ? (Nst + 31) / 32 * 32 : Nst;
 }
 
 // Euler fluxes and mesh velocity of one node (one reciprocal of rho)
@@ -773,21 +798,30 @@ AW_HD void pred_fwd(const Tab& T, int nit, const double (*w)[4], const double* X
   }
   tm.sync();
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
+  const int goff = geo_offset<M>(tm);
   for (int it = 0; it < nit; ++it) {
     const int nsl = it == 0 ? 1 : Nt;
-    for (int l = tm.rank; l < Nst; l += tm.size) {
-      for (int v = 0; v < 4; ++v) tp.q[it][l][v] = wk.q[l][v];
-      tp.x[it][l][0] = wk.x[l][0];
-      tp.x[it][l][1] = wk.x[l][1];
-      if (l < nsl * Mc) node_fluxes(T, wk.q[l], wk.F[l], wk.G[l], wk.V[l]);
+    // per node: tape, fluxes; on other ranks: the node's metric terms
+    for (int item = tm.rank; item < goff + nsl * Mc; item += tm.size) {
+      if (item < Nst) {
+        const int l = item;
+        for (int v = 0; v < 4; ++v) tp.q[it][l][v] = wk.q[l][v];
+        tp.x[it][l][0] = wk.x[l][0];
+        tp.x[it][l][1] = wk.x[l][1];
+        if (l < nsl * Mc) node_fluxes(T, wk.q[l], wk.F[l], wk.G[l], wk.V[l]);
+      } else if (item >= goff) {
+        const int l = item - goff;
+        node_geo<M>(T, wk.x, l / Mc, l % Mc, idt, it == 0, wk.geo[l]);
+      }
     }
     tm.sync();
     for (int it4 = tm.rank; it4 < nsl * Mc * 4; it4 += tm.size) {
       const int l = it4 / 4, v = it4 % 4;
-      NodeGeoV n;
-      node_geo_v<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, v, idt, it == 0, n);
-      const double fs = -(n.fx * n.xix + n.fe * n.etx + n.gx * n.xiy + n.ge * n.ety);
-      wk.P[l][v] = fs - (n.Qx * n.xit + n.Qe * n.ett);
+      double d[6];
+      node_sums_v<M>(T, tp.q[it], wk.F, wk.G, l / Mc, l % Mc, v, d);
+      const double* g = wk.geo[l];
+      const double fs = -(d[2] * g[kGxix] + d[3] * g[kGetx] + d[4] * g[kGxiy] + d[5] * g[kGety]);
+      wk.P[l][v] = fs - (d[0] * g[kGxit] + d[1] * g[kGett]);
     }
     tm.sync();
     for (int l = Mc + tm.rank; l < Nst; l += tm.size) {
@@ -904,10 +938,18 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
   tm.sync();
   // Picard iterations in reverse
   const double idt = nit > 0 ? 1.0 / dts : 0.0;
+  const int goff = geo_offset<M>(tm);
   for (int it = nit - 1; it >= 0; --it) {
     const int nsl = it == 0 ? 1 : Nt;
     const bool stat = it == 0;
-    for (int l = tm.rank; l < Nst; l += tm.size) {
+    for (int item = tm.rank; item < goff + nsl * Mc; item += tm.size) {
+      if (item >= goff) {  // the node's metric terms in the iterate
+        const int l = item - goff;
+        node_geo<M>(T, tp.x[it], l / Mc, l % Mc, idt, stat, wk.geo[l]);
+        continue;
+      }
+      if (item >= Nst) continue;
+      const int l = item;
       const int u = l / Mc, s = l % Mc;
       double P[4] = {0, 0, 0, 0}, V[2] = {0, 0};
       if (it > 0 || u == 0)
@@ -944,27 +986,26 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
     // then the metric terms of the node
     for (int it4 = tm.rank; it4 < nsl * Mc * 4; it4 += tm.size) {
       const int l = it4 / 4, v = it4 % 4;
-      NodeGeoV n;
-      node_geo_v<M>(T, tp.q[it], tp.x[it], wk.F, wk.G, l / Mc, l % Mc, v, idt, stat, n);
-      if (v == 0) {
-        double* g = wk.geo[l];
-        g[0] = n.xx; g[1] = n.xe; g[2] = n.yx; g[3] = n.ye; g[4] = n.xt; g[5] = n.yt; g[6] = n.idet;
-        g[7] = n.xix; g[8] = n.xiy; g[9] = n.etx; g[10] = n.ety; g[11] = n.xit; g[12] = n.ett;
-      }
+      double d[6];
+      node_sums_v<M>(T, tp.q[it], wk.F, wk.G, l / Mc, l % Mc, v, d);
+      const double* g = wk.geo[l];
       const double Pb = wk.Pb[l][v];
-      wk.dq[l][0][v] = -Pb * n.xit; wk.dq[l][1][v] = -Pb * n.ett;
-      wk.dq[l][2][v] = -Pb * n.xix; wk.dq[l][3][v] = -Pb * n.etx;
-      wk.dq[l][4][v] = -Pb * n.xiy; wk.dq[l][5][v] = -Pb * n.ety;
+      wk.dq[l][0][v] = -Pb * g[kGxit]; wk.dq[l][1][v] = -Pb * g[kGett];
+      wk.dq[l][2][v] = -Pb * g[kGxix]; wk.dq[l][3][v] = -Pb * g[kGetx];
+      wk.dq[l][4][v] = -Pb * g[kGxiy]; wk.dq[l][5][v] = -Pb * g[kGety];
       double* pt = wk.part[l][v];
-      pt[0] = -Pb * n.Qx; pt[1] = -Pb * n.Qe;
-      pt[2] = -Pb * n.fx; pt[3] = -Pb * n.fe; pt[4] = -Pb * n.gx; pt[5] = -Pb * n.ge;
+      pt[0] = -Pb * d[0]; pt[1] = -Pb * d[1];
+      pt[2] = -Pb * d[2]; pt[3] = -Pb * d[3]; pt[4] = -Pb * d[4]; pt[5] = -Pb * d[5];
     }
     tm.sync();
     for (int l = tm.rank; l < nsl * Mc; l += tm.size) {
-      NodeGeoV n;
+      struct {
+        double xx, xe, yx, ye, xt, yt, idet, xix, xiy, etx, ety, xit, ett;
+      } n;
       const double* g = wk.geo[l];
-      n.xx = g[0]; n.xe = g[1]; n.yx = g[2]; n.ye = g[3]; n.xt = g[4]; n.yt = g[5]; n.idet = g[6];
-      n.xix = g[7]; n.xiy = g[8]; n.etx = g[9]; n.ety = g[10]; n.xit = g[11]; n.ett = g[12];
+      n.xx = g[kGxx]; n.xe = g[kGxe]; n.yx = g[kGyx]; n.ye = g[kGye]; n.xt = g[kGxt]; n.yt = g[kGyt];
+      n.idet = g[kGid]; n.xix = g[kGxix]; n.xiy = g[kGxiy]; n.etx = g[kGetx]; n.ety = g[kGety];
+      n.xit = g[kGxit]; n.ett = g[kGett];
       double xitb = 0, ettb = 0, xixb = 0, etxb = 0, xiyb = 0, etyb = 0;
       for (int v = 0; v < 4; ++v) {
         const double* pt = wk.part[l][v];

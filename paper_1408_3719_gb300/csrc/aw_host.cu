@@ -1524,12 +1524,16 @@ int aw_adjoint(aw_ctx* c, const double* dJdQ, const double* dJdX, const double* 
     }
     c->last_seg_kept = false;
     for (int64_t j = len - 1; j >= 0; --j) {
+      // the sweep's lists and its reverse read the sweep-start state where
+      // the snapshot holds it (they write only scratch lists and adjoints);
+      // only the counters go back to the live block
       const aw_ctx::Snap& pre = j == 0 ? c->ckpt[seg] : c->slots[j];
-      if ((rc = snap_copy(c, pre, false))) return rc;
-      launch_phase_a_lists(c->tab, c->d, c->nsm, c->stream);
+      launch_adj_reset(c->d, pre.cnt, c->stream);
+      const Dev pv = snap_view(c, pre);
+      launch_phase_a_lists(c->tab, pv, c->nsm, c->stream);
       const Dev post = snap_view(c, c->slots[j + 1]);
-      launch_adj_elem(c->tab, post, c->d, a, c->nsm, c->stream, 0);
-      launch_adj_phase_a(c->tab, c->d, post, a, c->nsm, c->stream);
+      launch_adj_elem(c->tab, post, pv, a, c->nsm, c->stream, 0);
+      launch_adj_phase_a(c->tab, pv, post, a, c->nsm, c->stream);
       CK(cudaGetLastError());
     }
   }
