@@ -19,6 +19,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -477,12 +478,34 @@ struct CopyList {
   int count;
 };
 
+// 16-byte words where both arrays allow them, four loads in flight per
+// thread before their stores; the odd tail word (and unaligned arrays) by
+// 8-byte words
 __global__ void k_multi_copy(CopyList cl) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  constexpr int U = 4;
   for (int k = 0; k < cl.count; ++k) {
     const unsigned long long* __restrict__ s = cl.src[k];
     unsigned long long* __restrict__ dd = cl.dst[k];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cl.n[k]; i += stride) dd[i] = s[i];
+    const long long n = cl.n[k];
+    long long done = 0;
+    if ((((uintptr_t)s | (uintptr_t)dd) & 15) == 0) {
+      const long long n2 = n / 2;
+      const ulonglong2* __restrict__ s2 = reinterpret_cast<const ulonglong2*>(s);
+      ulonglong2* __restrict__ d2 = reinterpret_cast<ulonglong2*>(dd);
+      long long i = tid;
+      for (; i + (U - 1) * nthr < n2; i += U * nthr) {
+        ulonglong2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = s2[i + u * nthr];
+#pragma unroll
+        for (int u = 0; u < U; ++u) d2[i + u * nthr] = v[u];
+      }
+      for (; i < n2; i += nthr) d2[i] = s2[i];
+      done = 2 * n2;
+    }
+    for (long long i = done + tid; i < n; i += nthr) dd[i] = s[i];
   }
 }
 
