@@ -357,6 +357,14 @@ def run_ours(args, rank, world):
         e, (nX, nt) = s.get_elem(), s.get_nodes()
         np.savez(args.save_state, nX=nX, nt=nt, sweeps=warm_sweeps, **e)
     t_warm_s = time.perf_counter() - t0
+    # the mid-run state for the end-to-end measurement below (the autotuner
+    # restores the state it starts from)
+    snap, snap_nodes = (s.get_elem(), s.get_nodes()) if args.e2e else (None, None)
+    # clocks and throttle reasons sampled from the autotuner's sweeps through
+    # the timed region (which alone lasts ~10 ms, shorter than nvidia-smi's
+    # 20 ms sampling period): the same kernels at the same load
+    clocks = ClockSampler(local)
+    clocks.start()
     # tile shapes picked by the library's autotuner on this state (it times
     # the same sweeps for every shape and restores the state)
     if args.tiles:
@@ -364,12 +372,6 @@ def run_ours(args, rank, world):
         tiles, tune_ms = s.get_tiles(), {}
     else:
         tiles, tune_ms = s.autotune(args.tune_sweeps) if args.tune_sweeps > 0 else (s.get_tiles(), {})
-    # the mid-run state for the end-to-end measurement below
-    snap, snap_nodes = (s.get_elem(), s.get_nodes()) if args.e2e else (None, None)
-    # clocks and throttle reasons sampled from the warm-up sweeps through the
-    # timed region (which alone lasts ~10 ms)
-    clocks = ClockSampler(local)
-    clocks.start()
     for _ in range(args.warmup):
         s.sweep()
     s.get_state(t=t_el)
