@@ -315,7 +315,9 @@ __device__ void kidder_state(const Tab& T, double x, double y, double t, double*
 // |v.n_xy + n_t| + c |n_xy|.
 __device__ __forceinline__ void rusanov(const Tab& T, const double* qm, const double* qp, const double* n,
                                         double* F) {
-  double rim = 1.0 / qm[0], rip = 1.0 / qp[0];
+  // both sides' 1 / rho from one reciprocal
+  const double rr = 1.0 / (qm[0] * qp[0]);
+  double rim = qp[0] * rr, rip = qm[0] * rr;
   double um = qm[1] * rim, vm = qm[2] * rim, up = qp[1] * rip, vp = qp[2] * rip;
   double pm = (T.gamma - 1.0) * (qm[3] - 0.5 * (qm[1] * um + qm[2] * vm));
   double pp = (T.gamma - 1.0) * (qp[3] - 0.5 * (qp[1] * up + qp[2] * vp));
@@ -392,6 +394,17 @@ __device__ __forceinline__ void osher(const Tab& T, const double* qm, const doub
   for (int v = 0; v < 4; ++v) F[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * D[v];
 }
 
+// Per-edge data of a swept surface, formed once per edge (not once per Gauss
+// point): its four corners (x, y, t in seconds: a, b at the old node times,
+// b', a' at the new ones), the corner ticks, and for each side its element,
+// local edge, time (ticks) and reciprocal step (0 for a zero step).
+struct EdgeSetup {
+  double P[4][3];
+  double tk[4];
+  double tL, itL, tR, itR, etL;
+  int L, R, le, lr, bc;
+};
+
 // One lane per Gauss point: (M+1)^2 consecutive lanes per swept edge,
 // 32 / (M+1)^2 edges per warp, the point contributions summed by a fixed
 // shuffle tree within each edge's lanes.
@@ -400,20 +413,20 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
   // one thread per Gauss point, the block's EPB edges packed back to back
   // (an edge's points may span two warps: every lane of a warp FP64
   // instruction costs the pipe the same, used or not), the point sums
-  // through shared memory in point order
+  // through shared memory in point order.  The per-edge set-up runs first,
+  // one thread per edge, so that its FP64 work (tick conversions, the
+  // sides' reciprocal steps) is issued once per edge instead of once per
+  // Gauss point.
   constexpr int Nt = M + 1, NP = Nt * Nt, EPB = kBlock / NP;
   __shared__ double sGN[kBlock][7];
+  __shared__ EdgeSetup sE[EPB];
   const int epoch = d.cnt->epoch;
   const int n_active = d.cnt->n_active;
   const int slot = threadIdx.x / NP, pt = threadIdx.x % NP;
   for (int first = blockIdx.x * EPB; first < n_active; first += gridDim.x * EPB) {
-    const int q = first + slot;
-    const bool valid = slot < EPB && q < n_active;
-    double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
-    int ed = -1;
-    if (valid) {
-      ed = d.active_list[q];
-      const int gx = pt / Nt, gt = pt % Nt;
+    for (int k = threadIdx.x; k < EPB; k += kBlock) {
+      if (first + k >= n_active) continue;
+      const int ed = d.active_list[first + k];
       const int a = d.edge_nodes[2 * ed], b = d.edge_nodes[2 * ed + 1];
       const int L = d.edge_elem[2 * ed], R = d.edge_elem[2 * ed + 1];
       const int le = d.edge_loc[2 * ed], lr = d.edge_loc[2 * ed + 1];
@@ -421,16 +434,48 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       const int le1 = le == 2 ? 0 : le + 1;
       const double sax = d.cshift[6 * L + 2 * le], say = d.cshift[6 * L + 2 * le + 1];
       const double sbx = d.cshift[6 * L + 2 * le1], sby = d.cshift[6 * L + 2 * le1 + 1];
-      double P[4][3];
+      const long long tL = d.t[L], dtL = d.dt[L];
+      const double etL = d.etick[L];
+      long long tR = 0, dtR = 0;
+      if (R >= 0) {
+        tR = d.t[R];
+        dtR = d.dt[R];
+      }
+      EdgeSetup& E = sE[k];
       long long tk[4];
-      P[0][0] = d.nX[2 * a] + sax; P[0][1] = d.nX[2 * a + 1] + say; tk[0] = d.nt[a];
-      P[1][0] = d.nX[2 * b] + sbx; P[1][1] = d.nX[2 * b + 1] + sby; tk[1] = d.nt[b];
-      if (mb) { P[2][0] = d.nXn[2 * b] + sbx; P[2][1] = d.nXn[2 * b + 1] + sby; tk[2] = d.ntn[b]; }
-      else { P[2][0] = P[1][0]; P[2][1] = P[1][1]; tk[2] = tk[1]; }
-      if (ma) { P[3][0] = d.nXn[2 * a] + sax; P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
-      else { P[3][0] = P[0][0]; P[3][1] = P[0][1]; tk[3] = tk[0]; }
+      E.P[0][0] = d.nX[2 * a] + sax; E.P[0][1] = d.nX[2 * a + 1] + say; tk[0] = d.nt[a];
+      E.P[1][0] = d.nX[2 * b] + sbx; E.P[1][1] = d.nX[2 * b + 1] + sby; tk[1] = d.nt[b];
+      if (mb) { E.P[2][0] = d.nXn[2 * b] + sbx; E.P[2][1] = d.nXn[2 * b + 1] + sby; tk[2] = d.ntn[b]; }
+      else { E.P[2][0] = E.P[1][0]; E.P[2][1] = E.P[1][1]; tk[2] = tk[1]; }
+      if (ma) { E.P[3][0] = d.nXn[2 * a] + sax; E.P[3][1] = d.nXn[2 * a + 1] + say; tk[3] = d.ntn[a]; }
+      else { E.P[3][0] = E.P[0][0]; E.P[3][1] = E.P[0][1]; tk[3] = tk[0]; }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) P[k][2] = (double)tk[k] * d.etick[L];
+      for (int c = 0; c < 4; ++c) {
+        E.tk[c] = (double)tk[c];
+        E.P[c][2] = E.tk[c] * etL;
+      }
+      // a reciprocal costs the FP64 pipe half a divide
+      E.tL = (double)tL;
+      E.itL = dtL > 0 ? 1.0 / (double)dtL : 0.0;
+      E.tR = (double)tR;
+      E.itR = dtR > 0 ? 1.0 / (double)dtR : 0.0;
+      E.etL = etL;
+      E.L = L; E.R = R; E.le = le; E.lr = lr;
+      E.bc = d.edge_bc[ed];
+    }
+    __syncthreads();
+    const int q = first + slot;
+    const bool valid = slot < EPB && q < n_active;
+    double G[4] = {0, 0, 0, 0}, Nn[3] = {0, 0, 0};
+    if (valid) {
+      const EdgeSetup& E = sE[slot];
+      const int gx = pt / Nt, gt = pt % Nt;
+      const int L = E.L, R = E.R, le = E.le, lr = E.lr;
+      double P[4][3];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P[k][c] = E.P[k][c];
       const double chi = T.glx[gx], tau = T.glx[gt], wq = T.glw[gx] * T.glw[gt];
       double dchi[3], dtau[3], n[3];
 #pragma unroll
@@ -441,12 +486,11 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
       n[0] = dchi[1] * dtau[2] - dchi[2] * dtau[1];
       n[1] = dchi[2] * dtau[0] - dchi[0] * dtau[2];
       n[2] = dchi[0] * dtau[1] - dchi[1] * dtau[0];
-      const double tt = (1 - chi) * (1 - tau) * (double)tk[0] + chi * (1 - tau) * (double)tk[1] +
-                        chi * tau * (double)tk[2] + (1 - chi) * tau * (double)tk[3];
+      const double tt = (1 - chi) * (1 - tau) * E.tk[0] + chi * (1 - tau) * E.tk[1] + chi * tau * E.tk[2] +
+                        (1 - chi) * tau * E.tk[3];
       double qm[4], qp[4];
       {
-        const long long tL = d.t[L], dtL = d.dt[L];
-        const double tl = dtL > 0 ? (tt - (double)tL) * (1.0 / (double)dtL) : 0.0;  // a reciprocal costs the FP64 pipe half a divide
+        const double tl = (tt - E.tL) * E.itL;
         const double* c0 = d.trace + ((((size_t)L * 3 + le) * Nt + gx) * Nt) * 4;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -456,9 +500,9 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
           qm[v] = acc;
         }
       }
+      const int bc = E.bc;
       if (R >= 0) {
-        const long long tR = d.t[R], dtR = d.dt[R];
-        const double tr = dtR > 0 ? (tt - (double)tR) * (1.0 / (double)dtR) : 0.0;
+        const double tr = (tt - E.tR) * E.itR;
         const double* c0 = d.trace + ((((size_t)R * 3 + lr) * Nt + (Nt - 1 - gx)) * Nt) * 4;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -467,23 +511,22 @@ __global__ void __launch_bounds__(kBlock) k_flux_grp(Tab T, Dev d) {
           for (int p = Nt - 2; p >= 0; --p) acc = acc * tr + c0[p * 4 + v];
           qp[v] = acc;
         }
-      } else if (d.edge_bc[ed] == 1) {
+      } else if (bc == 1) {
         // transmissive: the boundary element's sweep-start average (phase A
         // updates Q after this kernel), not the inner trace value, with
         // which a gas at rest beside the boundary grows from roundoff
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = d.Q[4 * (size_t)L + v];
-      } else if (d.edge_bc[ed] == 3) {
+      } else if (bc == 3) {
         // the exact Kidder state at the quadrature point
         const double px = (1 - chi) * (1 - tau) * P[0][0] + chi * (1 - tau) * P[1][0] + chi * tau * P[2][0] +
                           (1 - chi) * tau * P[3][0];
         const double py = (1 - chi) * (1 - tau) * P[0][1] + chi * (1 - tau) * P[1][1] + chi * tau * P[2][1] +
                           (1 - chi) * tau * P[3][1];
-        kidder_state(T, px, py, tt * d.etick[L], qp);
+        kidder_state(T, px, py, tt * E.etL, qp);
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) qp[v] = qm[v];
-        const int bc = d.edge_bc[ed];
         if (bc == 0 || bc == 2) {  // mirror the normal momentum relative to the wall
           const double wu = bc == 2 ? T.wall_u : 0.0, wv = bc == 2 ? T.wall_v : 0.0;
           const double nn = n[0] * n[0] + n[1] * n[1];
@@ -772,7 +815,9 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst, G = S::G;
   __shared__ double sq[G][Nst][4], sf[G][Nst][4], sg[G][Nst][4], sP[G][Nst][4];
   __shared__ double sx[G][Nst][2], sV[G][Nst][2];
-  __shared__ double sDxi[Mc][Mc], sDeta[Mc][Mc], sB[Nt - 1][Nt], sDtau[Nt][Nt], sTr[3][Nt][Mc], sVt[Nt][Nt];
+  // sTr: the 3 Nt rows of edge-trace weights (edge, Gauss point), then the
+  // reference-average weights, so that traces and averages share one code path
+  __shared__ double sDxi[Mc][Mc], sDeta[Mc][Mc], sB[Nt - 1][Nt], sDtau[Nt][Nt], sTr[3 * Nt + 1][Mc], sVt[Nt][Nt];
   __shared__ double sdts[G];
   __shared__ int sidx[G], sbad[G];
   for (int k = threadIdx.x; k < Mc * Mc; k += blockDim.x) {
@@ -784,7 +829,8 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
     sDtau[k / Nt][k % Nt] = T.Dtau[k / Nt][k % Nt];
     sVt[k / Nt][k % Nt] = T.VtInv[k / Nt][k % Nt];
   }
-  for (int k = threadIdx.x; k < 3 * Nt * Mc; k += blockDim.x) sTr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc] = T.Tr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc];
+  for (int k = threadIdx.x; k < 3 * Nt * Mc; k += blockDim.x) sTr[k / Mc][k % Mc] = T.Tr[k / (Nt * Mc)][(k / Mc) % Nt][k % Mc];
+  for (int k = threadIdx.x; k < Mc; k += blockDim.x) sTr[3 * Nt][k] = T.wavg[k];
   const int n_ready = initial ? d.ne : d.cnt->n_ready;
   const long long gmin = d.cnt->gts_min;
   // thread -> (time slice t, element e, lattice node s).  A warp-wide FP64
@@ -1004,44 +1050,29 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
       double* out = d.qhat + ((size_t)i * Nst + l) * 4;
 #pragma unroll
       for (int v = 0; v < 4; ++v) out[v] = sq[e][l][v];
-      // derived tables: edge traces, reference averages, vertex displacements
+      // derived tables: edge traces and reference averages (one code path:
+      // a weighted sum over each time slice's nodes, then the tau powers),
+      // vertex displacements
       constexpr int nTr = 3 * Nt * 4, nItems = nTr + 4 + 6;
       for (int item = l; item < nItems; item += Nst) {
-        if (item < nTr) {
-          const int le = item / (Nt * 4), g = (item / 4) % Nt, v = item % 4;
+        if (item < nTr + 4) {
+          const int row = item / 4, v = item % 4;  // row < 3 Nt: edge row / Nt, Gauss point row % Nt
+          const double* wts = sTr[row];
           double val[Nt];
 #pragma unroll
           for (int tt = 0; tt < Nt; ++tt) {
             double acc = 0.0;
 #pragma unroll
-            for (int r = 0; r < Mc; ++r) acc += sTr[le][g][r] * sq[e][tt * Mc + r][v];
+            for (int r = 0; r < Mc; ++r) acc += wts[r] * sq[e][tt * Mc + r][v];
             val[tt] = acc;
           }
-          double* tr = d.trace + (((size_t)i * 3 + le) * Nt + g) * Nt * 4;
+          double* dst = row < 3 * Nt ? d.trace + ((size_t)i * 3 * Nt + row) * Nt * 4 : d.avgc + (size_t)i * Nt * 4;
 #pragma unroll
           for (int p = 0; p < Nt; ++p) {
             double acc = 0.0;
 #pragma unroll
             for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * val[tt];
-            tr[p * 4 + v] = acc;
-          }
-        } else if (item < nTr + 4) {
-          const int v = item - nTr;
-          double val[Nt];
-#pragma unroll
-          for (int tt = 0; tt < Nt; ++tt) {
-            double acc = 0.0;
-#pragma unroll
-            for (int r = 0; r < Mc; ++r) acc += T.wavg[r] * sq[e][tt * Mc + r][v];
-            val[tt] = acc;
-          }
-          double* av = d.avgc + (size_t)i * Nt * 4;
-#pragma unroll
-          for (int p = 0; p < Nt; ++p) {
-            double acc = 0.0;
-#pragma unroll
-            for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * val[tt];
-            av[p * 4 + v] = acc;
+            dst[p * 4 + v] = acc;
           }
         } else {
           const int kc = item - nTr - 4, k = kc / 2, c = kc % 2;
@@ -1058,7 +1089,7 @@ __global__ void __launch_bounds__(TH, TH >= 256 ? 2 : 3) k_predict_coop(Tab T, D
             double acc = 0.0;
 #pragma unroll
             for (int tt = 0; tt < Nt; ++tt) acc += sVt[p][tt] * vel[tt];
-            vd[p] = acc / (p + 1);
+            vd[p] = acc * (1.0 / (p + 1));  // p is unrolled: a constant factor
           }
         }
       }
