@@ -330,11 +330,16 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp, const
     tp.gy = tp.c[0][0][0] * J[1] + tp.c[0][1][0] * J[3];
     tp.gn = sqrt(tp.gx * tp.gx + tp.gy * tp.gy);
     tp.nx = 1.0; tp.ny = 0.0;
-    if (tp.gn > 0.0) { tp.nx = tp.gx / tp.gn; tp.ny = tp.gy / tp.gn; }
-    const double g = T.gamma, rho = in.Q[0], u = in.Q[1] / rho, v = in.Q[2] / rho, nx = tp.nx, ny = tp.ny;
+    if (tp.gn > 0.0) {  // reciprocals, not divides: this runs on one rank
+      const double ign = 1.0 / tp.gn;
+      tp.nx = tp.gx * ign;
+      tp.ny = tp.gy * ign;
+    }
+    const double g = T.gamma, rho = in.Q[0], ir = 1.0 / rho, u = in.Q[1] * ir, v = in.Q[2] * ir;
+    const double nx = tp.nx, ny = tp.ny;
     const double p = (g - 1.0) * (in.Q[3] - 0.5 * rho * (u * u + v * v));
-    const double a = sqrt(g * p / rho), H = (in.Q[3] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
-    const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
+    const double a = sqrt(g * p * ir), H = (in.Q[3] + p) * ir, un = u * nx + v * ny, ut = -u * ny + v * nx;
+    const double ia = 1.0 / a, q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) * ia * ia, b2 = b1 * q2;
     double* R = tp.R;
     double* Lm = tp.Lm;
     R[0] = 1; R[1] = 1; R[2] = 0; R[3] = 1;

@@ -1393,13 +1393,19 @@ k_recon_coop(Tab T, Dev d, int initial) {
       const double* c0 = sC + (size_t)(e * kNSten) * NU * 4;
       const double gx = c0[0 * 4] * el[10] + c0[1 * 4] * el[12];
       const double gy = c0[0 * 4] * el[11] + c0[1 * 4] * el[13];
+      // on G lanes of one warp: three reciprocals and two square roots, no
+      // divides (each costs the warp's full FP64 issue)
       const double gn = sqrt(gx * gx + gy * gy);
       double nx = 1.0, ny = 0.0;
-      if (gn > 0.0) { nx = gx / gn; ny = gy / gn; }
-      const double g = T.gamma, rho = el[6], u = el[7] / rho, v = el[8] / rho;
+      if (gn > 0.0) {
+        const double ign = 1.0 / gn;
+        nx = gx * ign;
+        ny = gy * ign;
+      }
+      const double g = T.gamma, rho = el[6], ir = 1.0 / rho, u = el[7] * ir, v = el[8] * ir;
       const double p = (g - 1.0) * (el[9] - 0.5 * rho * (u * u + v * v));
-      const double a = sqrt(g * p / rho), H = (el[9] + p) / rho, un = u * nx + v * ny, ut = -u * ny + v * nx;
-      const double q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) / (a * a), b2 = b1 * q2, ia = 1.0 / a;
+      const double a = sqrt(g * p * ir), H = (el[9] + p) * ir, un = u * nx + v * ny, ut = -u * ny + v * nx;
+      const double ia = 1.0 / a, q2 = 0.5 * (u * u + v * v), b1 = (g - 1.0) * ia * ia, b2 = b1 * q2;
       double* R = sRL + e * 32;
       double* Lm = R + 16;
       R[0] = 1; R[1] = 1; R[2] = 0; R[3] = 1;
