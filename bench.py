@@ -392,6 +392,7 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    clk["window"] = "the autotuner's sweeps, the warm-up sweeps and the timed region (same kernels, same load)"
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     updates = s.sync()
     # per-kernel CUDA-event times: a second pass of the same number of sweeps
