@@ -721,15 +721,6 @@ __device__ __forceinline__ void virtual_data(const Tab& T, const Dev& d, int j, 
   }
 }
 
-template <int M>
-__device__ __forceinline__ void centred_monomials(const Tab& T, double x, double y, double* m) {
-  // graded order: degree 1: x, y; degree 2: x^2, xy, y^2; degree 3: x^3, x^2 y, x y^2, y^3
-  m[0] = x;
-  m[1] = y;
-  if (M >= 2) { m[2] = x * x; m[3] = x * y; m[4] = y * y; }
-  if (M >= 3) { m[5] = m[2] * x; m[6] = m[2] * y; m[7] = m[4] * x; m[8] = m[4] * y; }
-}
-
 // predictor-derived tables of element i from qh[Nt][Mc][4]
 template <int M>
 __device__ __forceinline__ void write_products(const Tab& T, const Dev& d, int i, const double (*qh)[(M + 1) * (M + 2) / 2][4]) {
@@ -1205,7 +1196,6 @@ k_recon_coop(Tab T, Dev d, int initial) {
     // virtCellaverage, intConsRec), then the time-step candidates
     // (eq. timestep) on the last threads of the block, so that the warps
     // holding rows do not also run the time-step code with a few lanes
-    constexpr int NQ = M == 1 ? 1 : (M == 2 ? 3 : 4);  // points of the exact degree-M rule
     for (int item = tid; item < sPre[G]; item += nth) {
       int e = 0;
       while (item >= sPre[e + 1]) ++e;
@@ -1225,17 +1215,46 @@ k_recon_coop(Tab T, Dev d, int initial) {
           xr[k] = el[10] * px + el[11] * py - (1.0 / 3.0);
           yr[k] = el[12] * px + el[13] * py - (1.0 / 3.0);
         }
+        // averages of the monomials over the virtual member (a straight
+        // triangle) in closed form: with the centroid c and the vertex
+        // offsets u_k = v_k - c, the second central moments are
+        // (1/12) sum_k u_k u_k^T and the third (1/30) sum_k u_k (x) u_k (x) u_k,
+        // so E[x^2] = c_x^2 + S_xx, E[x^2 y] = c_x^2 c_y + c_y S_xx + 2 c_x S_xy
+        // + T_xxy, ...  (what the degree-M quadrature gives, with fewer
+        // operations)
         double row[NU];
+        const double cx = (xr[0] + xr[1] + xr[2]) * (1.0 / 3.0), cy = (yr[0] + yr[1] + yr[2]) * (1.0 / 3.0);
+        row[0] = cx;
+        row[1] = cy;
+        if constexpr (M >= 2) {
+          double ux[3], uy[3];
 #pragma unroll
-        for (int a = 0; a < NU; ++a) row[a] = 0.0;
+          for (int k = 0; k < 3; ++k) {
+            ux[k] = xr[k] - cx;
+            uy[k] = yr[k] - cy;
+          }
+          const double sxx = (ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2]) * (1.0 / 12.0);
+          const double sxy = (ux[0] * uy[0] + ux[1] * uy[1] + ux[2] * uy[2]) * (1.0 / 12.0);
+          const double syy = (uy[0] * uy[0] + uy[1] * uy[1] + uy[2] * uy[2]) * (1.0 / 12.0);
+          row[2] = cx * cx + sxx;
+          row[3] = cx * cy + sxy;
+          row[4] = cy * cy + syy;
+          if constexpr (M >= 3) {
+            double txxx = 0.0, txxy = 0.0, txyy = 0.0, tyyy = 0.0;
 #pragma unroll
-        for (int qq = 0; qq < NQ; ++qq) {
-          const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
-          const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
-          double m[kMaxNU];
-          centred_monomials<M>(T, x, y, m);
-#pragma unroll
-          for (int a = 0; a < NU; ++a) row[a] += T.qw[qq] * m[a];
+            for (int k = 0; k < 3; ++k) {
+              const double xx = ux[k] * ux[k], yy = uy[k] * uy[k];
+              txxx += xx * ux[k];
+              txxy += xx * uy[k];
+              txyy += yy * ux[k];
+              tyyy += yy * uy[k];
+            }
+            const double c30 = 1.0 / 30.0;
+            row[5] = cx * (cx * cx + 3.0 * sxx) + txxx * c30;
+            row[6] = cy * (cx * cx + sxx) + 2.0 * cx * sxy + txxy * c30;
+            row[7] = cx * (cy * cy + syy) + 2.0 * cy * sxy + txyy * c30;
+            row[8] = cy * (cy * cy + 3.0 * syy) + tyyy * c30;
+          }
         }
         double* dst = sRow + ((size_t)e * (MaxU + 1) + u + 1) * RW;
 #pragma unroll
