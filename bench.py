@@ -55,10 +55,11 @@ def predictor_flops(M: int) -> float:
 def recon_flops(M: int, members: float) -> float:
     Mc, Nt = (M + 1) * (M + 2) // 2, M + 1
     NU, NE = Mc - 1, 2 * Mc
-    nq = {1: 1, 2: 3, 3: 4}[M]
+    # monomial averages over the member from its centroid and central moments
+    moments = {1: 6, 2: 36, 3: 90}[M]
     per_member = (6 * 2 * Nt + 4 * 2 * (Nt - 1) + 4   # virtual vertices and average (Horner)
                   + 3 * 8                              # map to the reference frame of T_i
-                  + nq * (4 + max(NU - 2, 0) + 2 * NU) + NU + 4)
+                  + moments + NU + 4)
     per_stencil = ((NE - 1) * (NU * (NU + 1) + 8 * NU)  # normal equations
                    + NU ** 3 / 3 + 2 * NU               # Cholesky
                    + 4 * 2 * NU * NU                    # two triangular solves, 4 right-hand sides
