@@ -130,21 +130,80 @@ AW_HD inline void tri_area_rev(const double* X, double s, double* Xb) {
   Xb[5] += 0.5 * s * (X[2] - X[0]);
 }
 
-// graded monomials of degree 1..M and their x, y derivatives
+// Averages of the graded monomials (mono's order) over the straight triangle
+// with vertices (x_k, y_k), in closed form: with the centroid c and the
+// offsets u_k = v_k - c (sum u_k = 0), the second central moments are
+// S = (1/12) sum u u^T and the third (1/30) sum u (x) u (x) u; e.g.
+// E[x^2] = c_x^2 + S_xx, E[x^2 y] = c_y (c_x^2 + S_xx) + 2 c_x S_xy + T_xxy.
 template <int M>
-AW_HD inline void mono(double x, double y, double* m, double* mx, double* my) {
-  m[0] = x; mx[0] = 1; my[0] = 0;
-  m[1] = y; mx[1] = 0; my[1] = 1;
+AW_HD inline void tri_monomial_avgs(const double* x, const double* y, double* row) {
+  const double cx = (x[0] + x[1] + x[2]) * (1.0 / 3.0), cy = (y[0] + y[1] + y[2]) * (1.0 / 3.0);
+  row[0] = cx;
+  row[1] = cy;
   if (M >= 2) {
-    m[2] = x * x; mx[2] = 2 * x; my[2] = 0;
-    m[3] = x * y; mx[3] = y; my[3] = x;
-    m[4] = y * y; mx[4] = 0; my[4] = 2 * y;
+    double ux[3], uy[3];
+    for (int k = 0; k < 3; ++k) {
+      ux[k] = x[k] - cx;
+      uy[k] = y[k] - cy;
+    }
+    const double sxx = (ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2]) * (1.0 / 12.0);
+    const double sxy = (ux[0] * uy[0] + ux[1] * uy[1] + ux[2] * uy[2]) * (1.0 / 12.0);
+    const double syy = (uy[0] * uy[0] + uy[1] * uy[1] + uy[2] * uy[2]) * (1.0 / 12.0);
+    row[2] = cx * cx + sxx;
+    row[3] = cx * cy + sxy;
+    row[4] = cy * cy + syy;
+    if (M >= 3) {
+      double txxx = 0.0, txxy = 0.0, txyy = 0.0, tyyy = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double xx = ux[k] * ux[k], yy = uy[k] * uy[k];
+        txxx += xx * ux[k];
+        txxy += xx * uy[k];
+        txyy += yy * ux[k];
+        tyyy += yy * uy[k];
+      }
+      const double c30 = 1.0 / 30.0;
+      row[5] = cx * (cx * cx + 3.0 * sxx) + txxx * c30;
+      row[6] = cy * (cx * cx + sxx) + 2.0 * cx * sxy + txxy * c30;
+      row[7] = cx * (cy * cy + syy) + 2.0 * cy * sxy + txyy * c30;
+      row[8] = cy * (cy * cy + 3.0 * syy) + tyyy * c30;
+    }
   }
-  if (M >= 3) {
-    m[5] = m[2] * x; mx[5] = 3 * x * x; my[5] = 0;
-    m[6] = m[2] * y; mx[6] = 2 * x * y; my[6] = x * x;
-    m[7] = m[4] * x; mx[7] = y * y; my[7] = 2 * x * y;
-    m[8] = m[4] * y; mx[8] = 0; my[8] = 3 * y * y;
+}
+
+// Reverse of tri_monomial_avgs: adds sum_a rb[a] d row_a / d x_k to xb[k]
+// (and likewise yb); d c_x / d x_k = 1/3, d S_xx / d x_k = u_k / 6,
+// d (sum u_x^3) / d x_k = 3 u_k^2 - 12 S_xx, and so on (sum u = 0).
+template <int M>
+AW_HD inline void tri_monomial_avgs_rev(const double* x, const double* y, const double* rb, double* xb, double* yb) {
+  const double cx = (x[0] + x[1] + x[2]) * (1.0 / 3.0), cy = (y[0] + y[1] + y[2]) * (1.0 / 3.0);
+  double ux[3], uy[3];
+  for (int k = 0; k < 3; ++k) {
+    ux[k] = x[k] - cx;
+    uy[k] = y[k] - cy;
+  }
+  const double sxx = (ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2]) * (1.0 / 12.0);
+  const double sxy = (ux[0] * uy[0] + ux[1] * uy[1] + ux[2] * uy[2]) * (1.0 / 12.0);
+  const double syy = (uy[0] * uy[0] + uy[1] * uy[1] + uy[2] * uy[2]) * (1.0 / 12.0);
+  const double t3 = 1.0 / 3.0, c30 = 1.0 / 30.0;
+  for (int k = 0; k < 3; ++k) {
+    double gx = rb[0] * t3, gy = rb[1] * t3;
+    if (M >= 2) {
+      gx += rb[2] * (2.0 * cx * t3 + ux[k] * (1.0 / 6.0)) + rb[3] * (cy * t3 + uy[k] * (1.0 / 12.0));
+      gy += rb[3] * (cx * t3 + ux[k] * (1.0 / 12.0)) + rb[4] * (2.0 * cy * t3 + uy[k] * (1.0 / 6.0));
+    }
+    if (M >= 3) {
+      const double xy = ux[k] * uy[k];
+      gx += rb[5] * (cx * cx + sxx + 0.5 * cx * ux[k] + (3.0 * ux[k] * ux[k] - 12.0 * sxx) * c30);
+      gx += rb[6] * (2.0 * cx * cy * t3 + (cy * ux[k] + cx * uy[k]) * (1.0 / 6.0) + 2.0 * sxy * t3 +
+                     (2.0 * xy - 8.0 * sxy) * c30);
+      gx += rb[7] * ((cy * cy + syy) * t3 + cy * uy[k] * (1.0 / 6.0) + (uy[k] * uy[k] - 4.0 * syy) * c30);
+      gy += rb[6] * ((cx * cx + sxx) * t3 + cx * ux[k] * (1.0 / 6.0) + (ux[k] * ux[k] - 4.0 * sxx) * c30);
+      gy += rb[7] * (2.0 * cx * cy * t3 + (cx * uy[k] + cy * ux[k]) * (1.0 / 6.0) + 2.0 * sxy * t3 +
+                     (2.0 * xy - 8.0 * sxy) * c30);
+      gy += rb[8] * (cy * cy + syy + 0.5 * cy * uy[k] + (3.0 * uy[k] * uy[k] - 12.0 * syy) * c30);
+    }
+    xb[k] += gx;
+    yb[k] += gy;
   }
 }
 
@@ -261,14 +320,7 @@ AW_HD void recon_fwd(const Tab& T, const ReconIn<M>& in, ReconTape<M>& tp, const
       yr[k] = J[2] * px + J[3] * py - (1.0 / 3.0);
     }
     double row[NU];
-    for (int a = 0; a < NU; ++a) row[a] = 0.0;
-    for (int qq = 0; qq < T.nq; ++qq) {
-      const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
-      const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
-      double m[kMaxNU], mx[kMaxNU], my[kMaxNU];
-      mono<M>(x, y, m, mx, my);
-      for (int a = 0; a < NU; ++a) row[a] += T.qw[qq] * m[a];
-    }
+    tri_monomial_avgs<M>(xr, yr, row);
     double* dst = tp.rows[u + 1];
     for (int a = 0; a < NU; ++a) dst[a] = row[a] - T.mbar[a];
     for (int v = 0; v < 4; ++v) dst[NU + v] = in.Qv[u][v] - in.Q[v];
@@ -627,21 +679,7 @@ AW_HD void recon_rev(const Tab& T, const ReconIn<M>& in, const ReconTape<M>& tp,
       yr[k] = J[2] * px[k] + J[3] * py[k] - (1.0 / 3.0);
     }
     double xrb[3] = {0, 0, 0}, yrb[3] = {0, 0, 0};
-    for (int qq = 0; qq < T.nq; ++qq) {
-      const double x = T.qb[qq][0] * xr[0] + T.qb[qq][1] * xr[1] + T.qb[qq][2] * xr[2];
-      const double y = T.qb[qq][0] * yr[0] + T.qb[qq][1] * yr[1] + T.qb[qq][2] * yr[2];
-      double m[kMaxNU], mx[kMaxNU], my[kMaxNU];
-      mono<M>(x, y, m, mx, my);
-      double xb = 0.0, yb = 0.0;
-      for (int a = 0; a < NU; ++a) {
-        xb += rb[a] * T.qw[qq] * mx[a];
-        yb += rb[a] * T.qw[qq] * my[a];
-      }
-      for (int k = 0; k < 3; ++k) {
-        xrb[k] += T.qb[qq][k] * xb;
-        yrb[k] += T.qb[qq][k] * yb;
-      }
-    }
+    tri_monomial_avgs_rev<M>(xr, yr, rb, xrb, yrb);
     for (int k = 0; k < 3; ++k) {
       const double pxb = J[0] * xrb[k] + J[2] * yrb[k], pyb = J[1] * xrb[k] + J[3] * yrb[k];
       pJ[0] += xrb[k] * px[k];
