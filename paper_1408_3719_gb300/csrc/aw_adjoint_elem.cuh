@@ -946,19 +946,30 @@ AW_HD void pred_rev(const Tab& T, int nit, double dts, const PredTape<M>& tp, co
   using S = Sz<M>;
   constexpr int Mc = S::Mc, Nt = S::Nt, Nst = S::Nst;
   // tables: the adjoint of every node of the final predictor (per variable,
-  // then the vertex velocities per node)
+  // then the vertex velocities per node).  First the tables' adjoints through
+  // the tau powers, once per (edge, Gauss point, time slice, variable) and per
+  // (time slice, variable) of the average, not once per node; then per node.
+  double* vb = &wk.dq[0][0][0];  // free until the Picard iterations' reverse
+  constexpr int nV = 3 * Nt * Nt * 4, nA = Nt * 4;
+  static_assert(nV + nA <= Nst * 6 * 4, "table adjoints exceed their scratch");
+  for (int it = tm.rank; it < nV + nA; it += tm.size) {
+    double acc = 0.0;
+    if (it < nV) {
+      const int e = it / (Nt * Nt * 4), g = (it / (Nt * 4)) % Nt, tt = (it / 4) % Nt, v = it % 4;
+      for (int p = 0; p < Nt; ++p) acc += T.VtInv[p][tt] * tb.tr[e][g][p][v];
+    } else {
+      const int tt = (it - nV) / 4, v = (it - nV) % 4;
+      for (int p = 0; p < Nt; ++p) acc += T.VtInv[p][tt] * tb.av[p][v];
+    }
+    vb[it] = acc;
+  }
+  tm.sync();
   for (int it4 = tm.rank; it4 < Nst * 4; it4 += tm.size) {
     const int l = it4 / 4, v = it4 % 4, tt = l / Mc, r = l % Mc;
     double acc = 0.0;
     for (int e = 0; e < 3; ++e)
-      for (int g = 0; g < Nt; ++g) {
-        double valb = 0.0;
-        for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.tr[e][g][p][v];
-        acc += T.Tr[e][g][r] * valb;
-      }
-    double valb = 0.0;
-    for (int p = 0; p < Nt; ++p) valb += T.VtInv[p][tt] * tb.av[p][v];
-    acc += T.wavg[r] * valb;
+      for (int g = 0; g < Nt; ++g) acc += T.Tr[e][g][r] * vb[((e * Nt + g) * Nt + tt) * 4 + v];
+    acc += T.wavg[r] * vb[nV + tt * 4 + v];
     wk.qb[l][v] = acc;
   }
   tm.sync();
