@@ -318,23 +318,6 @@ int build_tab(aw_ctx* c) {
       T.SigU[j][i] = v / T.SigU[j][j];
     }
   }
-  // exact rules for averages of degree-M polynomials over a triangle
-  if (M == 1) {
-    T.nq = 1; T.qb[0][0] = T.qb[0][1] = T.qb[0][2] = 1.0 / 3.0; T.qw[0] = 1.0;
-  } else if (M == 2) {
-    T.nq = 3;
-    for (int k = 0; k < 3; ++k) {
-      for (int m = 0; m < 3; ++m) T.qb[k][m] = (m == k) ? 2.0 / 3.0 : 1.0 / 6.0;
-      T.qw[k] = 1.0 / 3.0;
-    }
-  } else {
-    T.nq = 4;
-    T.qb[0][0] = T.qb[0][1] = T.qb[0][2] = 1.0 / 3.0; T.qw[0] = -27.0 / 48.0;
-    for (int k = 0; k < 3; ++k) {
-      for (int m = 0; m < 3; ++m) T.qb[k + 1][m] = (m == k) ? 0.6 : 0.2;
-      T.qw[k + 1] = 25.0 / 48.0;
-    }
-  }
   return AW_OK;
 }
 

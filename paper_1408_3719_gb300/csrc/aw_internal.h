@@ -13,12 +13,11 @@ constexpr int kMaxNt = 4;    // M+1 Gauss-Lobatto times
 constexpr int kMaxNU = 9;    // Mc - 1 non-constant basis functions
 constexpr int kMaxNe = 20;   // stencil size n_e = 2 Mc
 constexpr int kNSten = 7;    // central + 3 primary + 3 reverse sectors
-constexpr int kMaxQ = 4;     // points of the reconstruction-average rule
 
 // Reference tables of one order M, built on the host at context creation and
 // passed to kernels by value (uniform reads broadcast from the parameter bank).
 struct Tab {
-  int M, Mc, Nt, Nst, NU, nq;
+  int M, Mc, Nt, Nst, NU;
   double gamma, cfl, tick;
   long long T;          // t_end in ticks
   int eulerian;         // mesh velocity V = 0
@@ -41,7 +40,6 @@ struct Tab {
   int mexp[kMaxNU][2];
   double mbar[kMaxNU];
   double SigU[kMaxNU][kMaxNU];    // upper Cholesky factor: sigma = |SigU c|^2
-  double qb[kMaxQ][3], qw[kMaxQ];
   double glx[kMaxNt], glw[kMaxNt];
 };
 
